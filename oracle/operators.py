@@ -1,0 +1,118 @@
+"""FP64 oracle operators: parallel-beam geometry, Joseph K / K^T, finite
+differences D / D^T.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+
+import numpy as np
+
+from . import _clib
+
+
+@dataclasses.dataclass
+class Geometry:
+    """Parallel-beam geometry (Sec. 2, eq. (radon-def): rays u cos + v sin = s).
+
+    theta: angles (float64); by default theta_a = a*pi/n_angles.
+    row_branch[a] is 1 when the ray is stepped over image rows (|cos| >= |sin|,
+    ties included).  For the default angles the test is done exactly on the
+    integer a (4a <= n or 4a >= 3n); for user angles it is done on the FP64
+    cos/sin values.
+    """
+    N: int
+    n_angles: int
+    n_det: int
+    spacing: float = 1.0
+    offset: float = 0.0
+    theta: np.ndarray | None = None
+
+    def __post_init__(self):
+        if self.theta is None:
+            self.theta = np.arange(self.n_angles, dtype=np.float64) * (math.pi / self.n_angles)
+            a = np.arange(self.n_angles)
+            rb = (4 * a <= self.n_angles) | (4 * a >= 3 * self.n_angles)
+        else:
+            self.theta = np.asarray(self.theta, dtype=np.float64)
+            rb = np.abs(np.cos(self.theta)) >= np.abs(np.sin(self.theta))
+        self.cos = np.ascontiguousarray(np.cos(self.theta))
+        self.sin = np.ascontiguousarray(np.sin(self.theta))
+        self.row_branch = np.ascontiguousarray(rb.astype(np.int32))
+
+    @property
+    def m(self) -> int:
+        return self.n_angles * self.n_det
+
+    @property
+    def n(self) -> int:
+        return self.N * self.N
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def K(x: np.ndarray, g: Geometry) -> np.ndarray:
+    """Joseph forward projection y = K x, y[a, t] (float64)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(g.N, g.N)
+    y = np.empty((g.n_angles, g.n_det), dtype=np.float64)
+    _clib.lib().oracle_joseph_forward(g.N, g.n_angles, g.n_det, _dp(g.cos), _dp(g.sin),
+                                      g.row_branch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                      g.spacing, g.offset, _dp(x), _dp(y))
+    return y
+
+
+def KT(y: np.ndarray, g: Geometry) -> np.ndarray:
+    """Exact transpose x = K^T y of the Joseph projector (float64, N x N)."""
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(g.n_angles, g.n_det)
+    x = np.empty((g.N, g.N), dtype=np.float64)
+    _clib.lib().oracle_joseph_transpose(g.N, g.n_angles, g.n_det, _dp(g.cos), _dp(g.sin),
+                                        g.row_branch.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                        g.spacing, g.offset, _dp(y), _dp(x))
+    return x
+
+
+# ---------------------------------------------------------------------------
+# Finite differences (Sec. 2): D_n has rows [1, -1], so (D_n x)_i = x_i - x_{i+1},
+# D_n in R^{(n-1) x n}.  In 2D, D_2 = [I (x) D_n ; D_n (x) I] acting on the
+# row-major image: horizontal differences (along a row) and vertical ones.
+# ---------------------------------------------------------------------------
+
+def D(x: np.ndarray):
+    """Return (dh, dv): dh[j, i] = x[j,i]-x[j,i+1] (N x N-1), dv[j, i] = x[j,i]-x[j+1,i] (N-1 x N)."""
+    x = np.asarray(x, dtype=np.float64)
+    return x[:, :-1] - x[:, 1:], x[:-1, :] - x[1:, :]
+
+
+def DT(dh: np.ndarray, dv: np.ndarray) -> np.ndarray:
+    """Transpose of D: D^T (dh, dv), N x N."""
+    N = dh.shape[0]
+    out = np.zeros((N, N), dtype=np.float64)
+    out[:, :-1] += dh
+    out[:, 1:] -= dh
+    out[:-1, :] += dv
+    out[1:, :] -= dv
+    return out
+
+
+def D1_matrix(n: int) -> np.ndarray:
+    """Dense D_n (Sec. 2): (n-1) x n with 1 on the diagonal and -1 above it."""
+    Dn = np.zeros((n - 1, n))
+    for i in range(n - 1):
+        Dn[i, i] = 1.0
+        Dn[i, i + 1] = -1.0
+    return Dn
+
+
+def dense_of(op, n_in: int) -> np.ndarray:
+    """Dense matrix of a linear map given as a function on flat vectors."""
+    cols = []
+    for k in range(n_in):
+        e = np.zeros(n_in)
+        e[k] = 1.0
+        cols.append(np.ravel(op(e)))
+    return np.stack(cols, axis=1)

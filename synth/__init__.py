@@ -1,0 +1,27 @@
+"""Seeded synthetic inputs for the NCS workloads (phantoms, sinograms, noise).
+
+This module is shared by the FP64 oracle, the tests and the benchmark.  It holds
+none of the method's arithmetic (no discrete projector, no finite differences,
+no circulant solve, no proximal map): the measured data are the exact line
+integrals of an ellipse phantom, so no discretised projector is needed to make
+them.
+
+Conventions (the paper's Radon transform, Sec. 2, eq. (radon-def)):
+  * image x[j, i], N x N, row-major; pixel centre (u, v) = (i - (N-1)/2, (N-1)/2 - j)
+    in pixel units (u to the right, v up);
+  * angles theta_a = a*pi/n_angles, a = 0..n_angles-1;
+  * detector bin centres s_t = (t - (n_det-1)/2) * det_spacing + det_offset;
+  * a ray is the line u cos(theta) + v sin(theta) = s; the sinogram is y[a, t].
+"""
+from .phantom import (  # noqa: F401
+    Ellipses,
+    draw_ellipses,
+    rasterize,
+    radon_ellipses,
+    angles,
+    det_centres,
+    ct_problem,
+    pet_problem,
+    WORKLOADS,
+    batch_sides,
+)

@@ -1,0 +1,162 @@
+"""Seeded ellipse phantoms, their exact parallel-beam sinograms, and noise.
+
+Recipe (the stand-in for the paper's patient / XCAT / PET data of Sec. 5, which
+are not available): x_true is a sum of random ellipses in a [-1, 1]^2 frame,
+b is the exact line integral of the same ellipses along every ray (pixel units)
+plus Gaussian noise (CT) or a Poisson draw (PET).  Every array is rounded once
+to float32 so that the GPU path and the FP64 oracle consume identical values.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Ellipses:
+    """Ellipse parameters in the normalised frame [-1, 1]^2 (one row per ellipse).
+
+    cx, cy: centre; ax, ay: semi-axes; phi: rotation of the ax-axis from +u;
+    rho: additive intensity.
+    """
+    cx: np.ndarray
+    cy: np.ndarray
+    ax: np.ndarray
+    ay: np.ndarray
+    phi: np.ndarray
+    rho: np.ndarray
+
+    def __len__(self):
+        return len(self.cx)
+
+
+def draw_ellipses(rng: np.random.Generator, n: int) -> Ellipses:
+    """Draw n ellipses: centres U[-0.8,0.8]^2, semi-axes U[0.05,0.5], rotation
+    U[0,pi), intensity U[0,1].  The draw order is fixed (centres, axes,
+    rotations, intensities) so a seed always gives the same phantom."""
+    c = rng.uniform(-0.8, 0.8, size=(n, 2))
+    ax = rng.uniform(0.05, 0.5, size=(n, 2))
+    phi = rng.uniform(0.0, math.pi, size=n)
+    rho = rng.uniform(0.0, 1.0, size=n)
+    return Ellipses(c[:, 0].copy(), c[:, 1].copy(), ax[:, 0].copy(), ax[:, 1].copy(), phi, rho)
+
+
+def _pixel_grid(N: int):
+    """Normalised coordinates of the pixel centres, arrays of shape (N, N)."""
+    idx = np.arange(N, dtype=np.float64)
+    u = (idx - (N - 1) / 2.0) * (2.0 / N)          # columns, left to right
+    v = ((N - 1) / 2.0 - idx) * (2.0 / N)          # rows, top to bottom
+    U, V = np.meshgrid(u, v)                       # U[j, i] = u_i, V[j, i] = v_j
+    return U, V
+
+
+def rasterize(ell: Ellipses, N: int) -> np.ndarray:
+    """Pixel value = sum of the intensities of the ellipses that contain the
+    pixel centre (float64, shape (N, N))."""
+    U, V = _pixel_grid(N)
+    img = np.zeros((N, N), dtype=np.float64)
+    for k in range(len(ell)):
+        du, dv = U - ell.cx[k], V - ell.cy[k]
+        c, s = math.cos(ell.phi[k]), math.sin(ell.phi[k])
+        p = (du * c + dv * s) / ell.ax[k]
+        q = (-du * s + dv * c) / ell.ay[k]
+        img += np.where(p * p + q * q <= 1.0, ell.rho[k], 0.0)
+    return img
+
+
+def angles(n_angles: int) -> np.ndarray:
+    """theta_a = a*pi/n_angles (float64)."""
+    return np.arange(n_angles, dtype=np.float64) * (math.pi / n_angles)
+
+
+def det_centres(n_det: int, det_spacing: float = 1.0, det_offset: float = 0.0) -> np.ndarray:
+    """s_t = (t - (n_det-1)/2)*spacing + offset in pixel units (float64)."""
+    return (np.arange(n_det, dtype=np.float64) - (n_det - 1) / 2.0) * det_spacing + det_offset
+
+
+def radon_ellipses(ell: Ellipses, N: int, theta: np.ndarray, s_pix: np.ndarray) -> np.ndarray:
+    """Exact line integrals (pixel units) of the ellipse phantom along the rays
+    u cos(theta) + v sin(theta) = s, returned as y[a, t] (float64).
+
+    For one ellipse the chord along a line at signed distance s' from its
+    centre is 2*A*B*sqrt(a2 - s'^2)/a2 with a2 = A^2 cos^2(theta-phi) +
+    B^2 sin^2(theta-phi) (textbook closed form; checked by brute-force
+    sampling in the tests).  Lengths are computed in the normalised frame and
+    scaled by N/2 to pixel units.
+    """
+    th = np.asarray(theta, dtype=np.float64)[:, None]
+    s = np.asarray(s_pix, dtype=np.float64)[None, :] * (2.0 / N)
+    out = np.zeros((th.shape[0], s.shape[1]), dtype=np.float64)
+    for k in range(len(ell)):
+        A, B = ell.ax[k], ell.ay[k]
+        d = th - ell.phi[k]
+        a2 = (A * np.cos(d)) ** 2 + (B * np.sin(d)) ** 2
+        sp = s - (ell.cx[k] * np.cos(th) + ell.cy[k] * np.sin(th))
+        disc = a2 - sp * sp
+        out += np.where(disc > 0.0, 2.0 * ell.rho[k] * A * B * np.sqrt(np.maximum(disc, 0.0)) / a2, 0.0)
+    return out * (N / 2.0)
+
+
+def _f32(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+
+
+def ct_problem(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int,
+               noise_frac: float, det_spacing: float = 1.0, det_offset: float = 0.0) -> dict:
+    """Seeded TV-CT instance: b = exact projection of the phantom + N(0, sigma^2)
+    with sigma = noise_frac * max(exact projection).  Arrays are float32."""
+    rng = np.random.default_rng(seed)
+    ell = draw_ellipses(rng, n_ellipses)
+    x_true = rasterize(ell, N)
+    th = angles(n_angles)
+    sino = radon_ellipses(ell, N, th, det_centres(n_det, det_spacing, det_offset))
+    sigma = noise_frac * float(sino.max())
+    b = sino + rng.normal(0.0, sigma, size=sino.shape)
+    return dict(kind="ct", seed=seed, N=N, n_angles=n_angles, n_det=n_det,
+                det_spacing=det_spacing, det_offset=det_offset,
+                x_true=_f32(x_true), b=_f32(b), sigma=sigma)
+
+
+def pet_problem(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int,
+                total_counts: float = 1e6, bg_frac: float = 0.1) -> dict:
+    """Seeded TV-PET instance: y ~ Poisson(s*P + r) where P is the exact
+    projection of the activity phantom, s scales sum(s*P) to total_counts and
+    the uniform background r is bg_frac times the mean of s*P.  Arrays float32;
+    r_bg is a full sinogram-shaped array (uniform)."""
+    rng = np.random.default_rng(seed)
+    ell = draw_ellipses(rng, n_ellipses)
+    x_true = rasterize(ell, N)
+    th = angles(n_angles)
+    sino = radon_ellipses(ell, N, th, det_centres(n_det))
+    scale = total_counts / float(sino.sum())
+    mean_counts = scale * sino
+    r = bg_frac * float(mean_counts.mean())
+    y = rng.poisson(mean_counts + r).astype(np.float64)
+    return dict(kind="pet", seed=seed, N=N, n_angles=n_angles, n_det=n_det,
+                det_spacing=1.0, det_offset=0.0,
+                x_true=_f32(x_true * scale), b=_f32(y),
+                r_bg=_f32(np.full_like(y, r)), scale=scale, r=r)
+
+
+def batch_sides(seed: int, n_slices: int = 64, choices=(256, 384, 512)) -> list:
+    """Image sides of the uneven batch, drawn by seed; angles = round(1.4*side),
+    bins = side + 2 for each slice."""
+    rng = np.random.default_rng(seed)
+    sides = rng.choice(np.asarray(choices), size=n_slices)
+    return [int(s) for s in sides]
+
+
+# Named workloads (sizes, regularisation and noise of each synthetic case).
+WORKLOADS = {
+    # 64x64 TV-CT, anisotropic TV, lambda 0.01, 1% noise, 10 ellipses.
+    "ct64": dict(kind="ct", N=64, n_angles=90, n_det=92, n_ellipses=10, noise_frac=0.01,
+                 lam=0.01, tv="aniso"),
+    # 512x512 TV-CT, isotropic TV, lambda 0.005, 0.5% noise, 20 ellipses.
+    "ct512": dict(kind="ct", N=512, n_angles=720, n_det=730, n_ellipses=20, noise_frac=0.005,
+                  lam=0.005, tv="iso"),
+    # 256x256 TV-PET, 1e6 counts, 10% background, lambda 0.02, nonnegativity.
+    "pet256": dict(kind="pet", N=256, n_angles=180, n_det=257, n_ellipses=15,
+                   lam=0.02, tv="aniso"),
+}
