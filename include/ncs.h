@@ -1,0 +1,184 @@
+/*
+ * ncs.h - C ABI of the GB300 (sm_103a) near-circulant splitting library.
+ *
+ * Near-circulant splitting (NCS), Ryu, Ko, Won, "Splitting with
+ * Near-Circulant Linear Systems: Applications to Total Variation CT and PET"
+ * (arXiv 1810.13100), solves  min_x g(Ax - b)  (Sec. 1, eq. (RCP)) with
+ *
+ *     x+   = x - M^+ A^T u                                  (eq. (NCS))
+ *     u+   = prox_{alpha g*}(u + alpha (A (2x+ - x) - b))
+ *
+ * for the TV-CT problem of Sec. 4.1, A = [K; (beta/alpha) D], and the TV-PET
+ * problem of Sec. 4.2, A = [K; (beta/alpha) D; kappa I] (the nonnegativity row of
+ * its remark).  K is a parallel-beam Joseph projector, D the 2-D forward
+ * difference operator (Sec. 2), and M = gamma I + alpha C is the circulant
+ * matrix whose eigenvalues come from eqs. (circ_R) and (circ_D), solved with a
+ * real 2-D FFT.  PDHG (eq. (PDHG)) is provided on the same kernels.
+ *
+ * Conventions shared by every entry point
+ *   - Image x: N x N float32, row-major, x[j*N + i]; row j, column i; pixel
+ *     centre (u, v) = (i - (N-1)/2, (N-1)/2 - j) in pixel units.
+ *   - Sinogram y: n_angles x n_det float32, row-major, y[a*n_det + t]; the ray
+ *     of bin t at angle theta_a is u cos + v sin = s_t (Sec. 2, eq. (radon-def)),
+ *     s_t = (t - (n_det-1)/2) * det_spacing + det_offset.
+ *   - TV dual v: 2 x N x N float32; v[0..N*N) holds the horizontal block
+ *     (D_h x)[j][i] = x[j][i] - x[j][i+1], v[N*N..2*N*N) the vertical block
+ *     (D_v x)[j][i] = x[j][i] - x[j+1][i]; the last column of the first block
+ *     and the last row of the second are not part of D (kept at zero).
+ *   - Nonnegativity dual s: N x N float32 (PET with nonneg only, else NULL).
+ *   - All array pointers are DEVICE pointers unless a name says host, and are
+ *     owned by the caller.  Work is enqueued on the plan's stream
+ *     (ncs_options.cuda_stream, or a stream the plan creates); calls return
+ *     after enqueueing unless documented as synchronising.
+ *   - Return value: NCS_OK (0) on success, a positive status for a normal
+ *     outcome that is not success (NCS_NOT_CONVERGED), a negative NCS_ERR_* on
+ *     failure.  No C++ exception crosses this boundary.
+ *   - One plan is used by one host thread at a time.
+ */
+#ifndef NCS_H_
+#define NCS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NCS_OK                 0
+#define NCS_NOT_CONVERGED      1   /* solve stopped at max_iter above tolerance */
+#define NCS_ERR_BADARG        -1   /* null pointer, bad size or parameter */
+#define NCS_ERR_UNSUPPORTED   -2   /* e.g. N not of the form 2^a 3^b, N > 4096 */
+#define NCS_ERR_CUDA          -3   /* a CUDA runtime call failed */
+#define NCS_ERR_NOMEM         -4   /* device allocation failed */
+#define NCS_ERR_DIVERGED      -5   /* objective became NaN/Inf */
+#define NCS_ERR_TIMEOUT       -6   /* a bounded device wait ran out */
+
+/* Parallel-beam geometry (Sec. 2, eq. (radon-def)). */
+typedef struct {
+    int n_angles;          /* number of projection angles, >= 1 */
+    int n_det;             /* detector bins per angle, >= 1 */
+    double det_spacing;    /* bin pitch in pixel units, >= 1 (0 -> 1) */
+    double det_offset;     /* shift of the bin centres, pixel units */
+    const double* angles;  /* host array of n_angles radians, or NULL for theta_a = a*pi/n_angles */
+} ncs_geometry;
+
+typedef enum { NCS_DATA_L2 = 0, NCS_DATA_KL = 1 } ncs_data_term;
+typedef enum { NCS_TV_ANISO = 0, NCS_TV_ISO = 1 } ncs_tv_kind;
+typedef enum { NCS_FP32 = 0, NCS_BF16_STORE = 1 } ncs_precision;
+
+/* Solver options.  Fill with ncs_options_default() and change what you need. */
+typedef struct {
+    double beta;           /* TV scaling beta of Sec. 4.1 (default alpha) */
+    double gamma;          /* gamma of M = gamma I + alpha C (default 0) */
+    double h_dc;           /* DC entry of H_R (eq. (circ_R)); NaN -> ||K 1||^2 / ||1||^2 */
+    double c_r;            /* C_R of eq. (circ_R); NaN -> n_angles * N / pi */
+    double kappa;          /* weight of the nonnegativity row (PET, nonneg = 1); default 1 */
+    ncs_data_term data;    /* NCS_DATA_L2: 1/2||Kx - b||^2; NCS_DATA_KL: Poisson likelihood (Sec. 4.2) */
+    ncs_tv_kind tv;        /* anisotropic box (Sec. 4.1) or isotropic per-pixel ball */
+    int nonneg;            /* 1: add the row kappa I with delta_{R+} (Sec. 4.2 remark); KL only */
+    ncs_precision prec;    /* storage precision of the iteration state */
+    double a3_margin;      /* M is rescaled to rho(M^{-1} alpha A^T A) = 1/(1+margin); default 1e-2; <0 disables */
+    int power_max_iter;    /* power iteration cap (default 500) */
+    double power_tol;      /* power iteration relative-change stop (default 1e-9) */
+    uint64_t power_seed;   /* seed of the SplitMix64 start vector (default 0) */
+    int check_every;       /* objective evaluated every T iterations in the solves (default 10) */
+    void* cuda_stream;     /* cudaStream_t to run on, or NULL for a plan-owned stream */
+} ncs_options;
+
+/* Result of ncs_solve / pdhg_solve. */
+typedef struct {
+    int iters;             /* iterations run */
+    int status;            /* NCS_OK, NCS_NOT_CONVERGED or an error */
+    double time_ms;        /* wall time of the iteration loop on the plan's stream */
+    double f;              /* FP64 objective at the returned x */
+    double gap;            /* (f - f_star)/|f_star|, or the last relative change of f if f_star is NaN */
+    double rho;            /* rho(M^{-1} alpha A^T A) before the rescale (NCS) or gamma_P (PDHG) */
+} ncs_report;
+
+typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and solver state */
+
+/* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
+ * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
+ * check_every 10, NULL stream. */
+void ncs_options_default(ncs_options* opt);
+
+/* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).
+ * Computes the per-angle Joseph coefficients and the eigenvalues of M (eqs.
+ * (circ_R), (circ_D)) on the host in FP64, then on the GPU the power-iteration
+ * bound rho = lambda_max(M^{-1} alpha A^T A) of assumption (A3) (Sec. 3) with FP64
+ * reductions, and rescales M so that (A3) holds with the margin.  Synchronises.
+ * lambda > 0 is the TV weight, alpha > 0 the dual step.
+ * Errors: NCS_ERR_BADARG, NCS_ERR_UNSUPPORTED, NCS_ERR_NOMEM, NCS_ERR_CUDA. */
+int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha,
+                    const ncs_options* opt, ncs_plan** out);
+
+/* Release the plan and everything it owns (NULL is a no-op). */
+void ncs_plan_destroy(ncs_plan* plan);
+
+/* Run n_iter >= 1 NCS iterations (eq. (NCS); explicit updates of Sec. 4.1 / 4.2) in
+ * place on the caller's state: x (N*N), u (n_angles*n_det), v (2*N*N), s (N*N, PET
+ * with nonneg only, else NULL); b is the measured sinogram (CT) or the counts
+ * (PET); bg is the PET background sinogram or NULL (CT: must be NULL).
+ * Asynchronous on the plan's stream. */
+int ncs_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
+             const float* b, const float* bg, int n_iter);
+
+/* Same as ncs_step for PDHG (eq. (PDHG)): x+ = x - gamma_P^{-1} A^T u with
+ * gamma_P = alpha lambda_max(A^T A)(1 + margin) (computed on first use). */
+int pdhg_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
+              const float* b, const float* bg, int n_iter);
+
+/* Solve with NCS from x (in: x^0, out: the result; device) and zero duals, until
+ * (f - f_star)/|f_star| <= tol (f_star finite) or the relative change of f over
+ * one check interval <= tol (f_star NaN), or max_iter iterations.  The FP64
+ * objective is evaluated every check_every iterations on the GPU; the loop runs
+ * as CUDA graphs of check_every iterations.  Synchronises.  report may be NULL.
+ * Returns NCS_OK, NCS_NOT_CONVERGED or an error. */
+int ncs_solve(ncs_plan* plan, const float* b, const float* bg, float* x,
+              double tol, int max_iter, double f_star, ncs_report* report);
+
+/* Same as ncs_solve with PDHG updates. */
+int pdhg_solve(ncs_plan* plan, const float* b, const float* bg, float* x,
+               double tol, int max_iter, double f_star, ncs_report* report);
+
+/* Host-side results of the setup power iterations: lambda_max(A^T A) (computed
+ * now if not yet) and rho = lambda_max(M^{-1} alpha A^T A) before the rescale.
+ * Synchronises. */
+int ncs_power_bound(ncs_plan* plan, double* lambda_max_AtA, double* rho_M);
+
+/* ---- Operators of the plan (device pointers, asynchronous) ---- */
+
+/* y = K x, the Joseph forward projection (N*N -> n_angles*n_det). */
+int ncs_apply_K(ncs_plan* plan, const float* x, float* y);
+
+/* x = K^T y, computed as a per-pixel gather with the same FP32 weights as K. */
+int ncs_apply_KT(ncs_plan* plan, const float* y, float* x);
+
+/* v = D x (2*N*N layout above) and x = D^T v. */
+int ncs_apply_D(ncs_plan* plan, const float* x, float* v);
+int ncs_apply_DT(ncs_plan* plan, const float* v, float* x);
+
+/* out = M^{-1} r = F^{-1} diag(mu)^{-1} F r with the plan's (rescaled) mu (Sec. 2). */
+int ncs_apply_Minv(ncs_plan* plan, const float* r, float* out);
+
+/* FP64 objective at x: 1/2||Kx - b||^2 + lambda TV(x) (L2), or
+ * KL(b, K x+ + bg) + lambda TV(x+) with x+ = max(x, 0) (KL).  Synchronises;
+ * writes the host double *f. */
+int ncs_objective(ncs_plan* plan, const float* x, const float* b, const float* bg, double* f);
+
+/* Copy the plan's eigenvalue table of M (after the (A3) rescale), N x N row-major
+ * in FP64, mu[p*N + q] for frequency p along rows and q along columns, to the
+ * host array mu_host.  Synchronises. */
+int ncs_get_mu(ncs_plan* plan, double* mu_host);
+
+/* Plan sizes: N, n_angles, n_det. */
+int ncs_plan_sizes(const ncs_plan* plan, int* N, int* n_angles, int* n_det);
+
+/* Human-readable name of a status code (static string). */
+const char* ncs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NCS_H_ */

@@ -1,0 +1,301 @@
+"""ctypes binding of the C ABI in include/ncs.h (argument marshalling only).
+
+Every numerical step runs in libncs.so; this module only converts torch CUDA
+tensors to device pointers, fills the C structs and maps status codes to
+exceptions.  There is no CPU fallback: if the library is missing the import of
+the plan class fails with a clear error.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libncs.so")
+
+NCS_OK = 0
+NCS_NOT_CONVERGED = 1
+NCS_ERR_BADARG = -1
+NCS_ERR_UNSUPPORTED = -2
+NCS_ERR_CUDA = -3
+NCS_ERR_NOMEM = -4
+NCS_ERR_DIVERGED = -5
+NCS_ERR_TIMEOUT = -6
+
+
+class NCSError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (status %d)" % (what, status_string(code), code))
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_angles", ctypes.c_int), ("n_det", ctypes.c_int),
+                ("det_spacing", ctypes.c_double), ("det_offset", ctypes.c_double),
+                ("angles", ctypes.POINTER(ctypes.c_double))]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("h_dc", ctypes.c_double),
+                ("c_r", ctypes.c_double), ("kappa", ctypes.c_double),
+                ("data", ctypes.c_int), ("tv", ctypes.c_int), ("nonneg", ctypes.c_int), ("prec", ctypes.c_int),
+                ("a3_margin", ctypes.c_double), ("power_max_iter", ctypes.c_int), ("power_tol", ctypes.c_double),
+                ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("time_ms", ctypes.c_double),
+                ("f", ctypes.c_double), ("gap", ctypes.c_double), ("rho", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+SIGNATURES = [
+    ("ncs_options_default", None, [ctypes.POINTER(Options)]),
+    ("ncs_plan_create", _I, [ctypes.POINTER(Geometry), _I, _I, _D, _D, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    ("ncs_plan_destroy", None, [_P]),
+    ("ncs_step", _I, [_P, _P, _P, _P, _P, _P, _P, _I]),
+    ("pdhg_step", _I, [_P, _P, _P, _P, _P, _P, _P, _I]),
+    ("ncs_solve", _I, [_P, _P, _P, _P, _D, _I, _D, ctypes.POINTER(Report)]),
+    ("pdhg_solve", _I, [_P, _P, _P, _P, _D, _I, _D, ctypes.POINTER(Report)]),
+    ("ncs_power_bound", _I, [_P, _DP, _DP]),
+    ("ncs_apply_K", _I, [_P, _P, _P]),
+    ("ncs_apply_KT", _I, [_P, _P, _P]),
+    ("ncs_apply_D", _I, [_P, _P, _P]),
+    ("ncs_apply_DT", _I, [_P, _P, _P]),
+    ("ncs_apply_Minv", _I, [_P, _P, _P]),
+    ("ncs_objective", _I, [_P, _P, _P, _P, _DP]),
+    ("ncs_get_mu", _I, [_P, _DP]),
+    ("ncs_plan_sizes", _I, [_P, _IP, _IP, _IP]),
+    ("ncs_status_string", ctypes.c_char_p, [_I]),
+]
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libncs.so (built in-tree by __graft_entry__.build() or
+    paper_1810_13100_gb300._build.build()).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("libncs.so is not built (%s); run `python -c 'import __graft_entry__ as g; g.build()'`"
+                           % path)
+    L = ctypes.CDLL(path)
+    for name, res, args in SIGNATURES:
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return load_library().ncs_status_string(code).decode()
+    except Exception:  # library missing
+        return "status %d" % code
+
+
+def _check(code, what):
+    if code < 0:
+        raise NCSError(code, what)
+    return code
+
+
+def _ptr(t, name, numel=None, allow_none=False):
+    """Device pointer of a contiguous float32 CUDA tensor (None -> NULL)."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError("%s is required" % name)
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous float32 tensor" % name)
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def default_options() -> Options:
+    o = Options()
+    load_library().ncs_options_default(ctypes.byref(o))
+    return o
+
+
+class Plan:
+    """An NCS plan: geometry, image side N, TV weight lam, dual step alpha and the
+    options of include/ncs.h.  Work runs on `stream` (a torch.cuda.Stream, a raw
+    cudaStream_t int, or None for a side stream ordered with torch's current stream)."""
+
+    def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
+                 kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
+                 power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
+                 det_spacing=1.0, det_offset=0.0, angles=None, stream=None):
+        import torch
+        L = load_library()
+        self._L = L
+        g = Geometry()
+        g.n_angles, g.n_det = int(n_angles), int(n_det)
+        g.det_spacing, g.det_offset = float(det_spacing), float(det_offset)
+        self._angles = None
+        if angles is not None:
+            arr = (ctypes.c_double * len(angles))(*[float(a) for a in angles])
+            self._angles = arr
+            g.angles = ctypes.cast(arr, _DP)
+        o = default_options()
+        nan = float("nan")
+        o.beta = nan if beta is None else float(beta)
+        o.gamma = float(gamma)
+        o.h_dc = nan if h_dc is None else float(h_dc)
+        o.c_r = nan if c_r is None else float(c_r)
+        o.kappa = float(kappa)
+        o.data = {"l2": 0, "kl": 1}[data]
+        o.tv = {"aniso": 0, "iso": 1}[tv]
+        o.nonneg = 1 if nonneg else 0
+        o.prec = {"fp32": 0, "bf16": 1}[precision]
+        o.a3_margin = float(a3_margin)
+        o.power_max_iter = int(power_max_iter)
+        o.power_tol = float(power_tol)
+        o.power_seed = int(power_seed)
+        o.check_every = int(check_every)
+        # With no stream given, the plan runs on a side stream that is ordered
+        # after torch's current stream on entry to every call and before it on
+        # exit, so results are visible to torch without extra synchronisation.
+        self._auto = stream is None
+        if stream is None:
+            stream = torch.cuda.Stream()
+        o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(L.ncs_plan_create(ctypes.byref(g), int(N), int(N), float(lam), float(alpha), ctypes.byref(o),
+                                 ctypes.byref(h)), "ncs_plan_create")
+        self._h = h
+        self.N, self.n_angles, self.n_det = int(N), int(n_angles), int(n_det)
+        self.lam, self.alpha = float(lam), float(alpha)
+        self.beta = float(alpha if beta is None else beta)
+        self.data, self.tv, self.nonneg = data, tv, bool(nonneg)
+
+    def _enter(self):
+        if self._auto:
+            import torch
+            self.stream.wait_stream(torch.cuda.current_stream())
+
+    def _leave(self):
+        if self._auto:
+            import torch
+            torch.cuda.current_stream().wait_stream(self.stream)
+
+    def _call(self, what, fn, *args):
+        self._enter()
+        try:
+            return _check(fn(*args), what)
+        finally:
+            self._leave()
+
+    # -------------------------------------------------------------- sizes
+    @property
+    def n(self):
+        return self.N * self.N
+
+    @property
+    def m(self):
+        return self.n_angles * self.n_det
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ncs_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- iterations
+    def _state_ptrs(self, x, u, v, s, b, bg):
+        return (_ptr(x, "x", self.n), _ptr(u, "u", self.m), _ptr(v, "v", 2 * self.n),
+                _ptr(s, "s", self.n, allow_none=True), _ptr(b, "b", self.m), _ptr(bg, "bg", self.m, allow_none=True))
+
+    def step(self, x, u, v, s, b, bg=None, n_iter=1):
+        """n_iter NCS iterations in place on (x, u, v, s)."""
+        self._call("ncs_step", self._L.ncs_step, self._h, *self._state_ptrs(x, u, v, s, b, bg), int(n_iter))
+
+    def pdhg_step(self, x, u, v, s, b, bg=None, n_iter=1):
+        self._call("pdhg_step", self._L.pdhg_step, self._h, *self._state_ptrs(x, u, v, s, b, bg), int(n_iter))
+
+    def _solve(self, fn, what, b, x, tol, max_iter, f_star, bg):
+        rep = Report()
+        self._call(what, fn, self._h, _ptr(b, "b", self.m), _ptr(bg, "bg", self.m, allow_none=True),
+                   _ptr(x, "x", self.n), float(tol), int(max_iter), float("nan") if f_star is None else float(f_star),
+                   ctypes.byref(rep))
+        return rep.as_dict()
+
+    def solve(self, b, x, tol=1e-4, max_iter=2000, f_star=None, bg=None):
+        """NCS from x (in/out) with zero duals to the tolerance; returns the report dict."""
+        return self._solve(self._L.ncs_solve, "ncs_solve", b, x, tol, max_iter, f_star, bg)
+
+    def pdhg_solve(self, b, x, tol=1e-4, max_iter=2000, f_star=None, bg=None):
+        return self._solve(self._L.pdhg_solve, "pdhg_solve", b, x, tol, max_iter, f_star, bg)
+
+    def power_bound(self):
+        lm, rho = ctypes.c_double(), ctypes.c_double()
+        self._call("ncs_power_bound", self._L.ncs_power_bound, self._h, ctypes.byref(lm), ctypes.byref(rho))
+        return lm.value, rho.value
+
+    # -------------------------------------------------------------- operators
+    def _out(self, out, numel, like):
+        import torch
+        if out is None:
+            out = torch.empty(numel, dtype=torch.float32, device=like.device)
+        return out
+
+    def apply_K(self, x, y=None):
+        y = self._out(y, self.m, x)
+        self._call("ncs_apply_K", self._L.ncs_apply_K, self._h, _ptr(x, "x", self.n), _ptr(y, "y", self.m))
+        return y
+
+    def apply_KT(self, y, x=None):
+        x = self._out(x, self.n, y)
+        self._call("ncs_apply_KT", self._L.ncs_apply_KT, self._h, _ptr(y, "y", self.m), _ptr(x, "x", self.n))
+        return x
+
+    def apply_D(self, x, v=None):
+        v = self._out(v, 2 * self.n, x)
+        self._call("ncs_apply_D", self._L.ncs_apply_D, self._h, _ptr(x, "x", self.n), _ptr(v, "v", 2 * self.n))
+        return v
+
+    def apply_DT(self, v, x=None):
+        x = self._out(x, self.n, v)
+        self._call("ncs_apply_DT", self._L.ncs_apply_DT, self._h, _ptr(v, "v", 2 * self.n), _ptr(x, "x", self.n))
+        return x
+
+    def apply_Minv(self, r, out=None):
+        out = self._out(out, self.n, r)
+        self._call("ncs_apply_Minv", self._L.ncs_apply_Minv, self._h, _ptr(r, "r", self.n), _ptr(out, "out", self.n))
+        return out
+
+    def objective(self, x, b, bg=None):
+        f = ctypes.c_double()
+        self._call("ncs_objective", self._L.ncs_objective, self._h, _ptr(x, "x", self.n), _ptr(b, "b", self.m),
+                   _ptr(bg, "bg", self.m, allow_none=True), ctypes.byref(f))
+        return f.value
+
+    def mu(self):
+        import numpy as np
+        out = np.empty(self.n, dtype=np.float64)
+        _check(self._L.ncs_get_mu(self._h, out.ctypes.data_as(_DP)), "ncs_get_mu")
+        return out.reshape(self.N, self.N)

@@ -1,0 +1,844 @@
+// Host runtime and C ABI of the NCS library (declarations in include/ncs.h).
+//
+// A plan owns: per-angle Joseph coefficients (FP64 on the host, rounded once),
+// the Stockham twiddle table and radix schedule, the eigenvalue table of M
+// (eqs. (circ_R), (circ_D)) after the (A3) rescale, the iteration workspace
+// (xbar, xbar^T, r, half spectrum), the solver state used by ncs_solve /
+// pdhg_solve, and cached CUDA graphs of check_every iterations.
+#include "../../include/ncs.h"
+#include "ncs_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <new>
+#include <vector>
+
+using namespace ncs;
+
+namespace {
+
+constexpr int kMaxPartials = 16384;
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int kind = -1;
+    const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+    int T = 0;
+};
+
+}  // namespace
+
+struct ncs_plan {
+    int dev = 0;
+    int N = 0, na = 0, nd = 0;
+    double lam = 0, alpha = 0, beta = 0, gamma = 0, kappa = 0, c_r = 0, h_dc = 0;
+    bool kl = false, iso = false, nonneg = false;
+    ncs_options opt{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    std::vector<AngleParam> h_ap;
+    AngleParam* d_ap = nullptr;
+    float2* d_tw = nullptr;
+    RadixPlan rp{};
+    std::vector<double> mu;          // eigenvalues of M, N x N, [p][q]
+    float* d_invmu = nullptr;        // 1/(N^2 mu), [q][p], q = 0..N/2
+    float* d_mu = nullptr;           // mu/N^2 (power iteration start only)
+    float *d_xbar = nullptr, *d_xbarT = nullptr, *d_r = nullptr, *d_tmp = nullptr, *d_tmpT = nullptr;
+    float2* d_spec = nullptr;
+    double *d_part0 = nullptr, *d_part1 = nullptr, *d_scal = nullptr, *h_pin = nullptr;
+    float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
+    double rho = std::numeric_limits<double>::quiet_NaN();
+    double lmax = std::numeric_limits<double>::quiet_NaN();
+    float gamma_p = 0.0f;
+    GraphCache graph;
+};
+
+namespace {
+
+#define CK(expr)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (expr);                                     \
+        if (e_ != cudaSuccess) {                                     \
+            fprintf(stderr, "ncs: %s failed: %s (%s:%d)\n", #expr,   \
+                    cudaGetErrorString(e_), __FILE__, __LINE__);     \
+            return NCS_ERR_CUDA;                                     \
+        }                                                            \
+    } while (0)
+
+#define CKS(expr)                         \
+    do {                                  \
+        int s_ = (expr);                  \
+        if (s_ < 0) return s_;            \
+    } while (0)
+
+size_t NN(const ncs_plan* p) { return (size_t)p->N * p->N; }
+size_t MM(const ncs_plan* p) { return (size_t)p->na * p->nd; }
+
+bool factor_radices(int N, RadixPlan* rp)
+{
+    rp->n = 0;
+    int n = N;
+    while (n % 8 == 0 && n > 1) { rp->r[rp->n++] = 8; n /= 8; if (rp->n >= 12) return false; }
+    while (n % 4 == 0 && n > 1) { rp->r[rp->n++] = 4; n /= 4; if (rp->n >= 12) return false; }
+    while (n % 2 == 0 && n > 1) { rp->r[rp->n++] = 2; n /= 2; if (rp->n >= 12) return false; }
+    while (n % 3 == 0 && n > 1) { rp->r[rp->n++] = 3; n /= 3; if (rp->n >= 12) return false; }
+    return n == 1;
+}
+
+template <class T>
+int dalloc(T** p, size_t count)
+{
+    if (count == 0) count = 1;
+    if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return NCS_ERR_NOMEM;
+    }
+    return NCS_OK;
+}
+
+// ---------------------------------------------------------------- enqueue helpers
+
+int enq_transpose(ncs_plan* p, const float* x, float* xT)
+{
+    TdArgs a{};
+    a.x = x;
+    a.xT = xT;
+    a.N = p->N;
+    CK(launch_td(TD_TRANSPOSE, a, p->st));
+    return NCS_OK;
+}
+
+int enq_K(ncs_plan* p, const float* x, const float* xT, float* y)
+{
+    FwdArgs f{};
+    f.img = x;
+    f.imgT = xT;
+    f.ap = p->d_ap;
+    f.N = p->N;
+    f.n_ang = p->na;
+    f.n_det = p->nd;
+    f.y = y;
+    CK(launch_fwd(FWD_PLAIN, f, p->st));
+    return NCS_OK;
+}
+
+int enq_gather(ncs_plan* p, int mode, const float* u, const float* v, float dscale, const float* s, float kappa,
+               float* r, float* x, float* xbar, float inv_gamma, int n_ang)
+{
+    GatherArgs g{};
+    g.u = u;
+    g.ap = p->d_ap;
+    g.N = p->N;
+    g.n_ang = n_ang;
+    g.n_det = p->nd;
+    g.v = v;
+    g.dscale = dscale;
+    g.s = s;
+    g.kappa = kappa;
+    g.r = r;
+    g.x = x;
+    g.xbar = xbar;
+    g.inv_gamma = inv_gamma;
+    CK(launch_gather(mode, g, p->st));
+    return NCS_OK;
+}
+
+// out = M^{-1} r (mode 1) or x <- x - M^{-1} r, xbar = 2 x+ - x (mode 0)
+int enq_solve(ncs_plan* p, const float* r, const float* table, int mode, float* x, float* xbar, float* out)
+{
+    CK(launch_rows_fwd(r, p->d_spec, p->d_tw, p->rp, p->N, p->st));
+    CK(launch_cols_solve(p->d_spec, table, p->d_tw, p->rp, p->N, p->st));
+    CK(launch_rows_inv(p->d_spec, p->d_tw, p->rp, p->N, mode, x, xbar, out, p->st));
+    return NCS_OK;
+}
+
+// v+, s+ prox and xbar^T
+int enq_td_prox(ncs_plan* p, float* v, float* s)
+{
+    TdArgs a{};
+    a.x = p->d_xbar;
+    a.xT = p->d_xbarT;
+    a.v = v;
+    a.s = p->nonneg ? s : nullptr;
+    a.N = p->N;
+    a.beta = (float)p->beta;
+    a.rad = (float)(p->lam * p->alpha / p->beta);
+    a.ak = (float)(p->alpha * p->kappa);
+    a.iso = p->iso ? 1 : 0;
+    CK(launch_td(TD_PROX, a, p->st));
+    return NCS_OK;
+}
+
+int enq_fwd_prox(ncs_plan* p, float* u, const float* b, const float* bg)
+{
+    FwdArgs f{};
+    f.img = p->d_xbar;
+    f.imgT = p->d_xbarT;
+    f.ap = p->d_ap;
+    f.N = p->N;
+    f.n_ang = p->na;
+    f.n_det = p->nd;
+    f.y = u;
+    f.b = b;
+    f.bg = bg;
+    f.alpha = (float)p->alpha;
+    f.inv1pa = (float)(1.0 / (1.0 + p->alpha));
+    CK(launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
+    return NCS_OK;
+}
+
+// One NCS iteration (eq. (NCS), Sec. 4.1 / 4.2).
+int enq_ncs_iter(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg)
+{
+    const float* sv = p->nonneg ? s : nullptr;
+    // r = K^T u + (beta/alpha) D^T v + kappa s
+    CKS(enq_gather(p, GATHER_R, u, v, (float)(p->beta / p->alpha), sv, (float)p->kappa, p->d_r, nullptr,
+                   nullptr, 0.f, p->na));
+    // x+ = x - M^+ r ; xbar = 2 x+ - x
+    CKS(enq_solve(p, p->d_r, p->d_invmu, 0, x, p->d_xbar, nullptr));
+    // v+ = Pi(v + beta D xbar), s+ = min(0, s + alpha kappa xbar), xbar^T
+    CKS(enq_td_prox(p, v, s));
+    // u+ = prox_{alpha g1*}(u + alpha (K xbar - b))
+    CKS(enq_fwd_prox(p, u, b, bg));
+    return NCS_OK;
+}
+
+// One PDHG iteration (eq. (PDHG)).
+int enq_pdhg_iter(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg)
+{
+    const float* sv = p->nonneg ? s : nullptr;
+    CKS(enq_gather(p, GATHER_PDHG, u, v, (float)(p->beta / p->alpha), sv, (float)p->kappa, nullptr, x,
+                   p->d_xbar, 1.0f / p->gamma_p, p->na));
+    CKS(enq_td_prox(p, v, s));
+    CKS(enq_fwd_prox(p, u, b, bg));
+    return NCS_OK;
+}
+
+// FP64 objective at x into d_scal[slot].
+int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, int slot)
+{
+    TdArgs a{};
+    a.x = x;
+    a.xT = p->d_tmpT;
+    a.xc = p->kl ? p->d_tmp : nullptr;
+    a.clamp = p->kl ? 1 : 0;
+    a.N = p->N;
+    a.iso = p->iso ? 1 : 0;
+    a.partials = p->d_part0;
+    CK(launch_td(TD_OBJ, a, p->st));
+    FwdArgs f{};
+    f.img = p->kl ? p->d_tmp : x;
+    f.imgT = p->d_tmpT;
+    f.ap = p->d_ap;
+    f.N = p->N;
+    f.n_ang = p->na;
+    f.n_det = p->nd;
+    f.b = b;
+    f.bg = bg;
+    f.partials = p->d_part1;
+    CK(launch_fwd(p->kl ? FWD_RESID_KL : FWD_RESID_L2, f, p->st));
+    CK(launch_finalize(p->d_part1, fwd_num_blocks(p->nd, p->na), p->kl ? 1.0 : 0.5, p->d_part0,
+                       td_num_blocks(p->N), p->lam, p->d_scal + slot, p->st));
+    return NCS_OK;
+}
+
+int enq_dot(ncs_plan* p, const float* a, const float* b, size_t n, int slot)
+{
+    CK(launch_dot_partials(a, b, n, p->d_part0, 1024, p->st));
+    CK(launch_finalize(p->d_part0, 1024, 1.0, nullptr, 0, 0.0, p->d_scal + slot, p->st));
+    return NCS_OK;
+}
+
+int read_scalars(ncs_plan* p, int count)
+{
+    CK(cudaMemcpyAsync(p->h_pin, p->d_scal, count * sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return NCS_OK;
+}
+
+// w = A^T A x (x, xT: scratch buffers provided by the caller)
+int enq_AtA(ncs_plan* p, const float* x, float* xT, float* yk, float* vb, float* sb, float* w)
+{
+    TdArgs a{};
+    a.x = x;
+    a.xT = xT;
+    a.v = vb;
+    a.s = p->nonneg ? sb : nullptr;
+    a.N = p->N;
+    a.beta = (float)(p->beta / p->alpha);
+    a.ak = (float)p->kappa;
+    CK(launch_td(TD_APPLY, a, p->st));
+    CKS(enq_K(p, x, xT, yk));
+    CKS(enq_gather(p, GATHER_R, yk, vb, (float)(p->beta / p->alpha), p->nonneg ? sb : nullptr, (float)p->kappa,
+                   w, nullptr, nullptr, 0.f, p->na));
+    return NCS_OK;
+}
+
+struct PowerBufs {
+    float *x = nullptr, *xT = nullptr, *w = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *s = nullptr;
+    ~PowerBufs()
+    {
+        cudaFree(x); cudaFree(xT); cudaFree(w); cudaFree(y); cudaFree(u); cudaFree(v); cudaFree(s);
+    }
+};
+
+int alloc_power(ncs_plan* p, PowerBufs& B)
+{
+    CKS(dalloc(&B.x, NN(p)));
+    CKS(dalloc(&B.xT, NN(p)));
+    CKS(dalloc(&B.w, NN(p)));
+    CKS(dalloc(&B.y, NN(p)));
+    CKS(dalloc(&B.u, MM(p)));
+    CKS(dalloc(&B.v, 2 * NN(p)));
+    CKS(dalloc(&B.s, NN(p)));
+    return NCS_OK;
+}
+
+// rho = lambda_max(M^{-1} alpha A^T A): x <- M^{-1} alpha A^T A x normalised; Rayleigh
+// quotient <x, alpha A^T A x> / <x, M x> (M inner product).  <x, M x> of the
+// next iterate comes for free: M (y/|y|) = w/|y|.
+int power_rho(ncs_plan* p, double* rho_out)
+{
+    PowerBufs B;
+    CKS(alloc_power(p, B));
+    const size_t n = NN(p);
+    CK(launch_splitmix(B.x, n, p->opt.power_seed, p->st));
+    CKS(enq_dot(p, B.x, B.x, n, 0));
+    CK(launch_scale_by_rsqrt(B.x, B.x, n, p->d_scal + 0, p->st));
+    // <x0, M x0> with one application of M
+    CKS(enq_solve(p, B.x, p->d_mu, 1, nullptr, nullptr, B.y));
+    CKS(enq_dot(p, B.x, B.y, n, 3));
+    CKS(read_scalars(p, 4));
+    double xMx = p->h_pin[3];
+    double rho = 0.0, rho_old = std::numeric_limits<double>::quiet_NaN();
+    for (int it = 1; it <= p->opt.power_max_iter; ++it) {
+        CKS(enq_AtA(p, B.x, B.xT, B.u, B.v, B.s, B.w));
+        CK(launch_scale(B.w, n, (float)p->alpha, p->st));
+        CKS(enq_dot(p, B.x, B.w, n, 0));
+        CKS(enq_solve(p, B.w, p->d_invmu, 1, nullptr, nullptr, B.y));
+        CKS(enq_dot(p, B.y, B.w, n, 1));
+        CKS(enq_dot(p, B.y, B.y, n, 2));
+        CK(launch_scale_by_rsqrt(B.y, B.x, n, p->d_scal + 2, p->st));
+        CKS(read_scalars(p, 3));
+        rho = p->h_pin[0] / xMx;
+        xMx = p->h_pin[1] / p->h_pin[2];
+        if (!std::isfinite(rho)) return NCS_ERR_DIVERGED;
+        if (it > 1 && std::fabs(rho - rho_old) <= p->opt.power_tol * std::fabs(rho)) break;
+        rho_old = rho;
+    }
+    *rho_out = rho;
+    return NCS_OK;
+}
+
+// lambda_max(A^T A) with the Rayleigh quotient <x, A^T A x>/<x, x>.
+int power_lmax(ncs_plan* p, double* out)
+{
+    PowerBufs B;
+    CKS(alloc_power(p, B));
+    const size_t n = NN(p);
+    CK(launch_splitmix(B.x, n, p->opt.power_seed, p->st));
+    CKS(enq_dot(p, B.x, B.x, n, 0));
+    CK(launch_scale_by_rsqrt(B.x, B.x, n, p->d_scal + 0, p->st));
+    double lm = 0.0, lm_old = 0.0;
+    for (int it = 1; it <= p->opt.power_max_iter; ++it) {
+        CKS(enq_AtA(p, B.x, B.xT, B.u, B.v, B.s, B.w));
+        CKS(enq_dot(p, B.x, B.w, n, 0));
+        CKS(enq_dot(p, B.x, B.x, n, 1));
+        CKS(enq_dot(p, B.w, B.w, n, 2));
+        CK(launch_scale_by_rsqrt(B.w, B.x, n, p->d_scal + 2, p->st));
+        CKS(read_scalars(p, 3));
+        lm = p->h_pin[0] / p->h_pin[1];
+        if (!std::isfinite(lm)) return NCS_ERR_DIVERGED;
+        if (it > 1 && std::fabs(lm - lm_old) <= p->opt.power_tol * std::fabs(lm)) break;
+        lm_old = lm;
+    }
+    *out = lm;
+    return NCS_OK;
+}
+
+int upload_mu(ncs_plan* p)
+{
+    const int N = p->N, H = N / 2;
+    std::vector<float> inv((size_t)(H + 1) * N), fwd((size_t)(H + 1) * N);
+    const double s = 1.0 / ((double)N * N);
+    for (int q = 0; q <= H; ++q)
+        for (int pp = 0; pp < N; ++pp) {
+            const double m = p->mu[(size_t)pp * N + q];
+            inv[(size_t)q * N + pp] = (float)(s / m);
+            fwd[(size_t)q * N + pp] = (float)(s * m);
+        }
+    CK(cudaMemcpyAsync(p->d_invmu, inv.data(), inv.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->d_mu, fwd.data(), fwd.size() * sizeof(float), cudaMemcpyHostToDevice, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return NCS_OK;
+}
+
+int ensure_state(ncs_plan* p)
+{
+    if (!p->d_u) CKS(dalloc(&p->d_u, MM(p)));
+    if (!p->d_v) CKS(dalloc(&p->d_v, 2 * NN(p)));
+    if (!p->d_s) CKS(dalloc(&p->d_s, NN(p)));
+    return NCS_OK;
+}
+
+int ensure_gamma_p(ncs_plan* p)
+{
+    if (!std::isfinite(p->lmax)) CKS(power_lmax(p, &p->lmax));
+    const double m = p->opt.a3_margin >= 0 ? p->opt.a3_margin : 0.0;
+    p->gamma_p = (float)(p->alpha * p->lmax * (1.0 + m));
+    return NCS_OK;
+}
+
+void free_plan(ncs_plan* p)
+{
+    if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
+    cudaFree(p->d_ap); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
+    cudaFree(p->d_xbar); cudaFree(p->d_xbarT); cudaFree(p->d_r); cudaFree(p->d_tmp); cudaFree(p->d_tmpT);
+    cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
+    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s);
+    if (p->h_pin) cudaFreeHost(p->h_pin);
+    if (p->own_stream && p->st) cudaStreamDestroy(p->st);
+}
+
+int build_plan(ncs_plan* p, const ncs_geometry* geom)
+{
+    const int N = p->N, na = p->na, nd = p->nd;
+    CK(cudaGetDevice(&p->dev));
+    if (p->opt.cuda_stream) {
+        p->st = (cudaStream_t)p->opt.cuda_stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking));
+        p->own_stream = true;
+    }
+    // per-angle Joseph coefficients in FP64, rounded once
+    const double ds = (geom->det_spacing > 0.0) ? geom->det_spacing : 1.0;
+    const double cN = 0.5 * (N - 1);
+    const double s0 = -0.5 * (nd - 1) * ds + geom->det_offset;
+    p->h_ap.resize(na);
+    for (int a = 0; a < na; ++a) {
+        double th, c, sn;
+        int row;
+        if (geom->angles) {
+            th = geom->angles[a];
+            c = std::cos(th);
+            sn = std::sin(th);
+            row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
+        } else {
+            th = a * M_PI / na;
+            c = std::cos(th);
+            sn = std::sin(th);
+            row = (4 * a <= na || 4 * a >= 3 * na) ? 1 : 0;   // exact test; ties step over rows
+        }
+        double A, B, C, W, invA;
+        if (row) {
+            // column index where ray t crosses row j: u = (s_t - v_j sin)/cos, f = u + cN
+            A = ds / c;
+            B = sn / c;
+            C = (s0 - cN * sn) / c + cN;
+            W = 1.0 / std::fabs(c);
+            invA = c / ds;
+        } else {
+            // row index where ray t crosses column i: v = (s_t - u_i cos)/sin, f = cN - v
+            A = -ds / sn;
+            B = c / sn;
+            C = cN - (s0 + cN * c) / sn;
+            W = 1.0 / std::fabs(sn);
+            invA = -sn / ds;
+        }
+        AngleParam& q = p->h_ap[a];
+        // X = X_hi + X_lo, X_hi a multiple of 2^-10 (see AngleParam)
+        auto hi = [](double X) { return std::nearbyint(X * 1024.0) / 1024.0; };
+        q.Ahi = (float)hi(A);
+        q.Alo = (float)(A - hi(A));
+        q.Bhi = (float)hi(B);
+        q.Blo = (float)(B - hi(B));
+        q.Chi = (float)hi(C);
+        q.Clo = (float)(C - hi(C));
+        q.W = (float)W;
+        q.invA = (float)invA;
+        // H = A_hi t + B_hi q + C_hi is exact only while every partial sum stays below 2^14
+        if (std::fabs(hi(A)) * (nd - 1) + std::fabs(hi(B)) * (N - 1) + std::fabs(hi(C)) >= 16384.0)
+            return NCS_ERR_UNSUPPORTED;
+        q.row = row;
+        q.pad0 = q.pad1 = q.pad2 = 0;
+    }
+    CKS(dalloc(&p->d_ap, na));
+    CK(cudaMemcpyAsync(p->d_ap, p->h_ap.data(), na * sizeof(AngleParam), cudaMemcpyHostToDevice, p->st));
+    // twiddles exp(-2 pi i m / N) in FP64, rounded once
+    std::vector<float2> tw(N);
+    for (int m = 0; m < N; ++m) {
+        const double ang = -2.0 * M_PI * (double)m / (double)N;
+        tw[m] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+    CKS(dalloc(&p->d_tw, N));
+    CK(cudaMemcpyAsync(p->d_tw, tw.data(), N * sizeof(float2), cudaMemcpyHostToDevice, p->st));
+    const size_t n = NN(p), H = N / 2;
+    CKS(dalloc(&p->d_invmu, (H + 1) * N));
+    CKS(dalloc(&p->d_mu, (H + 1) * N));
+    CKS(dalloc(&p->d_xbar, n));
+    CKS(dalloc(&p->d_xbarT, n));
+    CKS(dalloc(&p->d_r, n));
+    CKS(dalloc(&p->d_tmp, n));
+    CKS(dalloc(&p->d_tmpT, n));
+    CKS(dalloc(&p->d_spec, (H + 1) * N));
+    CKS(dalloc(&p->d_part0, kMaxPartials));
+    CKS(dalloc(&p->d_part1, (size_t)fwd_num_blocks(nd, na)));
+    CKS(dalloc(&p->d_scal, 16));
+    if (cudaMallocHost((void**)&p->h_pin, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return NCS_ERR_NOMEM;
+    }
+    if (td_num_blocks(N) > kMaxPartials) return NCS_ERR_UNSUPPORTED;
+    // DC of H_R: ||K 1||^2 / ||1||^2 unless given
+    if (std::isnan(p->h_dc)) {
+        float* ones = p->d_tmp;
+        std::vector<float> h1(n, 1.0f);
+        CK(cudaMemcpyAsync(ones, h1.data(), n * sizeof(float), cudaMemcpyHostToDevice, p->st));
+        float* y = nullptr;
+        CKS(dalloc(&y, MM(p)));
+        int rc = enq_K(p, ones, ones, y);
+        if (rc == NCS_OK) rc = enq_dot(p, y, y, MM(p), 0);
+        if (rc == NCS_OK) rc = read_scalars(p, 1);
+        cudaFree(y);
+        if (rc != NCS_OK) return rc;
+        p->h_dc = p->h_pin[0] / (double)n;
+    }
+    if (std::isnan(p->c_r)) p->c_r = (double)na * N / M_PI;
+    // eigenvalues of M = gamma I + alpha C, C ~ A^T A (eqs. (circ_R), (circ_D))
+    p->mu.assign(n, 0.0);
+    const double b2a = p->beta * p->beta / p->alpha;
+    const double kap = p->nonneg ? p->alpha * p->kappa * p->kappa : 0.0;
+    for (int pp = 0; pp < N; ++pp) {
+        const double jp = std::min(pp, N - pp);
+        const double sp = std::sin(M_PI * pp / N);
+        for (int q = 0; q < N; ++q) {
+            const double kq = std::min(q, N - q);
+            const double sq = std::sin(M_PI * q / N);
+            const double hr = (pp == 0 && q == 0) ? p->h_dc : p->c_r / std::sqrt(jp * jp + kq * kq);
+            const double hd = 4.0 * (sp * sp + sq * sq);
+            p->mu[(size_t)pp * N + q] = p->gamma + p->alpha * hr + b2a * hd + kap;
+        }
+    }
+    for (double m : p->mu)
+        if (!(m > 0.0)) return NCS_ERR_BADARG;
+    CKS(upload_mu(p));
+    // (A3): rho = lambda_max(M^{-1} alpha A^T A); rescale M to rho = 1/(1+margin)
+    CKS(power_rho(p, &p->rho));
+    if (p->opt.a3_margin >= 0.0) {
+        const double f = p->rho * (1.0 + p->opt.a3_margin);
+        for (double& m : p->mu) m *= f;
+        CKS(upload_mu(p));
+    }
+    return NCS_OK;
+}
+
+int check_plan(const ncs_plan* p) { return p ? NCS_OK : NCS_ERR_BADARG; }
+
+int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* x, double tol, int max_iter,
+                 double f_star, ncs_report* rep)
+{
+    if (!b || !x || max_iter < 1 || !(tol >= 0.0)) return NCS_ERR_BADARG;
+    if (!p->kl && bg) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    CKS(ensure_state(p));
+    if (kind == 1) CKS(ensure_gamma_p(p));
+    CK(cudaMemsetAsync(p->d_u, 0, MM(p) * sizeof(float), p->st));
+    CK(cudaMemsetAsync(p->d_v, 0, 2 * NN(p) * sizeof(float), p->st));
+    CK(cudaMemsetAsync(p->d_s, 0, NN(p) * sizeof(float), p->st));
+    const int T = p->opt.check_every > 0 ? p->opt.check_every : 10;
+    auto enq_block = [&](int n_it) -> int {
+        for (int k = 0; k < n_it; ++k) {
+            if (kind == 0) CKS(enq_ncs_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
+            else CKS(enq_pdhg_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
+        }
+        CKS(enq_objective(p, x, b, bg, 0));
+        CK(cudaMemcpyAsync(p->h_pin, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+        return NCS_OK;
+    };
+    // CUDA graph of T iterations + objective, cached per (kind, pointers)
+    GraphCache& G = p->graph;
+    const void* key[4] = {b, bg, x, nullptr};
+    bool hit = G.exec && G.kind == kind && G.T == T && !memcmp(G.key, key, sizeof(key));
+    if (!hit) {
+        if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+        int rc = enq_block(T);
+        cudaError_t e = cudaStreamEndCapture(p->st, &graph);
+        if (rc != NCS_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
+        CK(e);
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CK(e);
+        G.kind = kind;
+        G.T = T;
+        memcpy(G.key, key, sizeof(key));
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, p->st));
+    int it = 0, status = NCS_NOT_CONVERGED;
+    double f = std::numeric_limits<double>::quiet_NaN(), f_prev = f, gap = f;
+    while (it < max_iter) {
+        const int n_it = std::min(T, max_iter - it);
+        if (n_it == T) CK(cudaGraphLaunch(G.exec, p->st));
+        else CKS(enq_block(n_it));
+        CK(cudaStreamSynchronize(p->st));
+        it += n_it;
+        f = p->h_pin[0];
+        if (!std::isfinite(f)) { status = NCS_ERR_DIVERGED; break; }
+        if (std::isfinite(f_star)) gap = (f - f_star) / std::fabs(f_star);
+        else gap = std::isfinite(f_prev) ? std::fabs(f - f_prev) / std::fabs(f) : gap;
+        if (std::isfinite(gap) && gap <= tol) { status = NCS_OK; break; }
+        f_prev = f;
+    }
+    CK(cudaEventRecord(e1, p->st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rep) {
+        rep->iters = it;
+        rep->status = status;
+        rep->time_ms = ms;
+        rep->f = f;
+        rep->gap = gap;
+        rep->rho = kind == 0 ? p->rho : (double)p->gamma_p;
+    }
+    return status;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+
+extern "C" {
+
+void ncs_options_default(ncs_options* o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    o->beta = nan;
+    o->gamma = 0.0;
+    o->h_dc = nan;
+    o->c_r = nan;
+    o->kappa = 1.0;
+    o->data = NCS_DATA_L2;
+    o->tv = NCS_TV_ANISO;
+    o->nonneg = 0;
+    o->prec = NCS_FP32;
+    o->a3_margin = 1e-2;
+    o->power_max_iter = 500;
+    o->power_tol = 1e-9;
+    o->power_seed = 0;
+    o->check_every = 10;
+    o->cuda_stream = nullptr;
+}
+
+int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,
+                    ncs_plan** out)
+{
+    if (!out) return NCS_ERR_BADARG;
+    *out = nullptr;
+    if (!geom || nx != ny || nx < 8 || geom->n_angles < 1 || geom->n_det < 1) return NCS_ERR_BADARG;
+    if (!(lambda >= 0.0) || !(alpha > 0.0)) return NCS_ERR_BADARG;
+    if (geom->det_spacing != 0.0 && !(geom->det_spacing >= 1.0)) return NCS_ERR_UNSUPPORTED;
+    ncs_options o;
+    if (opt) o = *opt;
+    else ncs_options_default(&o);
+    if (o.prec != NCS_FP32) return NCS_ERR_UNSUPPORTED;
+    if (o.nonneg && o.data != NCS_DATA_KL) return NCS_ERR_BADARG;
+    if (o.power_max_iter < 1 || !(o.power_tol >= 0.0)) return NCS_ERR_BADARG;
+    RadixPlan rp;
+    if (nx % 2 != 0 || nx > 4096 || !factor_radices(nx, &rp)) return NCS_ERR_UNSUPPORTED;
+    if (geom->angles)
+        for (int a = 0; a < geom->n_angles; ++a)
+            if (!std::isfinite(geom->angles[a])) return NCS_ERR_BADARG;
+    ncs_plan* p = new (std::nothrow) ncs_plan();
+    if (!p) return NCS_ERR_NOMEM;
+    p->N = nx;
+    p->na = geom->n_angles;
+    p->nd = geom->n_det;
+    p->lam = lambda;
+    p->alpha = alpha;
+    p->beta = std::isnan(o.beta) ? alpha : o.beta;
+    p->gamma = o.gamma;
+    p->kappa = o.kappa;
+    p->c_r = o.c_r;
+    p->h_dc = o.h_dc;
+    p->kl = o.data == NCS_DATA_KL;
+    p->iso = o.tv == NCS_TV_ISO;
+    p->nonneg = o.nonneg != 0;
+    p->opt = o;
+    p->rp = rp;
+    if (!(p->beta > 0.0) || !(p->gamma >= 0.0) || (p->nonneg && !(p->kappa > 0.0))) {
+        delete p;
+        return NCS_ERR_BADARG;
+    }
+    int rc = build_plan(p, geom);
+    if (rc != NCS_OK) {
+        free_plan(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return NCS_OK;
+}
+
+void ncs_plan_destroy(ncs_plan* p)
+{
+    if (!p) return;
+    cudaSetDevice(p->dev);
+    if (p->st) cudaStreamSynchronize(p->st);
+    free_plan(p);
+    delete p;
+}
+
+int ncs_step(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg, int n_iter)
+{
+    CKS(check_plan(p));
+    if (!x || !u || !v || !b || n_iter < 1) return NCS_ERR_BADARG;
+    if (p->nonneg && !s) return NCS_ERR_BADARG;
+    if (!p->kl && bg) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    for (int k = 0; k < n_iter; ++k) CKS(enq_ncs_iter(p, x, u, v, s, b, bg));
+    return NCS_OK;
+}
+
+int pdhg_step(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg, int n_iter)
+{
+    CKS(check_plan(p));
+    if (!x || !u || !v || !b || n_iter < 1) return NCS_ERR_BADARG;
+    if (p->nonneg && !s) return NCS_ERR_BADARG;
+    if (!p->kl && bg) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    CKS(ensure_gamma_p(p));
+    for (int k = 0; k < n_iter; ++k) CKS(enq_pdhg_iter(p, x, u, v, s, b, bg));
+    return NCS_OK;
+}
+
+int ncs_solve(ncs_plan* p, const float* b, const float* bg, float* x, double tol, int max_iter, double f_star,
+              ncs_report* rep)
+{
+    CKS(check_plan(p));
+    return solve_common(p, 0, b, bg, x, tol, max_iter, f_star, rep);
+}
+
+int pdhg_solve(ncs_plan* p, const float* b, const float* bg, float* x, double tol, int max_iter, double f_star,
+               ncs_report* rep)
+{
+    CKS(check_plan(p));
+    return solve_common(p, 1, b, bg, x, tol, max_iter, f_star, rep);
+}
+
+int ncs_power_bound(ncs_plan* p, double* lambda_max_AtA, double* rho_M)
+{
+    CKS(check_plan(p));
+    CK(cudaSetDevice(p->dev));
+    if (lambda_max_AtA) {
+        if (!std::isfinite(p->lmax)) CKS(power_lmax(p, &p->lmax));
+        *lambda_max_AtA = p->lmax;
+    }
+    if (rho_M) *rho_M = p->rho;
+    return NCS_OK;
+}
+
+int ncs_apply_K(ncs_plan* p, const float* x, float* y)
+{
+    CKS(check_plan(p));
+    if (!x || !y) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    CKS(enq_transpose(p, x, p->d_tmpT));
+    return enq_K(p, x, p->d_tmpT, y);
+}
+
+int ncs_apply_KT(ncs_plan* p, const float* y, float* x)
+{
+    CKS(check_plan(p));
+    if (!x || !y) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    return enq_gather(p, GATHER_R, y, nullptr, 0.f, nullptr, 0.f, x, nullptr, nullptr, 0.f, p->na);
+}
+
+int ncs_apply_D(ncs_plan* p, const float* x, float* v)
+{
+    CKS(check_plan(p));
+    if (!x || !v) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    TdArgs a{};
+    a.x = x;
+    a.v = v;
+    a.N = p->N;
+    a.beta = 1.0f;
+    CK(launch_td(TD_APPLY, a, p->st));
+    return NCS_OK;
+}
+
+int ncs_apply_DT(ncs_plan* p, const float* v, float* x)
+{
+    CKS(check_plan(p));
+    if (!x || !v) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    // the gather with no angles is D^T v alone
+    return enq_gather(p, GATHER_R, nullptr, v, 1.0f, nullptr, 0.f, x, nullptr, nullptr, 0.f, 0);
+}
+
+int ncs_apply_Minv(ncs_plan* p, const float* r, float* out)
+{
+    CKS(check_plan(p));
+    if (!r || !out) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    return enq_solve(p, r, p->d_invmu, 1, nullptr, nullptr, out);
+}
+
+int ncs_objective(ncs_plan* p, const float* x, const float* b, const float* bg, double* f)
+{
+    CKS(check_plan(p));
+    if (!x || !b || !f) return NCS_ERR_BADARG;
+    if (!p->kl && bg) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    CKS(enq_objective(p, x, b, bg, 0));
+    CKS(read_scalars(p, 1));
+    *f = p->h_pin[0];
+    return NCS_OK;
+}
+
+int ncs_get_mu(ncs_plan* p, double* mu_host)
+{
+    CKS(check_plan(p));
+    if (!mu_host) return NCS_ERR_BADARG;
+    memcpy(mu_host, p->mu.data(), p->mu.size() * sizeof(double));
+    return NCS_OK;
+}
+
+int ncs_plan_sizes(const ncs_plan* p, int* N, int* n_angles, int* n_det)
+{
+    CKS(check_plan(p));
+    if (N) *N = p->N;
+    if (n_angles) *n_angles = p->na;
+    if (n_det) *n_det = p->nd;
+    return NCS_OK;
+}
+
+const char* ncs_status_string(int s)
+{
+    switch (s) {
+        case NCS_OK: return "ok";
+        case NCS_NOT_CONVERGED: return "not converged within max_iter";
+        case NCS_ERR_BADARG: return "bad argument";
+        case NCS_ERR_UNSUPPORTED: return "unsupported size or option";
+        case NCS_ERR_CUDA: return "CUDA error";
+        case NCS_ERR_NOMEM: return "out of device memory";
+        case NCS_ERR_DIVERGED: return "diverged (non-finite objective)";
+        case NCS_ERR_TIMEOUT: return "device wait timed out";
+        default: return "unknown status";
+    }
+}
+
+}  // extern "C"

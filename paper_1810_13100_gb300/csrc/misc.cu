@@ -1,0 +1,243 @@
+// Finite differences, TV dual prox, transposes and FP64 reductions for sm_103a.
+//
+// k_td works on 32 x 32 image tiles staged in shared memory with a one-pixel
+// halo (right column, bottom row), so D (Sec. 2: (D_n x)_i = x_i - x_{i+1}) is
+// formed from shared memory and the transposed image x^T (read by the
+// column-branch rays of the projector) is written with coalesced stores.
+//   TD_PROX : v+ = Pi(v + beta D xbar)  (box [-lam alpha/beta, lam alpha/beta]
+//             of Sec. 4.1, or the per-pixel l2 ball for isotropic TV) and
+//             s+ = min(0, s + alpha kappa xbar) (Sec. 4.2 nonnegativity row)
+//   TD_APPLY: v = c D x, s = kappa x (the D and I rows of A)
+//   TD_OBJ  : TV(x) partial sums in FP64 (optionally at max(x, 0))
+#include "ncs_internal.cuh"
+
+namespace ncs {
+
+namespace {
+
+constexpr int TT = 32;      // tile side
+constexpr int TR = 8;       // block rows
+
+template <int MODE>
+__global__ void __launch_bounds__(TT * TR)
+k_td(TdArgs g)
+{
+    __shared__ float tile[TT + 1][TT + 1];
+    __shared__ double red[TT * TR];
+    const int N = g.N;
+    const int i0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r <= TT; r += TR) {
+        for (int c = tx; c <= TT; c += TT) {
+            const int gj = j0 + r, gi = i0 + c;
+            float val = (gj < N && gi < N) ? g.x[(size_t)gj * N + gi] : 0.0f;
+            if (MODE == TD_OBJ && g.clamp) val = fmaxf(val, 0.0f);
+            tile[r][c] = val;
+        }
+    }
+    __syncthreads();
+    double tv = 0.0;
+    const size_t NN = (size_t)N * N;
+#pragma unroll
+    for (int q = 0; q < TT / TR; ++q) {
+        const int r = ty + q * TR, c = tx;
+        const int gj = j0 + r, gi = i0 + c;
+        if (gj >= N || gi >= N) continue;
+        const size_t pix = (size_t)gj * N + gi;
+        const float xv = tile[r][c];
+        const bool hx = gi < N - 1, hy = gj < N - 1;
+        const float dh = hx ? xv - tile[r][c + 1] : 0.0f;
+        const float dv = hy ? xv - tile[r + 1][c] : 0.0f;
+        if (MODE == TD_PROX) {
+            float zh = hx ? fmaf(g.beta, dh, g.v[pix]) : 0.0f;
+            float zv = hy ? fmaf(g.beta, dv, g.v[NN + pix]) : 0.0f;
+            if (g.iso) {
+                const float n2 = fmaf(zh, zh, zv * zv);
+                if (n2 > g.rad * g.rad) {
+                    const float f = g.rad * rsqrtf(n2);
+                    zh *= f;
+                    zv *= f;
+                }
+            } else {
+                zh = fminf(fmaxf(zh, -g.rad), g.rad);
+                zv = fminf(fmaxf(zv, -g.rad), g.rad);
+            }
+            g.v[pix] = zh;
+            g.v[NN + pix] = zv;
+            if (g.s) g.s[pix] = fminf(fmaf(g.ak, xv, g.s[pix]), 0.0f);
+        } else if (MODE == TD_APPLY) {
+            if (g.v) {
+                g.v[pix] = g.beta * dh;
+                g.v[NN + pix] = g.beta * dv;
+            }
+            if (g.s) g.s[pix] = g.ak * xv;
+        } else if (MODE == TD_OBJ) {
+            const double a = dh, b = dv;
+            tv += g.iso ? sqrt(a * a + b * b) : fabs(a) + fabs(b);
+            if (g.clamp && g.xc) g.xc[pix] = xv;
+        }
+    }
+    // transposed store: xT[i][j] = x[j][i]
+    if (g.xT) {
+#pragma unroll
+        for (int q = 0; q < TT / TR; ++q) {
+            const int oi = i0 + ty + q * TR, oj = j0 + tx;
+            if (oi < N && oj < N) g.xT[(size_t)oi * N + oj] = tile[tx][ty + q * TR];
+        }
+    }
+    if (MODE == TD_OBJ) {
+        const int tid = ty * TT + tx;
+        red[tid] = tv;
+        __syncthreads();
+        for (int s = TT * TR / 2; s > 0; s >>= 1) {
+            if (tid < s) red[tid] += red[tid + s];
+            __syncthreads();
+        }
+        if (tid == 0) g.partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
+    }
+}
+
+constexpr int RB = 256;     // reduction block
+
+__global__ void k_dot_partials(const float* __restrict__ a, const float* __restrict__ b, size_t n,
+                               double* __restrict__ partials)
+{
+    __shared__ double red[RB];
+    double s = 0.0;
+    for (size_t k = (size_t)blockIdx.x * RB + threadIdx.x; k < n; k += (size_t)gridDim.x * RB)
+        s += (double)a[k] * (double)b[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__device__ double block_sum_fixed(const double* p, int n, double* red)
+{
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += RB) s += p[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = RB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    double out = red[0];
+    __syncthreads();
+    return out;
+}
+
+__global__ void k_finalize(const double* p0, int n0, double c0, const double* p1, int n1, double c1, double* out)
+{
+    __shared__ double red[RB];
+    double s0 = block_sum_fixed(p0, n0, red);
+    double s1 = p1 ? block_sum_fixed(p1, n1, red) : 0.0;
+    if (threadIdx.x == 0) out[0] = c0 * s0 + c1 * s1;
+}
+
+__global__ void k_scale_by_rsqrt(const float* __restrict__ x, float* __restrict__ y, size_t n,
+                                 const double* __restrict__ nrm2)
+{
+    const float f = (float)(1.0 / sqrt(nrm2[0]));
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = x[k] * f;
+}
+
+__global__ void k_scale(float* a, size_t n, float alpha)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        a[k] *= alpha;
+}
+
+__global__ void k_axpy(float alpha, const float* __restrict__ x, float* __restrict__ y, size_t n)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = fmaf(alpha, x[k], y[k]);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): state seed + (k+1) * golden gamma, two
+// xor-shift-multiply rounds; the top 53 bits give a uniform in [0, 1).
+__global__ void k_splitmix(float* x, size_t n, uint64_t seed)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + (uint64_t)(k + 1) * 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z = z ^ (z >> 31);
+        const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+        x[k] = (float)(2.0 * u - 1.0);
+    }
+}
+
+int grid_for(size_t n)
+{
+    size_t g = (n + 255) / 256;
+    if (g > 1216) g = 1216;     // 8 x 152 SMs
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+int td_num_blocks(int N)
+{
+    const int b = (N + TT - 1) / TT;
+    return b * b;
+}
+
+cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st)
+{
+    const int b = (a.N + TT - 1) / TT;
+    dim3 grid(b, b), block(TT, TR);
+    switch (mode) {
+        case TD_PROX: k_td<TD_PROX><<<grid, block, 0, st>>>(a); break;
+        case TD_APPLY: k_td<TD_APPLY><<<grid, block, 0, st>>>(a); break;
+        case TD_OBJ: k_td<TD_OBJ><<<grid, block, 0, st>>>(a); break;
+        case TD_TRANSPOSE: k_td<TD_TRANSPOSE><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dot_partials(const float* a, const float* b, size_t n, double* partials, int nblk,
+                                cudaStream_t st)
+{
+    k_dot_partials<<<nblk, RB, 0, st>>>(a, b, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* p0, int n0, double c0, const double* p1, int n1, double c1,
+                            double* out, cudaStream_t st)
+{
+    k_finalize<<<1, RB, 0, st>>>(p0, n0, c0, p1, n1, c1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_by_rsqrt(const float* x, float* y, size_t n, const double* nrm2, cudaStream_t st)
+{
+    k_scale_by_rsqrt<<<grid_for(n), 256, 0, st>>>(x, y, n, nrm2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale(float* a, size_t n, float alpha, cudaStream_t st)
+{
+    k_scale<<<grid_for(n), 256, 0, st>>>(a, n, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(float a, const float* x, float* y, size_t n, cudaStream_t st)
+{
+    k_axpy<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_splitmix(float* x, size_t n, uint64_t seed, cudaStream_t st)
+{
+    k_splitmix<<<grid_for(n), 256, 0, st>>>(x, n, seed);
+    return cudaGetLastError();
+}
+
+}  // namespace ncs

@@ -1,0 +1,129 @@
+// Internal declarations shared by the CUDA translation units of the NCS library.
+// Not part of the public C ABI (include/ncs.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ncs {
+
+// Per-angle Joseph coefficients, FP64 on the host, rounded once.
+// A ray (a, t) crosses stepping line q (an image row, or a row of x^T for
+// column-branch angles) at the fractional index f = A t + B q + C along the
+// interpolation axis.  To keep the interpolation weight accurate in FP32 at
+// large N, each coefficient is split as X = X_hi + X_lo with X_hi a multiple of
+// 2^-10: then H = A_hi t + B_hi q + C_hi is exact in FP32 (|H| < 2^14) in any
+// evaluation order, and the small remainder L = B_lo q + (A_lo t + C_lo) is
+// evaluated in that fixed order.  The integer part of f is floor(H) +
+// floor((H - floor(H)) + L) and the weight is the fractional part of the
+// same sum, so the forward projector and the gather evaluate identical bits.
+// W = 1/|cos| or 1/|sin| is the path length per step; invA ~ 1/A locates the
+// rays that reach a pixel in the gather.
+struct AngleParam {
+    float Ahi, Alo, Bhi, Blo;
+    float Chi, Clo, W, invA;
+    int row;       // 1: stepped over rows of x; 0: over rows of x^T
+    int pad0, pad1, pad2;
+};
+
+// Forward-projection epilogues.
+enum FwdMode {
+    FWD_PLAIN = 0,     // y = K x
+    FWD_PROX_L2 = 1,   // u+ = (u + alpha (K x - b)) / (1 + alpha)
+    FWD_PROX_KL = 2,   // u+ = S(u + alpha (K x + bg); alpha b)
+    FWD_RESID_L2 = 3,  // partial sums of (K x - b)^2 (FP64)
+    FWD_RESID_KL = 4,  // partial sums of mu - b + b log(b/mu), mu = K x + bg (FP64)
+};
+
+struct FwdArgs {
+    const float* img;    // row-major image (row-branch angles)
+    const float* imgT;   // transposed image (column-branch angles)
+    const AngleParam* ap;
+    int N, n_ang, n_det;
+    float* y;            // PLAIN: output; PROX: dual u, updated in place
+    const float* b;
+    const float* bg;     // KL background or nullptr
+    float alpha, inv1pa;
+    double* partials;    // RESID: one partial per block (gridDim.x * gridDim.y)
+};
+
+// Gather epilogues.
+enum GatherMode {
+    GATHER_R = 0,        // r = K^T u + dscale D^T v + kappa s
+    GATHER_PDHG = 1,     // x+ = x - inv_gamma * r ; xbar = 2 x+ - x
+};
+
+struct GatherArgs {
+    const float* u;
+    const AngleParam* ap;
+    int N, n_ang, n_det;
+    const float* v;      // 2*N*N or nullptr
+    float dscale;
+    const float* s;      // N*N or nullptr
+    float kappa;
+    float* r;            // GATHER_R output
+    float* x;            // GATHER_PDHG: primal, updated in place
+    float* xbar;         // GATHER_PDHG: extrapolated primal
+    float inv_gamma;
+};
+
+// Transpose / finite-difference pass.
+enum TdMode {
+    TD_PROX = 0,         // v+ = Pi(v + beta D xbar), s+ = min(0, s + alpha kappa xbar), xbarT
+    TD_APPLY = 1,        // v = dscale D x, s = kappa x (if s), xT
+    TD_OBJ = 2,          // xc = clamp(x) (if clamp), xcT, TV partial sums (FP64)
+    TD_TRANSPOSE = 3,    // xT only
+};
+
+struct TdArgs {
+    const float* x;
+    float* xT;
+    float* v;            // 2*N*N
+    float* s;            // N*N or nullptr
+    float* xc;           // TD_OBJ with clamp: clamped copy
+    int N;
+    float beta;          // TD_PROX: beta; TD_APPLY: dscale
+    float rad;           // TV ball / box radius lambda alpha / beta
+    float ak;            // alpha * kappa (TD_PROX) or kappa (TD_APPLY)
+    int iso;             // 1: isotropic TV
+    int clamp;           // TD_OBJ: evaluate at max(x, 0)
+    double* partials;
+};
+
+struct RadixPlan {
+    int n;               // number of stages
+    int r[12];           // radices (2, 3, 4 or 8)
+};
+
+// ---- launchers (all asynchronous on `st`) ----
+cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st);
+int fwd_num_blocks(int n_det, int n_ang);
+cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st);
+cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st);
+int td_num_blocks(int N);
+
+cudaError_t launch_rows_fwd(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N,
+                            cudaStream_t st);
+cudaError_t launch_cols_solve(float2* S, const float* invmu, const float2* tw, const RadixPlan& rp, int N,
+                              cudaStream_t st);
+// mode 0: x <- x - delta, xbar <- x_old - 2 delta ; mode 1: out <- delta
+cudaError_t launch_rows_inv(const float2* S, const float2* tw, const RadixPlan& rp, int N, int mode,
+                            float* x, float* xbar, float* out, cudaStream_t st);
+
+// FP64 reductions.  Partial sums go to `partials` (one per block), finalize
+// sums them in a fixed order, so results are deterministic.
+cudaError_t launch_dot_partials(const float* a, const float* b, size_t n, double* partials, int nblk,
+                                cudaStream_t st);
+// out[0] = c0 * sum(p0[0..n0)) + c1 * sum(p1[0..n1))   (p1 may be null)
+cudaError_t launch_finalize(const double* p0, int n0, double c0, const double* p1, int n1, double c1,
+                            double* out, cudaStream_t st);
+// y = x * rsqrt(*nrm2)  (nrm2 on the device)
+cudaError_t launch_scale_by_rsqrt(const float* x, float* y, size_t n, const double* nrm2, cudaStream_t st);
+// a = alpha * a
+cudaError_t launch_scale(float* a, size_t n, float alpha, cudaStream_t st);
+// SplitMix64 uniforms in [-1, 1)
+cudaError_t launch_splitmix(float* x, size_t n, uint64_t seed, cudaStream_t st);
+// y = a*x + y ; y = x
+cudaError_t launch_axpy(float a, const float* x, float* y, size_t n, cudaStream_t st);
+
+}  // namespace ncs
