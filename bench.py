@@ -1,0 +1,400 @@
+"""Benchmark of the NCS hot path on the 512x512 TV-CT workload (720 angles,
+730 bins, isotropic TV, lambda 0.005, 20 seeded ellipses, 0.5% noise).
+
+One "step" is one NCS iteration with every step of the hot path: the K^T
+gather, the FFT solve with M, the primal update, the TV dual prox, the forward
+projection with the data prox, and (every check_every = 10 steps) the FP64
+objective reduction read back by the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is NCS iterations per second summed over
+ranks (replicas: each GPU solves its own slice, no collective on the data path).
+L2 is flushed (256 MiB write, untimed) before every timed step; each step is
+timed with CUDA events on the plan's stream.  Also reported: time to a 1e-4
+relative objective gap for NCS and PDHG on the same GPU (against the FP64
+oracle's f* stored in tests/golden), per-kernel times, the roofline of the
+dominant kernel, the end-to-end rate through the Python API with host buffers,
+and the FP64 CPU oracle timed on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "ct512"
+# NCS / PDHG parameters for this workload, tuned on the {1,3} x 10^p grid (Sec. 5)
+NCS_PARAMS = dict(alpha=0.003, beta=0.003, gamma=0.0)
+PDHG_PARAMS = dict(alpha=0.001, beta=0.001)
+CHECK_EVERY = 10
+TTG_TOL = 1e-4
+TTG_CAP = 2000
+METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def load_fstar(workload, seed):
+    path = os.path.join(ROOT, "tests", "golden", "fstar_%s_s%d.json" % (workload, seed))
+    try:
+        with open(path) as fh:
+            return json.load(fh)["f_star"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def _cuda_available():
+    import torch
+    return torch.cuda.is_available()
+
+
+def reduce_max(value, ws):
+    """Max of a float over ranks (identity for one rank)."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value, ws):
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def make_inputs(seed):
+    import synth
+    W = synth.WORKLOADS[WORKLOAD]
+    pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+    return W, pr
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+
+def oracle_rate(seed, budget_s=15.0, min_iters=2):
+    """FP64 oracle NCS iterations per second on the host cores for a bounded
+    sample of the workload (iterations from the zero state)."""
+    import numpy as np
+    from oracle import circulant as oci, operators as oop, solvers as osv
+    W, pr = make_inputs(seed)
+    g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
+    P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=NCS_PARAMS["alpha"],
+                    beta=NCS_PARAMS["beta"], tv=W["tv"])
+    # the oracle's M with a short power iteration for the (A3) rescale: setup, not a step
+    mu, _ = osv.a3_scaled_mu(P, oci.mu_table(g, P.alpha, P.beta, NCS_PARAMS["gamma"]), max_iter=3)
+    Minv = osv.circulant_Minv(mu)
+    st = osv.zero_state(P)
+    st = osv.ncs_step(P, st, Minv)          # warm-up (library loading, page faults)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < min_iters or time.perf_counter() - t_start < budget_s:
+        t0 = time.perf_counter()
+        st = osv.ncs_step(P, st, Minv)
+        if (len(times) + 1) % CHECK_EVERY == 0:
+            osv.objective(P, st.x)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= 1000:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(rate=len(times) / sum(times), iters=len(times), seconds=sum(times), cores=cores,
+                per_iter=times)
+
+
+def run_reference(args, ws, rank):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    per_iter_budget = max(5.0, min(150.0, 0.8 * args.steps))
+    # warm-up steps (untimed), then timed steps bounded to a few minutes
+    r = oracle_rate(args.seed, budget_s=per_iter_budget, min_iters=min(args.steps, 3))
+    times = r["per_iter"][: args.steps]
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": args.gpus,
+        "steps": len(times), "warmup": 1, "ms_per_step": 1000.0 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "512x512 TV-CT, 720 angles x 730 bins, iso TV lambda 0.005, seed %d" % args.seed,
+                   "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": "it/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": "%d FP64 oracle NCS iterations of the 512x512 workload from zero" % len(times)},
+        "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1810_13100_gb300 as ncs
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W, pr = make_inputs(args.seed + rank)
+    N, na, nd = W["N"], W["n_angles"], W["n_det"]
+    n, m = N * N, na * nd
+    plan = ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], gamma=NCS_PARAMS["gamma"],
+                    tv=W["tv"], check_every=CHECK_EVERY)
+    b = torch.from_numpy(pr["b"].ravel()).to(dev)
+    x = torch.zeros(n, device=dev)
+    u = torch.zeros(m, device=dev)
+    v = torch.zeros(2 * n, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream = plan.stream
+    cur = torch.cuda.current_stream()
+
+    def one_step(k):
+        plan.step(x, u, v, None, b, n_iter=1)
+        if (k + 1) % CHECK_EVERY == 0:
+            plan.objective(x, b)                  # FP64 reduction read by the host
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.profile(True)
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        for k in range(args.steps):
+            flush.fill_(float(k))                         # evict L2 (untimed)
+            stream.wait_stream(cur)
+            starts[k].record(stream)
+            one_step(k)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    barrier(ws)
+    kern = plan.profile_read()
+    plan.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_ms = sum(step_ms)
+    t_max = reduce_max(t_ms, ws)
+    total_iters = reduce_sum(args.steps, ws)
+    value = total_iters / (t_max / 1000.0)
+    launches = sum(c for _, c in kern.values())
+
+    # ---- roofline of the dominant kernel (algorithmic work / measured duration)
+    peaks, peak_kind = load_peaks()
+    dom = max(kern.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    clk_sum = clk.summary()
+    nnz = plan.nnz()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FMA = 2 flops
+    roof = None
+    if dom_name in ("joseph_gather", "joseph_fwd", "joseph_fwd_resid"):
+        flops = 2.0 * nnz
+        achieved = flops / (dom_ms / dom_n / 1000.0) / 1e12
+        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
+                "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
+    # whole-iteration algorithmic bytes (FP32 state read + written once, b read, spectrum round trips)
+    it_bytes = 4.0 * (10 * n + 3 * m)
+    it_gbs = it_bytes / (t_ms / args.steps / 1000.0) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+
+    # ---- end to end through the Python API with host buffers
+    e2e = None
+    if not args.skip_e2e:
+        b_host = torch.from_numpy(pr["b"].ravel()).pin_memory()
+        x_host = torch.empty(n, dtype=torch.float32).pin_memory()
+        xe = torch.zeros(n, device=dev)
+        ue = torch.zeros(m, device=dev)
+        ve = torch.zeros(2 * n, device=dev)
+        be = torch.empty(m, device=dev)
+        k_e2e = max(10, min(args.steps, 200))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(k_e2e):
+            be.copy_(b_host, non_blocking=True)
+            plan.step(xe, ue, ve, None, be, n_iter=1)
+            if (k + 1) % CHECK_EVERY == 0:
+                plan.objective(xe, be)
+            x_host.copy_(xe, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": reduce_sum(k_e2e, ws) / reduce_max(dt, ws), "unit": "it/s",
+               "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 4 * n}
+
+    # ---- time to 1e-4 gap, NCS vs PDHG (same GPU, same inputs, zero start)
+    ttg = None
+    f_star = load_fstar(WORKLOAD, args.seed + rank)
+    if not args.skip_ttg and f_star is not None:
+        ttg = {"tol": TTG_TOL, "cap": TTG_CAP, "f_star": f_star}
+        xs = torch.zeros(n, device=dev)
+        rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
+        ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        if rep["status"] != 0 and args.ttg_extended:
+            xs.zero_()
+            rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=args.ttg_extended, f_star=f_star)
+            ttg["ncs_extended"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        pplan = ncs.Plan(N, na, nd, W["lam"], PDHG_PARAMS["alpha"], beta=PDHG_PARAMS["beta"], tv=W["tv"],
+                         check_every=CHECK_EVERY)
+        xs.zero_()
+        rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
+        ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        pplan.close()
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        r = oracle_rate(args.seed, budget_s=args.cpu_seconds)
+        cpu = {"value": r["rate"], "unit": "it/s", "cores": r["cores"], "kind": "oracle",
+               "sample": "%d FP64 oracle NCS iterations of the 512x512 workload from zero (%.1f s)"
+                         % (r["iters"], r["seconds"])}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "512x512 TV-CT, 720 angles x 730 bins, iso TV lambda 0.005, 20 ellipses, "
+                                   "0.5%% noise, seed %d" % args.seed,
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "flushed before every timed step (256 MiB write, untimed)",
+                       "check_every": CHECK_EVERY, "ncs": NCS_PARAMS},
+            "roofline": roof,
+            "iteration_hbm": {"achieved": it_gbs, "peak": hbm, "unit": "GB/s", "frac": it_gbs / hbm,
+                              "algorithmic_bytes_per_iter": it_bytes, "peak_kind": peak_kind},
+            "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kern.items()},
+            "kernel_share": {k: v[0] / max(1e-12, sum(w[0] for w in kern.values())) for k, v in kern.items()},
+            "gpu_launches": launches,
+            "e2e": e2e, "time_to_gap": ttg, "cpu_baseline": cpu, "clocks": clk_sum,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--skip-ttg", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ttg-extended", type=int, default=8000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        # the oracle runs on the host of rank 0 only; other ranks exit without work
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    ws, rank, local = dist_setup()
+    if True:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,38 @@ int ncs_get_mu(ncs_plan* plan, double* mu_host);
 /* Plan sizes: N, n_angles, n_det. */
 int ncs_plan_sizes(const ncs_plan* plan, int* N, int* n_angles, int* n_det);
 
+/* ---- Measurement ---- */
+
+/* Kernel classes reported by ncs_profile_read. */
+#define NCS_KERNEL_GATHER      0   /* K^T gather (+ D^T, nonneg row, PDHG update) */
+#define NCS_KERNEL_ROWS_FWD    1   /* FFT solve: row transforms */
+#define NCS_KERNEL_COLS_SOLVE  2   /* FFT solve: column transforms and 1/mu */
+#define NCS_KERNEL_ROWS_INV    3   /* FFT solve: inverse rows and primal update */
+#define NCS_KERNEL_TD          4   /* D x, TV / nonneg dual prox, transposes, TV sums */
+#define NCS_KERNEL_FWD         5   /* K forward projection with the data prox */
+#define NCS_KERNEL_FWD_RESID   6   /* K forward projection with the FP64 data-term sum */
+#define NCS_KERNEL_REDUCE      7   /* FP64 reductions */
+#define NCS_KERNEL_COUNT       8
+
+/* Turn per-kernel timing on (1) or off (0) and clear what was recorded.  While
+ * on, every kernel the plan enqueues outside graph capture is bracketed by
+ * CUDA events on the plan's stream (at most 2^18 launches are kept).
+ * Synchronises. */
+int ncs_profile_enable(ncs_plan* plan, int on);
+
+/* Sum of the recorded kernel durations (ms) and launch counts per class into
+ * ms[NCS_KERNEL_COUNT] and launches[NCS_KERNEL_COUNT] (host arrays), then clear
+ * the record.  Synchronises. */
+int ncs_profile_read(ncs_plan* plan, double* ms, int* launches);
+
+/* Name of a kernel class (static string). */
+const char* ncs_kernel_name(int kernel_class);
+
+/* Number of nonzero weights of the plan's K, counted on the host with the same
+ * FP32 arithmetic the kernels use (the work of one application of K or K^T is
+ * 2 * nnz flops).  Computed once per plan. */
+int ncs_plan_nnz(ncs_plan* plan, double* nnz);
+
 /* Human-readable name of a status code (static string). */
 const char* ncs_status_string(int status);
 

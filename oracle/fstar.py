@@ -1,0 +1,100 @@
+"""Reference minimum f* of a named workload by a long FP64 oracle NCS run.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).  Writes
+tests/golden/fstar_<workload>_s<seed>.json with f*, the iteration count and
+the decrease of f over the last stretch of the run (an error indicator).  The
+relative objective gap (f - f*)/|f*| of the benchmark and tests is measured
+against this value.
+
+    python -m oracle.fstar ct512 --seed 0 --iters 8000 --checkpoint /tmp/ct512.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import time
+
+import numpy as np
+
+from . import circulant as oci
+from . import operators as oop
+from . import solvers as osv
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+# NCS parameters of the reference runs ({1,3} x 10^p grid, Sec. 5)
+PARAMS = {
+    "ct64": dict(alpha=0.01, beta=0.01, gamma=0.0),
+    "ct512": dict(alpha=0.003, beta=0.003, gamma=0.0),
+    "pet256": dict(alpha=0.1, beta=0.1, gamma=0.0),
+}
+
+
+def problem(workload: str, seed: int):
+    import synth
+    W = synth.WORKLOADS[workload]
+    g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
+    p = PARAMS[workload]
+    if W["kind"] == "ct":
+        pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+        P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=p["alpha"], beta=p["beta"],
+                        tv=W["tv"])
+    else:
+        pr = synth.pet_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"])
+        P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=p["alpha"], beta=p["beta"],
+                        tv=W["tv"], kind="pet", kappa=1.0, r_bg=pr["r_bg"].astype(np.float64))
+    return P, p
+
+
+def golden_path(workload: str, seed: int) -> str:
+    return os.path.join(ROOT, "tests", "golden", "fstar_%s_s%d.json" % (workload, seed))
+
+
+def run(workload: str, seed: int, iters: int, checkpoint: str | None, every: int = 250):
+    P, p = problem(workload, seed)
+    mu0 = oci.mu_table(P.g, P.alpha, P.beta, p["gamma"], kappa=P.kappa)
+    mus, rho = osv.a3_scaled_mu(P, mu0)
+    Minv = osv.circulant_Minv(mus)
+    st, k0, hist = osv.zero_state(P), 0, []
+    if checkpoint and os.path.exists(checkpoint):
+        z = np.load(checkpoint)
+        st = osv.State(z["x"], z["u"], z["vh"], z["vv"], z["s"] if "s" in z.files else None)
+        k0, hist = int(z["k"]), [tuple(h) for h in z["hist"]]
+    t0 = time.time()
+    for k in range(k0, iters):
+        st = osv.ncs_step(P, st, Minv)
+        if (k + 1) % every == 0 or k + 1 == iters:
+            f = osv.objective(P, st.x)
+            hist.append((k + 1, f))
+            print("%s seed %d iter %d f %.12e  (%.0fs)" % (workload, seed, k + 1, f, time.time() - t0), flush=True)
+            if checkpoint:
+                extra = {"s": st.s} if st.s is not None else {}
+                np.savez(checkpoint + ".tmp.npz", x=st.x, u=st.u, vh=st.vh, vv=st.vv, k=k + 1,
+                         hist=np.array(hist), **extra)
+                os.replace(checkpoint + ".tmp.npz", checkpoint)
+    f_star = min(h[1] for h in hist)
+    last = [h for h in hist if h[0] >= hist[-1][0] - 1000]
+    out = dict(workload=workload, seed=seed, f_star=f_star, iterations=hist[-1][0], rho=rho,
+               params=p, decrease_last_1000=last[0][1] - last[-1][1],
+               note="FP64 oracle NCS (Sec. 4.1/4.2 updates) from zero; f_star is the lowest objective seen")
+    path = golden_path(workload, seed)
+    with open(path, "w") as fh:
+        json.dump(out, fh, indent=1)
+    print("wrote", path, out)
+    return out
+
+
+def load(workload: str, seed: int = 0):
+    with open(golden_path(workload, seed)) as fh:
+        return json.load(fh)
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    ap.add_argument("workload")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--iters", type=int, default=8000)
+    ap.add_argument("--checkpoint", default=None)
+    a = ap.parse_args()
+    run(a.workload, a.seed, a.iters, a.checkpoint)

@@ -78,7 +78,13 @@ SIGNATURES = [
     ("ncs_get_mu", _I, [_P, _DP]),
     ("ncs_plan_sizes", _I, [_P, _IP, _IP, _IP]),
     ("ncs_status_string", ctypes.c_char_p, [_I]),
+    ("ncs_profile_enable", _I, [_P, _I]),
+    ("ncs_profile_read", _I, [_P, _DP, _IP]),
+    ("ncs_kernel_name", ctypes.c_char_p, [_I]),
+    ("ncs_plan_nnz", _I, [_P, _DP]),
 ]
+
+NCS_KERNEL_COUNT = 8
 
 
 def load_library(path: str | None = None) -> ctypes.CDLL:
@@ -293,6 +299,23 @@ class Plan:
         self._call("ncs_objective", self._L.ncs_objective, self._h, _ptr(x, "x", self.n), _ptr(b, "b", self.m),
                    _ptr(bg, "bg", self.m, allow_none=True), ctypes.byref(f))
         return f.value
+
+    def profile(self, on=True):
+        """Turn per-kernel CUDA-event timing on or off (clears the record)."""
+        self._call("ncs_profile_enable", self._L.ncs_profile_enable, self._h, 1 if on else 0)
+
+    def profile_read(self):
+        """{kernel name: (total ms, launches)} since the last read, then cleared."""
+        ms = (ctypes.c_double * NCS_KERNEL_COUNT)()
+        n = (ctypes.c_int * NCS_KERNEL_COUNT)()
+        self._call("ncs_profile_read", self._L.ncs_profile_read, self._h, ms, n)
+        return {self._L.ncs_kernel_name(k).decode(): (ms[k], n[k]) for k in range(NCS_KERNEL_COUNT)}
+
+    def nnz(self):
+        """Nonzero weights of K (2 * nnz flops per application of K or K^T)."""
+        v = ctypes.c_double()
+        _check(self._L.ncs_plan_nnz(self._h, ctypes.byref(v)), "ncs_plan_nnz")
+        return v.value
 
     def mu(self):
         import numpy as np

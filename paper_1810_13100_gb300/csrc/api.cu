@@ -49,10 +49,20 @@ struct ncs_plan {
     float2* d_spec = nullptr;
     double *d_part0 = nullptr, *d_part1 = nullptr, *d_scal = nullptr, *h_pin = nullptr;
     float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
+    int gparts = 1;                  // angle slices of the gather
+    float* d_gpart = nullptr;        // gather scratch: gparts * N * N partial sums
+    int* d_gcount = nullptr;         // gather scratch: arrival counter per 32 x 32 tile
     double rho = std::numeric_limits<double>::quiet_NaN();
     double lmax = std::numeric_limits<double>::quiet_NaN();
     float gamma_p = 0.0f;
     GraphCache graph;
+    // per-kernel event timing (ncs_profile_enable / ncs_profile_read)
+    bool prof = false;
+    bool capturing = false;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> ev_pool;
+    double nnz_K = -1.0;
 };
 
 namespace {
@@ -71,6 +81,52 @@ namespace {
     do {                                  \
         int s_ = (expr);                  \
         if (s_ < 0) return s_;            \
+    } while (0)
+
+constexpr size_t kMaxProfRecords = 1u << 18;
+
+cudaEvent_t prof_event(ncs_plan* p)
+{
+    if (!p->ev_pool.empty()) {
+        cudaEvent_t e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one kernel launch with CUDA events on the plan's stream while
+// profiling is on (never inside graph capture).
+struct ProfScope {
+    ncs_plan* p;
+    int cls;
+    cudaEvent_t a = nullptr;
+    ProfScope(ncs_plan* p_, int cls_) : p(p_), cls(cls_)
+    {
+        if (p->prof && !p->capturing && p->recs.size() < kMaxProfRecords) {
+            a = prof_event(p);
+            if (a) cudaEventRecord(a, p->st);
+        }
+    }
+    ~ProfScope()
+    {
+        if (!a) return;
+        cudaEvent_t b = prof_event(p);
+        if (!b) { p->ev_pool.push_back(a); return; }
+        cudaEventRecord(b, p->st);
+        p->recs.push_back({cls, a, b});
+    }
+};
+
+#define CKP(cls, expr)              \
+    do {                            \
+        ProfScope ps_(p, (cls));    \
+        CK(expr);                   \
     } while (0)
 
 size_t NN(const ncs_plan* p) { return (size_t)p->N * p->N; }
@@ -107,7 +163,7 @@ int enq_transpose(ncs_plan* p, const float* x, float* xT)
     a.x = x;
     a.xT = xT;
     a.N = p->N;
-    CK(launch_td(TD_TRANSPOSE, a, p->st));
+    CKP(NCS_KERNEL_TD, launch_td(TD_TRANSPOSE, a, p->st));
     return NCS_OK;
 }
 
@@ -121,7 +177,7 @@ int enq_K(ncs_plan* p, const float* x, const float* xT, float* y)
     f.n_ang = p->na;
     f.n_det = p->nd;
     f.y = y;
-    CK(launch_fwd(FWD_PLAIN, f, p->st));
+    CKP(NCS_KERNEL_FWD, launch_fwd(FWD_PLAIN, f, p->st));
     return NCS_OK;
 }
 
@@ -134,6 +190,9 @@ int enq_gather(ncs_plan* p, int mode, const float* u, const float* v, float dsca
     g.N = p->N;
     g.n_ang = n_ang;
     g.n_det = p->nd;
+    g.parts = n_ang > 0 ? p->gparts : 1;
+    g.part = p->d_gpart;
+    g.counters = p->d_gcount;
     g.v = v;
     g.dscale = dscale;
     g.s = s;
@@ -142,16 +201,16 @@ int enq_gather(ncs_plan* p, int mode, const float* u, const float* v, float dsca
     g.x = x;
     g.xbar = xbar;
     g.inv_gamma = inv_gamma;
-    CK(launch_gather(mode, g, p->st));
+    CKP(NCS_KERNEL_GATHER, launch_gather(mode, g, p->st));
     return NCS_OK;
 }
 
 // out = M^{-1} r (mode 1) or x <- x - M^{-1} r, xbar = 2 x+ - x (mode 0)
 int enq_solve(ncs_plan* p, const float* r, const float* table, int mode, float* x, float* xbar, float* out)
 {
-    CK(launch_rows_fwd(r, p->d_spec, p->d_tw, p->rp, p->N, p->st));
-    CK(launch_cols_solve(p->d_spec, table, p->d_tw, p->rp, p->N, p->st));
-    CK(launch_rows_inv(p->d_spec, p->d_tw, p->rp, p->N, mode, x, xbar, out, p->st));
+    CKP(NCS_KERNEL_ROWS_FWD, launch_rows_fwd(r, p->d_spec, p->d_tw, p->rp, p->N, p->st));
+    CKP(NCS_KERNEL_COLS_SOLVE, launch_cols_solve(p->d_spec, table, p->d_tw, p->rp, p->N, p->st));
+    CKP(NCS_KERNEL_ROWS_INV, launch_rows_inv(p->d_spec, p->d_tw, p->rp, p->N, mode, x, xbar, out, p->st));
     return NCS_OK;
 }
 
@@ -168,7 +227,7 @@ int enq_td_prox(ncs_plan* p, float* v, float* s)
     a.rad = (float)(p->lam * p->alpha / p->beta);
     a.ak = (float)(p->alpha * p->kappa);
     a.iso = p->iso ? 1 : 0;
-    CK(launch_td(TD_PROX, a, p->st));
+    CKP(NCS_KERNEL_TD, launch_td(TD_PROX, a, p->st));
     return NCS_OK;
 }
 
@@ -186,7 +245,7 @@ int enq_fwd_prox(ncs_plan* p, float* u, const float* b, const float* bg)
     f.bg = bg;
     f.alpha = (float)p->alpha;
     f.inv1pa = (float)(1.0 / (1.0 + p->alpha));
-    CK(launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
+    CKP(NCS_KERNEL_FWD, launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
     return NCS_OK;
 }
 
@@ -228,7 +287,7 @@ int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, 
     a.N = p->N;
     a.iso = p->iso ? 1 : 0;
     a.partials = p->d_part0;
-    CK(launch_td(TD_OBJ, a, p->st));
+    CKP(NCS_KERNEL_TD, launch_td(TD_OBJ, a, p->st));
     FwdArgs f{};
     f.img = p->kl ? p->d_tmp : x;
     f.imgT = p->d_tmpT;
@@ -239,8 +298,8 @@ int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, 
     f.b = b;
     f.bg = bg;
     f.partials = p->d_part1;
-    CK(launch_fwd(p->kl ? FWD_RESID_KL : FWD_RESID_L2, f, p->st));
-    CK(launch_finalize(p->d_part1, fwd_num_blocks(p->nd, p->na), p->kl ? 1.0 : 0.5, p->d_part0,
+    CKP(NCS_KERNEL_FWD_RESID, launch_fwd(p->kl ? FWD_RESID_KL : FWD_RESID_L2, f, p->st));
+    CKP(NCS_KERNEL_REDUCE, launch_finalize(p->d_part1, fwd_num_blocks(p->nd, p->na), p->kl ? 1.0 : 0.5, p->d_part0,
                        td_num_blocks(p->N), p->lam, p->d_scal + slot, p->st));
     return NCS_OK;
 }
@@ -394,11 +453,16 @@ int ensure_gamma_p(ncs_plan* p)
 
 void free_plan(ncs_plan* p)
 {
+    for (auto& r : p->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : p->ev_pool) cudaEventDestroy(e);
+    p->recs.clear();
+    p->ev_pool.clear();
     if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
     cudaFree(p->d_ap); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
     cudaFree(p->d_xbar); cudaFree(p->d_xbarT); cudaFree(p->d_r); cudaFree(p->d_tmp); cudaFree(p->d_tmpT);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
     cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s);
+    cudaFree(p->d_gpart); cudaFree(p->d_gcount);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
 }
@@ -484,6 +548,10 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     CKS(dalloc(&p->d_tmp, n));
     CKS(dalloc(&p->d_tmpT, n));
     CKS(dalloc(&p->d_spec, (H + 1) * N));
+    p->gparts = gather_parts(N, na);
+    CKS(dalloc(&p->d_gpart, p->gparts > 1 ? (size_t)p->gparts * n : 1));
+    CKS(dalloc(&p->d_gcount, gather_tiles(N)));
+    CK(cudaMemsetAsync(p->d_gcount, 0, gather_tiles(N) * sizeof(int), p->st));
     CKS(dalloc(&p->d_part0, kMaxPartials));
     CKS(dalloc(&p->d_part1, (size_t)fwd_num_blocks(nd, na)));
     CKS(dalloc(&p->d_scal, 16));
@@ -566,7 +634,9 @@ int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* 
         if (G.exec) { cudaGraphExecDestroy(G.exec); G.exec = nullptr; }
         cudaGraph_t graph;
         CK(cudaStreamBeginCapture(p->st, cudaStreamCaptureModeThreadLocal));
+        p->capturing = true;
         int rc = enq_block(T);
+        p->capturing = false;
         cudaError_t e = cudaStreamEndCapture(p->st, &graph);
         if (rc != NCS_OK) { if (e == cudaSuccess) cudaGraphDestroy(graph); return rc; }
         CK(e);
@@ -823,6 +893,86 @@ int ncs_plan_sizes(const ncs_plan* p, int* N, int* n_angles, int* n_det)
     if (N) *N = p->N;
     if (n_angles) *n_angles = p->na;
     if (n_det) *n_det = p->nd;
+    return NCS_OK;
+}
+
+int ncs_profile_enable(ncs_plan* p, int on)
+{
+    CKS(check_plan(p));
+    CK(cudaSetDevice(p->dev));
+    CK(cudaStreamSynchronize(p->st));
+    for (auto& r : p->recs) { p->ev_pool.push_back(r.a); p->ev_pool.push_back(r.b); }
+    p->recs.clear();
+    p->prof = on != 0;
+    return NCS_OK;
+}
+
+int ncs_profile_read(ncs_plan* p, double* ms, int* launches)
+{
+    CKS(check_plan(p));
+    if (!ms || !launches) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    CK(cudaStreamSynchronize(p->st));
+    for (int k = 0; k < NCS_KERNEL_COUNT; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    int rc = NCS_OK;
+    for (auto& r : p->recs) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { cudaGetLastError(); rc = NCS_ERR_CUDA; }
+        ms[r.cls] += t;
+        launches[r.cls] += 1;
+        p->ev_pool.push_back(r.a);
+        p->ev_pool.push_back(r.b);
+    }
+    p->recs.clear();
+    return rc;
+}
+
+const char* ncs_kernel_name(int k)
+{
+    switch (k) {
+        case NCS_KERNEL_GATHER: return "joseph_gather";
+        case NCS_KERNEL_ROWS_FWD: return "fft_rows_fwd";
+        case NCS_KERNEL_COLS_SOLVE: return "fft_cols_solve";
+        case NCS_KERNEL_ROWS_INV: return "fft_rows_inv";
+        case NCS_KERNEL_TD: return "tv_prox_transpose";
+        case NCS_KERNEL_FWD: return "joseph_fwd";
+        case NCS_KERNEL_FWD_RESID: return "joseph_fwd_resid";
+        case NCS_KERNEL_REDUCE: return "reduce_fp64";
+        default: return "unknown";
+    }
+}
+
+int ncs_plan_nnz(ncs_plan* p, double* nnz)
+{
+    CKS(check_plan(p));
+    if (!nnz) return NCS_ERR_BADARG;
+    if (p->nnz_K < 0.0) {
+        // count the nonzero weights of K exactly as the kernels evaluate them
+        const int N = p->N;
+        double cnt = 0.0;
+        for (int a = 0; a < p->na; ++a) {
+            const AngleParam& q = p->h_ap[a];
+            for (int t = 0; t < p->nd; ++t) {
+                const float tf = (float)t;
+                const float Hr = std::fma(q.Ahi, tf, q.Chi);
+                const float Lr = std::fma(q.Alo, tf, q.Clo);
+                for (int j = 0; j < N; ++j) {
+                    const float jf = (float)j;
+                    const float H = std::fma(q.Bhi, jf, Hr);
+                    const float L = std::fma(q.Blo, jf, Lr);
+                    const float Hi = std::floor(H);
+                    const float fr = (H - Hi) + L;
+                    const float fl = std::floor(fr);
+                    const float w = fr - fl;
+                    const int i0 = (int)(Hi + fl);
+                    if (i0 >= 0 && i0 < N && 1.0f - w != 0.0f) cnt += 1.0;
+                    if (i0 + 1 >= 0 && i0 + 1 < N && w != 0.0f) cnt += 1.0;
+                }
+            }
+        }
+        p->nnz_K = cnt;
+    }
+    *nnz = p->nnz_K;
     return NCS_OK;
 }
 

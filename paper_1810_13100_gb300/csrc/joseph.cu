@@ -8,11 +8,15 @@
 // (Sec. 4.1: divide by 1 + alpha; Sec. 4.2: the closed-form S(u; c)), or
 // reduces the data term of the objective in FP64.
 //
-// K^T (gather, pixel-driven, no atomics): every pixel loops over the angles,
-// finds the <= 2 rays that reach it and evaluates exactly the FP32 weight
-// expression the forward kernel uses, so the two kernels hold the same matrix.
-// The epilogue adds (beta/alpha) D^T v and kappa s (A^T of Sec. 4) and, for
-// PDHG (eq. (PDHG)), applies the primal update.
+// K^T (gather, no atomics on data): a block owns a 32 x 32 pixel tile and a
+// slice of the angles.  Each warp takes whole angles and walks the (ray, line)
+// pairs that cross the tile, evaluating exactly the FP32 crossing and weight
+// expression of the forward kernel (so the two kernels hold the same matrix),
+// and accumulates into its own shared-memory tile.  The warp tiles are summed
+// in a fixed order; when the angles are split over several blocks, the last
+// block of a tile (an arrival counter) sums the slices in slice order.  The
+// epilogue adds (beta/alpha) D^T v and kappa s (A^T of Sec. 4) and, for PDHG
+// (eq. (PDHG)), applies the primal update.
 #include "ncs_internal.cuh"
 
 namespace ncs {
@@ -132,72 +136,144 @@ k_fwd(FwdArgs g)
     }
 }
 
-constexpr int GB_X = 32, GB_Y = 8;     // gather block: 32 x 8 pixels
-constexpr int GCHUNK = 256;            // angles staged in shared memory at a time
+constexpr int GT = 32;     // gather tile side (pixels)
+constexpr int GW = 8;      // warps per gather block
 
-template <int MODE>
-__global__ void __launch_bounds__(GB_X * GB_Y)
-k_gather(GatherArgs g)
+// All (ray, line) pairs of one angle that reach a 32 x 32 tile, accumulated by
+// one warp into its private shared-memory tile A.  ROW: the angle steps over
+// image rows (line = row, window along columns); otherwise over columns.  o0 is
+// the tile's first index along the interpolation axis, l0 its first line.
+// Lanes take consecutive rays of a line, so the loads of u coalesce; a pixel
+// receives at most one "right" weight (1 - w) and one "left" weight w per
+// angle, so the two phases never write one address twice.
+template <bool ROW>
+__device__ __forceinline__ void gather_angle(const AngleParam& p, const float* __restrict__ ua, int n_det, int N,
+                                             int o0, int l0, int lane, float (*A)[GT + 1])
 {
-    __shared__ AngleParam sap[GCHUNK];
-    const int N = g.N;
-    const int i = blockIdx.x * GB_X + threadIdx.x;
-    const int j = blockIdx.y * GB_Y + threadIdx.y;
-    const bool inb = (i < N) && (j < N);
-    const int tid = threadIdx.y * GB_X + threadIdx.x;
-    const float fi_ = (float)i, fj_ = (float)j;
-    float acc = 0.0f;
-    for (int a0 = 0; a0 < g.n_ang; a0 += GCHUNK) {
-        const int na = min(GCHUNK, g.n_ang - a0);
-        __syncthreads();
-        for (int q = tid; q < na; q += GB_X * GB_Y) sap[q] = g.ap[a0 + q];
-        __syncthreads();
-        if (!inb) continue;
-        for (int aa = 0; aa < na; ++aa) {
-            const AngleParam p = sap[aa];
-            // own: the index interpolated along; other: the stepping index
-            const float own = p.row ? fi_ : fj_;
-            const float other = p.row ? fj_ : fi_;
-            const float Hq = fmaf(p.Bhi, other, p.Chi);                 // exact
-            const float base = Hq + fmaf(p.Blo, other, p.Clo);             // ~ B q + C
-            const int tc = (int)rintf((own - base) * p.invA);
-            const float* __restrict__ ua = g.u + (size_t)(a0 + aa) * g.n_det;
-            float acc_a = 0.0f;
-#pragma unroll
-            for (int q = -1; q <= 1; ++q) {
-                const int t = tc + q;
-                if (t >= 0 && t < g.n_det) {
-                    const float tf = (float)t;
-                    float k0f;
-                    const float w = split_weight(fmaf(p.Ahi, tf, Hq), fmaf(p.Blo, other, fmaf(p.Alo, tf, p.Clo)), k0f);
-                    const float wt = (k0f == own) ? (1.0f - w) : ((k0f + 1.0f == own) ? w : 0.0f);
-                    if (wt != 0.0f) acc_a = fmaf(wt, __ldg(ua + t), acc_a);
-                }
-            }
-            acc = fmaf(p.W, acc_a, acc);
+    const float lf0 = (float)l0;
+    const float base0 = fmaf(p.Bhi, lf0, p.Chi) + fmaf(p.Blo, lf0, p.Clo);      // ~ B l0 + C
+    const float ta = ((float)o0 - 1.0f - base0) * p.invA;
+    const float tb = ((float)o0 + (float)GT - base0) * p.invA;
+    const float T0 = fminf(ta, tb) - 1e-3f;                                      // first ray of line l0
+    const float dT = -(p.Bhi + p.Blo) * p.invA;                                  // shift per line
+    const int RPL = (int)ceilf((float)(GT + 1) * fabsf(p.invA) + 2e-3f) + 1;     // rays per line (>= 25)
+    int lo = lane / RPL, r = lane - lo * RPL;
+    for (int it = 0; it < RPL; ++it) {
+        const int line = l0 + lo;
+        const int t = (int)floorf(fmaf((float)lo, dT, T0)) + r;
+        float vR = 0.0f, vL = 0.0f;
+        int kk = -2;
+        if (line < N && t >= 0 && t < n_det) {
+            const float tf = (float)t, lf = (float)line;
+            float k0f;
+            const float w = split_weight(fmaf(p.Ahi, tf, fmaf(p.Bhi, lf, p.Chi)),
+                                         fmaf(p.Blo, lf, fmaf(p.Alo, tf, p.Clo)), k0f);
+            kk = (int)k0f - o0;
+            const float Wu = p.W * __ldg(ua + t);
+            vR = fmaf(-w, Wu, Wu);
+            vL = w * Wu;
+        }
+        if (kk >= 0 && kk < GT) {
+            if (ROW) A[lo][kk] += vR;
+            else A[kk][lo] += vR;
+        }
+        __syncwarp();
+        if (kk >= -1 && kk < GT - 1) {
+            if (ROW) A[lo][kk + 1] += vL;
+            else A[kk + 1][lo] += vL;
+        }
+        __syncwarp();
+        r += 32;
+        while (r >= RPL) {
+            r -= RPL;
+            ++lo;
         }
     }
-    if (!inb) return;
-    const size_t pix = (size_t)j * N + i;
-    float r = acc;
-    if (g.v) {
-        const float* vh = g.v;
-        const float* vv = g.v + (size_t)N * N;
-        float dt = 0.0f;
-        if (i < N - 1) dt += vh[pix];
-        if (i >= 1) dt -= vh[pix - 1];
-        if (j < N - 1) dt += vv[pix];
-        if (j >= 1) dt -= vv[pix - N];
-        r = fmaf(g.dscale, dt, r);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(GT * GW)
+k_gather(GatherArgs g)
+{
+    __shared__ float acc[GW][GT][GT + 1];
+    __shared__ int s_last;
+    const int N = g.N;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
+    float (*A)[GT + 1] = acc[wid];
+    for (int rr = 0; rr < GT; ++rr) A[rr][lane] = 0.0f;
+    __syncwarp();
+    // this block's slice of the angles; warps take whole angles round robin
+    const int P = gridDim.z, part = blockIdx.z;
+    const int a_beg = (int)(((long long)g.n_ang * part) / P);
+    const int a_end = (int)(((long long)g.n_ang * (part + 1)) / P);
+    for (int a = a_beg + wid; a < a_end; a += GW) {
+        const AngleParam p = g.ap[a];
+        const float* __restrict__ ua = g.u + (size_t)a * g.n_det;
+        if (p.row) gather_angle<true>(p, ua, g.n_det, N, i0, j0, lane, A);
+        else gather_angle<false>(p, ua, g.n_det, N, j0, i0, lane, A);
     }
-    if (g.s) r = fmaf(g.kappa, g.s[pix], r);
-    if (MODE == GATHER_R) {
-        g.r[pix] = r;
-    } else {
-        const float x = g.x[pix];
-        const float x1 = fmaf(-g.inv_gamma, r, x);
-        g.x[pix] = x1;
-        g.xbar[pix] = 2.0f * x1 - x;
+    __syncthreads();
+    // sum the warp tiles in a fixed order; thread -> pixels (q*8 + wid, lane)
+    float tot[GT / GW];
+#pragma unroll
+    for (int q = 0; q < GT / GW; ++q) {
+        const int rr = q * GW + wid;
+        float sum = 0.0f;
+#pragma unroll
+        for (int w = 0; w < GW; ++w) sum += acc[w][rr][lane];
+        tot[q] = sum;
+    }
+    if (P > 1) {
+        // angle slices of this tile: the last block to arrive sums them in slice order
+        const size_t NN = (size_t)N * N;
+#pragma unroll
+        for (int q = 0; q < GT / GW; ++q) {
+            const int j = j0 + q * GW + wid, i = i0 + lane;
+            if (j < N && i < N) g.part[(size_t)part * NN + (size_t)j * N + i] = tot[q];
+        }
+        __threadfence();
+        __syncthreads();
+        const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+        if (tid == 0) s_last = (atomicAdd(&g.counters[tile], 1) == P - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+#pragma unroll
+        for (int q = 0; q < GT / GW; ++q) {
+            const int j = j0 + q * GW + wid, i = i0 + lane;
+            float sum = 0.0f;
+            if (j < N && i < N)
+                for (int pp = 0; pp < P; ++pp) sum += __ldcg(g.part + (size_t)pp * NN + (size_t)j * N + i);
+            tot[q] = sum;
+        }
+        if (tid == 0) g.counters[tile] = 0;
+    }
+#pragma unroll
+    for (int q = 0; q < GT / GW; ++q) {
+        const int j = j0 + q * GW + wid, i = i0 + lane;
+        if (j >= N || i >= N) continue;
+        const size_t pix = (size_t)j * N + i;
+        float r = tot[q];
+        if (g.v) {
+            const float* vh = g.v;
+            const float* vv = g.v + (size_t)N * N;
+            float dt = 0.0f;
+            if (i < N - 1) dt += vh[pix];
+            if (i >= 1) dt -= vh[pix - 1];
+            if (j < N - 1) dt += vv[pix];
+            if (j >= 1) dt -= vv[pix - N];
+            r = fmaf(g.dscale, dt, r);
+        }
+        if (g.s) r = fmaf(g.kappa, g.s[pix], r);
+        if (MODE == GATHER_R) {
+            g.r[pix] = r;
+        } else {
+            const float x = g.x[pix];
+            const float x1 = fmaf(-g.inv_gamma, r, x);
+            g.x[pix] = x1;
+            g.xbar[pix] = 2.0f * x1 - x;
+        }
     }
 }
 
@@ -222,9 +298,28 @@ cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+size_t gather_tiles(int N)
+{
+    const size_t b = (size_t)(N + GT - 1) / GT;
+    return b * b;
+}
+
+int gather_parts(int N, int n_ang)
+{
+    // about 2048 blocks (several waves of 152 SMs x 6 blocks); at most 64 slices
+    const long long tiles = (long long)gather_tiles(N);
+    long long p = (2048 + tiles - 1) / tiles;
+    if (p > 64) p = 64;
+    if (p > n_ang) p = n_ang;
+    if (p < 1) p = 1;
+    return (int)p;
+}
+
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
 {
-    dim3 grid((a.N + GB_X - 1) / GB_X, (a.N + GB_Y - 1) / GB_Y), block(GB_X, GB_Y);
+    const int b = (a.N + GT - 1) / GT;
+    dim3 grid(b, b, a.parts), block(GT * GW);
+    if (a.parts < 1 || (a.parts > 1 && (!a.part || !a.counters))) return cudaErrorInvalidValue;
     if (mode == GATHER_R) k_gather<GATHER_R><<<grid, block, 0, st>>>(a);
     else if (mode == GATHER_PDHG) k_gather<GATHER_PDHG><<<grid, block, 0, st>>>(a);
     else return cudaErrorInvalidValue;

@@ -57,6 +57,9 @@ struct GatherArgs {
     const float* u;
     const AngleParam* ap;
     int N, n_ang, n_det;
+    int parts;           // angle slices per tile (gridDim.z)
+    float* part;         // scratch: parts * N * N partial sums (parts > 1)
+    int* counters;       // scratch: one arrival counter per 32 x 32 tile, zero between launches
     const float* v;      // 2*N*N or nullptr
     float dscale;
     const float* s;      // N*N or nullptr
@@ -99,6 +102,8 @@ struct RadixPlan {
 cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st);
 int fwd_num_blocks(int n_det, int n_ang);
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st);
+int gather_parts(int N, int n_ang);          // angle slices the gather uses for this size
+size_t gather_tiles(int N);                  // 32 x 32 tiles of an N x N image
 cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st);
 int td_num_blocks(int N);
 
