@@ -207,6 +207,32 @@ const char* ncs_kernel_name(int kernel_class);
  * 2 * nnz flops).  Computed once per plan. */
 int ncs_plan_nnz(ncs_plan* plan, double* nnz);
 
+/* ---- Backprojection without device allocation ---- */
+
+/* Largest sizes ncs_apply_KT_static accepts. */
+#define NCS_STATIC_MAX_N       512
+#define NCS_STATIC_MAX_ANGLES  2048
+
+/* x = K^T y for the geometry and an N x N image, without a plan and without
+ * allocating any device memory.  The paper has no counterpart: this is for
+ * callers that cannot allocate device memory when they need a backprojection
+ * (a process whose memory pool owns the whole GPU, a framework whose allocator
+ * must not be bypassed, code that reserved all memory up front).  It runs the
+ * same tiled gather kernel as ncs_apply_KT with its working memory (angle
+ * table, per-tile counters, partial sums of the angle slices) taken from one
+ * file-scope device array of about 4.1 MiB that every GPU loading the library
+ * holds until the process exits.  y: n_angles*n_det, x: N*N, both device
+ * pointers owned by the caller; cuda_stream: a cudaStream_t or NULL (legacy
+ * default stream).  Asynchronous, apart from the host-to-device copy of the
+ * angle table, which returns once the table is staged.
+ * Sizes N > NCS_STATIC_MAX_N or n_angles > NCS_STATIC_MAX_ANGLES return
+ * NCS_ERR_UNSUPPORTED; N < 8, null pointers or an empty geometry return
+ * NCS_ERR_BADARG.  All calls share the array: calls whose work overlaps on the
+ * GPU (several streams or host threads) race and must be serialised by the
+ * caller.  The first call on a device looks up the array's address with that
+ * device current; make it before any stream capture. */
+int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float* y, float* x, void* cuda_stream);
+
 /* Human-readable name of a status code (static string). */
 const char* ncs_status_string(int status);
 

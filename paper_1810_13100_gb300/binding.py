@@ -82,6 +82,7 @@ SIGNATURES = [
     ("ncs_profile_read", _I, [_P, _DP, _IP]),
     ("ncs_kernel_name", ctypes.c_char_p, [_I]),
     ("ncs_plan_nnz", _I, [_P, _DP]),
+    ("ncs_apply_KT_static", _I, [ctypes.POINTER(Geometry), _I, _P, _P, _P]),
 ]
 
 NCS_KERNEL_COUNT = 8
