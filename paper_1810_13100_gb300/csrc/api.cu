@@ -45,7 +45,9 @@ struct ncs_plan {
     std::vector<double> mu;          // eigenvalues of M, N x N, [p][q]
     float* d_invmu = nullptr;        // 1/(N^2 mu), [q][p], q = 0..N/2
     float* d_mu = nullptr;           // mu/N^2 (power iteration start only)
-    float *d_xbar = nullptr, *d_xbarT = nullptr, *d_r = nullptr, *d_tmp = nullptr, *d_tmpT = nullptr;
+    float *d_xbar = nullptr, *d_r = nullptr, *d_tmp = nullptr;
+    // pair images (see PAIR_PAD) of xbar / xbar^T and of a scratch image / its transpose
+    float2 *d_xb2 = nullptr, *d_xbT2 = nullptr, *d_tmp2 = nullptr, *d_tmpT2 = nullptr;
     float2* d_spec = nullptr;
     double *d_part0 = nullptr, *d_part1 = nullptr, *d_scal = nullptr, *h_pin = nullptr;
     float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
@@ -157,21 +159,33 @@ int dalloc(T** p, size_t count)
 
 // ---------------------------------------------------------------- enqueue helpers
 
-int enq_transpose(ncs_plan* p, const float* x, float* xT)
+size_t pair_elems(const ncs_plan* p) { return (size_t)p->N * pair_pitch(p->N); }
+
+// allocate a pair image with its zero border
+int alloc_pair(ncs_plan* p, float2** out)
+{
+    CKS(dalloc(out, pair_elems(p)));
+    CK(cudaMemsetAsync(*out, 0, pair_elems(p) * sizeof(float2), p->st));
+    return NCS_OK;
+}
+
+// pair images of x and x^T
+int enq_pairs(ncs_plan* p, const float* x, float2* x2, float2* xT2)
 {
     TdArgs a{};
     a.x = x;
-    a.xT = xT;
+    a.x2 = x2;
+    a.xT2 = xT2;
     a.N = p->N;
     CKP(NCS_KERNEL_TD, launch_td(TD_TRANSPOSE, a, p->st));
     return NCS_OK;
 }
 
-int enq_K(ncs_plan* p, const float* x, const float* xT, float* y)
+int enq_K(ncs_plan* p, const float2* x2, const float2* xT2, float* y)
 {
     FwdArgs f{};
-    f.img = x;
-    f.imgT = xT;
+    f.img2 = x2;
+    f.imgT2 = xT2;
     f.ap = p->d_ap;
     f.N = p->N;
     f.n_ang = p->na;
@@ -219,7 +233,8 @@ int enq_td_prox(ncs_plan* p, float* v, float* s)
 {
     TdArgs a{};
     a.x = p->d_xbar;
-    a.xT = p->d_xbarT;
+    a.x2 = p->d_xb2;
+    a.xT2 = p->d_xbT2;
     a.v = v;
     a.s = p->nonneg ? s : nullptr;
     a.N = p->N;
@@ -234,8 +249,8 @@ int enq_td_prox(ncs_plan* p, float* v, float* s)
 int enq_fwd_prox(ncs_plan* p, float* u, const float* b, const float* bg)
 {
     FwdArgs f{};
-    f.img = p->d_xbar;
-    f.imgT = p->d_xbarT;
+    f.img2 = p->d_xb2;
+    f.imgT2 = p->d_xbT2;
     f.ap = p->d_ap;
     f.N = p->N;
     f.n_ang = p->na;
@@ -281,16 +296,16 @@ int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, 
 {
     TdArgs a{};
     a.x = x;
-    a.xT = p->d_tmpT;
-    a.xc = p->kl ? p->d_tmp : nullptr;
+    a.x2 = p->d_tmp2;
+    a.xT2 = p->d_tmpT2;
     a.clamp = p->kl ? 1 : 0;
     a.N = p->N;
     a.iso = p->iso ? 1 : 0;
     a.partials = p->d_part0;
     CKP(NCS_KERNEL_TD, launch_td(TD_OBJ, a, p->st));
     FwdArgs f{};
-    f.img = p->kl ? p->d_tmp : x;
-    f.imgT = p->d_tmpT;
+    f.img2 = p->d_tmp2;
+    f.imgT2 = p->d_tmpT2;
     f.ap = p->d_ap;
     f.N = p->N;
     f.n_ang = p->na;
@@ -318,36 +333,36 @@ int read_scalars(ncs_plan* p, int count)
     return NCS_OK;
 }
 
-// w = A^T A x (x, xT: scratch buffers provided by the caller)
-int enq_AtA(ncs_plan* p, const float* x, float* xT, float* yk, float* vb, float* sb, float* w)
+// w = A^T A x (yk, vb, sb: scratch buffers provided by the caller)
+int enq_AtA(ncs_plan* p, const float* x, float* yk, float* vb, float* sb, float* w)
 {
     TdArgs a{};
     a.x = x;
-    a.xT = xT;
+    a.x2 = p->d_tmp2;
+    a.xT2 = p->d_tmpT2;
     a.v = vb;
     a.s = p->nonneg ? sb : nullptr;
     a.N = p->N;
     a.beta = (float)(p->beta / p->alpha);
     a.ak = (float)p->kappa;
     CK(launch_td(TD_APPLY, a, p->st));
-    CKS(enq_K(p, x, xT, yk));
+    CKS(enq_K(p, p->d_tmp2, p->d_tmpT2, yk));
     CKS(enq_gather(p, GATHER_R, yk, vb, (float)(p->beta / p->alpha), p->nonneg ? sb : nullptr, (float)p->kappa,
                    w, nullptr, nullptr, 0.f, p->na));
     return NCS_OK;
 }
 
 struct PowerBufs {
-    float *x = nullptr, *xT = nullptr, *w = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *s = nullptr;
+    float *x = nullptr, *w = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *s = nullptr;
     ~PowerBufs()
     {
-        cudaFree(x); cudaFree(xT); cudaFree(w); cudaFree(y); cudaFree(u); cudaFree(v); cudaFree(s);
+        cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(u); cudaFree(v); cudaFree(s);
     }
 };
 
 int alloc_power(ncs_plan* p, PowerBufs& B)
 {
     CKS(dalloc(&B.x, NN(p)));
-    CKS(dalloc(&B.xT, NN(p)));
     CKS(dalloc(&B.w, NN(p)));
     CKS(dalloc(&B.y, NN(p)));
     CKS(dalloc(&B.u, MM(p)));
@@ -374,7 +389,7 @@ int power_rho(ncs_plan* p, double* rho_out)
     double xMx = p->h_pin[3];
     double rho = 0.0, rho_old = std::numeric_limits<double>::quiet_NaN();
     for (int it = 1; it <= p->opt.power_max_iter; ++it) {
-        CKS(enq_AtA(p, B.x, B.xT, B.u, B.v, B.s, B.w));
+        CKS(enq_AtA(p, B.x, B.u, B.v, B.s, B.w));
         CK(launch_scale(B.w, n, (float)p->alpha, p->st));
         CKS(enq_dot(p, B.x, B.w, n, 0));
         CKS(enq_solve(p, B.w, p->d_invmu, 1, nullptr, nullptr, B.y));
@@ -403,7 +418,7 @@ int power_lmax(ncs_plan* p, double* out)
     CK(launch_scale_by_rsqrt(B.x, B.x, n, p->d_scal + 0, p->st));
     double lm = 0.0, lm_old = 0.0;
     for (int it = 1; it <= p->opt.power_max_iter; ++it) {
-        CKS(enq_AtA(p, B.x, B.xT, B.u, B.v, B.s, B.w));
+        CKS(enq_AtA(p, B.x, B.u, B.v, B.s, B.w));
         CKS(enq_dot(p, B.x, B.w, n, 0));
         CKS(enq_dot(p, B.x, B.x, n, 1));
         CKS(enq_dot(p, B.w, B.w, n, 2));
@@ -459,7 +474,8 @@ void free_plan(ncs_plan* p)
     p->ev_pool.clear();
     if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
     cudaFree(p->d_ap); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
-    cudaFree(p->d_xbar); cudaFree(p->d_xbarT); cudaFree(p->d_r); cudaFree(p->d_tmp); cudaFree(p->d_tmpT);
+    cudaFree(p->d_xbar); cudaFree(p->d_r); cudaFree(p->d_tmp);
+    cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
     cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s);
     cudaFree(p->d_gpart); cudaFree(p->d_gcount);
@@ -543,10 +559,12 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     CKS(dalloc(&p->d_invmu, (H + 1) * N));
     CKS(dalloc(&p->d_mu, (H + 1) * N));
     CKS(dalloc(&p->d_xbar, n));
-    CKS(dalloc(&p->d_xbarT, n));
     CKS(dalloc(&p->d_r, n));
     CKS(dalloc(&p->d_tmp, n));
-    CKS(dalloc(&p->d_tmpT, n));
+    CKS(alloc_pair(p, &p->d_xb2));
+    CKS(alloc_pair(p, &p->d_xbT2));
+    CKS(alloc_pair(p, &p->d_tmp2));
+    CKS(alloc_pair(p, &p->d_tmpT2));
     CKS(dalloc(&p->d_spec, (H + 1) * N));
     p->gparts = gather_parts(N, na);
     CKS(dalloc(&p->d_gpart, p->gparts > 1 ? (size_t)p->gparts * n : 1));
@@ -567,7 +585,8 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
         CK(cudaMemcpyAsync(ones, h1.data(), n * sizeof(float), cudaMemcpyHostToDevice, p->st));
         float* y = nullptr;
         CKS(dalloc(&y, MM(p)));
-        int rc = enq_K(p, ones, ones, y);
+        int rc = enq_pairs(p, ones, p->d_tmp2, p->d_tmpT2);
+        if (rc == NCS_OK) rc = enq_K(p, p->d_tmp2, p->d_tmpT2, y);
         if (rc == NCS_OK) rc = enq_dot(p, y, y, MM(p), 0);
         if (rc == NCS_OK) rc = read_scalars(p, 1);
         cudaFree(y);
@@ -824,8 +843,8 @@ int ncs_apply_K(ncs_plan* p, const float* x, float* y)
     CKS(check_plan(p));
     if (!x || !y) return NCS_ERR_BADARG;
     CK(cudaSetDevice(p->dev));
-    CKS(enq_transpose(p, x, p->d_tmpT));
-    return enq_K(p, x, p->d_tmpT, y);
+    CKS(enq_pairs(p, x, p->d_tmp2, p->d_tmpT2));
+    return enq_K(p, p->d_tmp2, p->d_tmpT2, y);
 }
 
 int ncs_apply_KT(ncs_plan* p, const float* y, float* x)
@@ -955,11 +974,10 @@ int ncs_plan_nnz(ncs_plan* p, double* nnz)
             for (int t = 0; t < p->nd; ++t) {
                 const float tf = (float)t;
                 const float Hr = std::fma(q.Ahi, tf, q.Chi);
-                const float Lr = std::fma(q.Alo, tf, q.Clo);
                 for (int j = 0; j < N; ++j) {
                     const float jf = (float)j;
                     const float H = std::fma(q.Bhi, jf, Hr);
-                    const float L = std::fma(q.Blo, jf, Lr);
+                    const float L = std::fma(q.Alo, tf, std::fma(q.Blo, jf, q.Clo));
                     const float Hi = std::floor(H);
                     const float fr = (H - Hi) + L;
                     const float fl = std::floor(fr);

@@ -3,7 +3,7 @@
 // K (forward, ray-driven): one thread per (angle, bin, row segment); the ray
 // is stepped over the rows of x (row-branch angles) or of x^T (column-branch
 // angles), so a warp of 32 consecutive bins always reads one contiguous row
-// segment.  Partial sums of the segments are combined in shared memory in a
+// segment; both taps of a step come from one 8-byte load of the pair image.  Partial sums of the segments are combined in shared memory in a
 // fixed order, then a fused epilogue applies prox_{alpha g*} to the data dual
 // (Sec. 4.1: divide by 1 + alpha; Sec. 4.2: the closed-form S(u; c)), or
 // reduces the data term of the objective in FP64.
@@ -27,7 +27,7 @@ constexpr int FWD_TB = 64;    // bins per block
 constexpr int FWD_SEG = 4;    // row segments per ray
 
 // Integer index k0 and interpolation weight w of the crossing f = H + L, where
-// H = A_hi t + B_hi q + C_hi is exact and L = B_lo q + (A_lo t + C_lo) is small.
+// H = A_hi t + B_hi q + C_hi is exact and L = A_lo t + (B_lo q + C_lo) is small.
 // The one expression both kernels use, so they hold the same FP32 matrix.
 __device__ __forceinline__ float split_weight(float H, float L, float& k0)
 {
@@ -56,19 +56,20 @@ k_fwd(FwdArgs g)
     __shared__ double dred[FWD_TB];
     const int a = blockIdx.y;
     const AngleParam p = g.ap[a];
-    const float* __restrict__ im = p.row ? g.img : g.imgT;
+    const float2* __restrict__ im2 = p.row ? g.img2 : g.imgT2;
+    const int pitch = pair_pitch(g.N);
     const int N = g.N;
     const int t = blockIdx.x * FWD_TB + threadIdx.x;
     float acc = 0.0f;
     if (t < g.n_det) {
         const float ft = (float)t;
         const float Hr = fmaf(p.Ahi, ft, p.Chi);    // exact
-        const float Lr = fmaf(p.Alo, ft, p.Clo);
         const float B = p.Bhi + p.Blo;
         // Rows where the ray can touch the image: f in [-1, N).  Found in FP32
-        // with a 2-row margin; the per-step bounds checks stay, so the range
-        // only skips steps whose contribution is zero.
-        const float f0 = Hr + Lr;
+        // with a 2-row margin (|B| <= 1, so f stays in (-4, N + 3) on every
+        // processed row and the pair image's zero border absorbs the steps
+        // outside the image).
+        const float f0 = Hr + fmaf(p.Alo, ft, p.Clo);
         int jlo = 0, jhi = N;
         if (fabsf(B) > 1e-6f) {
             float j1 = (-1.0f - f0) / B, j2 = ((float)N - f0) / B;
@@ -87,13 +88,11 @@ k_fwd(FwdArgs g)
         for (int j = js; j < je; ++j) {
             const float jf = (float)j;
             float k0f;
-            const float w = split_weight(fmaf(p.Bhi, jf, Hr), fmaf(p.Blo, jf, Lr), k0f);
+            const float w = split_weight(fmaf(p.Bhi, jf, Hr), fmaf(p.Alo, ft, fmaf(p.Blo, jf, p.Clo)), k0f);
             const int i0 = (int)k0f;
-            const float* __restrict__ row = im + (size_t)j * N;
-            const float x0 = (i0 >= 0 && i0 < N) ? __ldg(row + i0) : 0.0f;
-            const float x1 = (i0 >= -1 && i0 + 1 < N) ? __ldg(row + i0 + 1) : 0.0f;
-            acc = fmaf(1.0f - w, x0, acc);
-            acc = fmaf(w, x1, acc);
+            const float2 xv = __ldg(im2 + (size_t)j * pitch + PAIR_PAD + i0);
+            acc = fmaf(1.0f - w, xv.x, acc);
+            acc = fmaf(w, xv.y, acc);
         }
     }
     red[threadIdx.y][threadIdx.x] = acc;
@@ -139,46 +138,47 @@ k_fwd(FwdArgs g)
 constexpr int GT = 32;     // gather tile side (pixels)
 constexpr int GW = 8;      // warps per gather block
 
+// Per-line quantities of one angle for a warp: first ray tl, the exact
+// B_hi q + C_hi, the remainder B_lo q + C_lo and the line index q.
+struct LineEntry {
+    int tl;
+    float Hq, Lq;
+    int line;
+};
+
 // All (ray, line) pairs of one angle that reach a 32 x 32 tile, accumulated by
 // one warp into its private shared-memory tile A.  ROW: the angle steps over
 // image rows (line = row, window along columns); otherwise over columns.  o0 is
 // the tile's first index along the interpolation axis, l0 its first line.
 // Lanes take consecutive rays of a line, so the loads of u coalesce; a pixel
 // receives at most one "right" weight (1 - w) and one "left" weight w per
-// angle, so the two phases never write one address twice.
-template <bool ROW>
-__device__ __forceinline__ void gather_angle(const AngleParam& p, const float* __restrict__ ua, int n_det, int N,
-                                             int o0, int l0, int lane, float (*A)[GT + 1])
+// angle, so the two phases never write one address twice.  CHECK: test the
+// line and ray ranges per pair (edge tiles and rays beyond the detector).
+template <bool ROW, bool CHECK>
+__device__ __forceinline__ void gather_pairs(const AngleParam& p, const float* __restrict__ ua, int n_det, int N,
+                                             int o0, int RPL, int lane, const LineEntry* tab, float (*A)[GT + 1])
 {
-    const float lf0 = (float)l0;
-    const float base0 = fmaf(p.Bhi, lf0, p.Chi) + fmaf(p.Blo, lf0, p.Clo);      // ~ B l0 + C
-    const float ta = ((float)o0 - 1.0f - base0) * p.invA;
-    const float tb = ((float)o0 + (float)GT - base0) * p.invA;
-    const float T0 = fminf(ta, tb) - 1e-3f;                                      // first ray of line l0
-    const float dT = -(p.Bhi + p.Blo) * p.invA;                                  // shift per line
-    const int RPL = (int)ceilf((float)(GT + 1) * fabsf(p.invA) + 2e-3f) + 1;     // rays per line (>= 25)
     int lo = lane / RPL, r = lane - lo * RPL;
     for (int it = 0; it < RPL; ++it) {
-        const int line = l0 + lo;
-        const int t = (int)floorf(fmaf((float)lo, dT, T0)) + r;
+        const LineEntry e = tab[lo];
+        const int t = e.tl + r;
         float vR = 0.0f, vL = 0.0f;
         int kk = -2;
-        if (line < N && t >= 0 && t < n_det) {
-            const float tf = (float)t, lf = (float)line;
+        if (!CHECK || (e.line < N && (unsigned)t < (unsigned)n_det)) {
+            const float tf = (float)t;
             float k0f;
-            const float w = split_weight(fmaf(p.Ahi, tf, fmaf(p.Bhi, lf, p.Chi)),
-                                         fmaf(p.Blo, lf, fmaf(p.Alo, tf, p.Clo)), k0f);
+            const float w = split_weight(fmaf(p.Ahi, tf, e.Hq), fmaf(p.Alo, tf, e.Lq), k0f);
             kk = (int)k0f - o0;
             const float Wu = p.W * __ldg(ua + t);
             vR = fmaf(-w, Wu, Wu);
             vL = w * Wu;
         }
-        if (kk >= 0 && kk < GT) {
+        if ((unsigned)kk < (unsigned)GT) {
             if (ROW) A[lo][kk] += vR;
             else A[kk][lo] += vR;
         }
         __syncwarp();
-        if (kk >= -1 && kk < GT - 1) {
+        if ((unsigned)(kk + 1) < (unsigned)GT) {
             if (ROW) A[lo][kk + 1] += vL;
             else A[kk + 1][lo] += vL;
         }
@@ -191,11 +191,43 @@ __device__ __forceinline__ void gather_angle(const AngleParam& p, const float* _
     }
 }
 
+template <bool ROW>
+__device__ __forceinline__ void gather_angle(const AngleParam& p, const float* __restrict__ ua, int n_det, int N,
+                                             int o0, int l0, int lane, LineEntry* tab, float (*A)[GT + 1])
+{
+    const float lf0 = (float)l0;
+    const float base0 = fmaf(p.Bhi, lf0, p.Chi) + fmaf(p.Blo, lf0, p.Clo);      // ~ B l0 + C
+    const float ta = ((float)o0 - 1.0f - base0) * p.invA;
+    const float tb = ((float)o0 + (float)GT - base0) * p.invA;
+    const float T0 = fminf(ta, tb) - 1e-3f;                                      // first ray of line l0
+    const float dT = -(p.Bhi + p.Blo) * p.invA;                                  // shift per line
+    const int RPL = (int)ceilf((float)(GT + 1) * fabsf(p.invA) + 2e-3f) + 1;     // rays per line
+    {
+        const int line = l0 + lane;
+        const float lf = (float)line;
+        LineEntry e;
+        e.tl = (int)floorf(fmaf((float)lane, dT, T0));
+        e.Hq = fmaf(p.Bhi, lf, p.Chi);                                           // exact
+        e.Lq = fmaf(p.Blo, lf, p.Clo);
+        e.line = line;
+        tab[lane] = e;
+    }
+    __syncwarp();
+    // interior: every line inside the image and every ray on the detector
+    const int t_first = min(tab[0].tl, tab[GT - 1].tl);
+    const int t_last = max(tab[0].tl, tab[GT - 1].tl) + RPL - 1;
+    const bool inside = (l0 + GT <= N) && t_first >= 0 && t_last < n_det;
+    if (inside) gather_pairs<ROW, false>(p, ua, n_det, N, o0, RPL, lane, tab, A);
+    else gather_pairs<ROW, true>(p, ua, n_det, N, o0, RPL, lane, tab, A);
+    __syncwarp();
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(GT * GW)
 k_gather(GatherArgs g)
 {
     __shared__ float acc[GW][GT][GT + 1];
+    __shared__ LineEntry lines[GW][GT];
     __shared__ int s_last;
     const int N = g.N;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -210,8 +242,8 @@ k_gather(GatherArgs g)
     for (int a = a_beg + wid; a < a_end; a += GW) {
         const AngleParam p = g.ap[a];
         const float* __restrict__ ua = g.u + (size_t)a * g.n_det;
-        if (p.row) gather_angle<true>(p, ua, g.n_det, N, i0, j0, lane, A);
-        else gather_angle<false>(p, ua, g.n_det, N, j0, i0, lane, A);
+        if (p.row) gather_angle<true>(p, ua, g.n_det, N, i0, j0, lane, lines[wid], A);
+        else gather_angle<false>(p, ua, g.n_det, N, j0, i0, lane, lines[wid], A);
     }
     __syncthreads();
     // sum the warp tiles in a fixed order; thread -> pixels (q*8 + wid, lane)

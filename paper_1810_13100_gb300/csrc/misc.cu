@@ -9,6 +9,8 @@
 //             s+ = min(0, s + alpha kappa xbar) (Sec. 4.2 nonnegativity row)
 //   TD_APPLY: v = c D x, s = kappa x (the D and I rows of A)
 //   TD_OBJ  : TV(x) partial sums in FP64 (optionally at max(x, 0))
+// Every mode also writes the pair images of x and x^T that the forward
+// projector reads (see PAIR_PAD), from the same shared-memory tile.
 #include "ncs_internal.cuh"
 
 namespace ncs {
@@ -74,15 +76,31 @@ k_td(TdArgs g)
         } else if (MODE == TD_OBJ) {
             const double a = dh, b = dv;
             tv += g.iso ? sqrt(a * a + b * b) : fabs(a) + fabs(b);
-            if (g.clamp && g.xc) g.xc[pix] = xv;
         }
     }
-    // transposed store: xT[i][j] = x[j][i]
-    if (g.xT) {
+    // pair images: x2 row j entry i = (x[j][i], x[j][i+1]); xT2 row i entry j = (x[j][i], x[j+1][i])
+    const int P = pair_pitch(N);
+    if (g.x2) {
+#pragma unroll
+        for (int q = 0; q < TT / TR; ++q) {
+            const int r = ty + q * TR, c = tx;
+            const int gj = j0 + r, gi = i0 + c;
+            if (gj < N && gi < N) {
+                float2* rowp = g.x2 + (size_t)gj * P + PAIR_PAD;
+                rowp[gi] = make_float2(tile[r][c], tile[r][c + 1]);
+                if (gi == 0) rowp[-1] = make_float2(0.0f, tile[r][0]);
+            }
+        }
+    }
+    if (g.xT2) {
 #pragma unroll
         for (int q = 0; q < TT / TR; ++q) {
             const int oi = i0 + ty + q * TR, oj = j0 + tx;
-            if (oi < N && oj < N) g.xT[(size_t)oi * N + oj] = tile[tx][ty + q * TR];
+            if (oi < N && oj < N) {
+                float2* rowp = g.xT2 + (size_t)oi * P + PAIR_PAD;
+                rowp[oj] = make_float2(tile[tx][ty + q * TR], tile[tx + 1][ty + q * TR]);
+                if (oj == 0) rowp[-1] = make_float2(0.0f, tile[0][ty + q * TR]);
+            }
         }
     }
     if (MODE == TD_OBJ) {

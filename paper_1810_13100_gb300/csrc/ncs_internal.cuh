@@ -13,7 +13,7 @@ namespace ncs {
 // interpolation axis.  To keep the interpolation weight accurate in FP32 at
 // large N, each coefficient is split as X = X_hi + X_lo with X_hi a multiple of
 // 2^-10: then H = A_hi t + B_hi q + C_hi is exact in FP32 (|H| < 2^14) in any
-// evaluation order, and the small remainder L = B_lo q + (A_lo t + C_lo) is
+// evaluation order, and the small remainder L = A_lo t + (B_lo q + C_lo) is
 // evaluated in that fixed order.  The integer part of f is floor(H) +
 // floor((H - floor(H)) + L) and the weight is the fractional part of the
 // same sum, so the forward projector and the gather evaluate identical bits.
@@ -26,6 +26,14 @@ struct AngleParam {
     int pad0, pad1, pad2;
 };
 
+// Images read by the forward projector are stored as "pair images": entry i of
+// row j holds (x[j][i], x[j][i+1]) as one float2, so one aligned 8-byte load
+// serves both interpolation taps, and each row carries PAIR_PAD zero entries on
+// either side (row pitch N + 2 PAIR_PAD), so the projector's steps need no
+// bounds checks.  Entry i sits at offset i + PAIR_PAD, i in [-PAIR_PAD, N + PAIR_PAD).
+constexpr int PAIR_PAD = 4;
+inline __host__ __device__ int pair_pitch(int N) { return N + 2 * PAIR_PAD; }
+
 // Forward-projection epilogues.
 enum FwdMode {
     FWD_PLAIN = 0,     // y = K x
@@ -36,8 +44,8 @@ enum FwdMode {
 };
 
 struct FwdArgs {
-    const float* img;    // row-major image (row-branch angles)
-    const float* imgT;   // transposed image (column-branch angles)
+    const float2* img2;  // pair image of x (row-branch angles)
+    const float2* imgT2; // pair image of x^T (column-branch angles)
     const AngleParam* ap;
     int N, n_ang, n_det;
     float* y;            // PLAIN: output; PROX: dual u, updated in place
@@ -72,18 +80,18 @@ struct GatherArgs {
 
 // Transpose / finite-difference pass.
 enum TdMode {
-    TD_PROX = 0,         // v+ = Pi(v + beta D xbar), s+ = min(0, s + alpha kappa xbar), xbarT
-    TD_APPLY = 1,        // v = dscale D x, s = kappa x (if s), xT
-    TD_OBJ = 2,          // xc = clamp(x) (if clamp), xcT, TV partial sums (FP64)
-    TD_TRANSPOSE = 3,    // xT only
+    TD_PROX = 0,         // v+ = Pi(v + beta D xbar), s+ = min(0, s + alpha kappa xbar), pair images
+    TD_APPLY = 1,        // v = dscale D x, s = kappa x (if s), pair images
+    TD_OBJ = 2,          // pair images of x (clamped at 0 if clamp), TV partial sums (FP64)
+    TD_TRANSPOSE = 3,    // pair images only
 };
 
 struct TdArgs {
     const float* x;
-    float* xT;
+    float2* x2;          // pair image of x (or nullptr)
+    float2* xT2;         // pair image of x^T (or nullptr)
     float* v;            // 2*N*N
     float* s;            // N*N or nullptr
-    float* xc;           // TD_OBJ with clamp: clamped copy
     int N;
     float beta;          // TD_PROX: beta; TD_APPLY: dscale
     float rad;           // TV ball / box radius lambda alpha / beta
