@@ -40,6 +40,9 @@ CHECK_EVERY = 10
 TTG_TOL = 1e-4
 TTG_CAP = 2000
 METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
+# DRAM bytes (read + write) per launch of the current kernels, from one ncu capture
+# (profiles/ncu_k_gather_k_fwd_ct512.md); set to None when a kernel changes.
+NCU_TRAFFIC = {"joseph_gather": 4121088.0, "joseph_fwd": 8507392.0}
 
 
 def load_peaks():
@@ -289,7 +292,7 @@ def run_ours(args, ws, rank, local):
         flops = 2.0 * nnz
         achieved = flops / (dom_ms / dom_n / 1000.0) / 1e12
         roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get(dom_name),
                 "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
                 "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
     # whole-iteration algorithmic bytes (FP32 state read + written once, b read, spectrum round trips)

@@ -1,0 +1,117 @@
+"""GPU solves to a relative objective gap, checked by the FP64 oracle.
+
+ncs_solve and pdhg_solve run on the 64x64 TV-CT workload (90 angles, 92 bins,
+anisotropic TV, lambda 0.01) from zero until the GPU's FP64 objective is within
+1e-4 of f*, the oracle's reference minimum (tests/golden/fstar_ct64_s0.json).
+The oracle then evaluates the returned image in FP64: f(x_gpu) <= f*(1 + 1e-4)
+up to the FP32 representation of x (a few 1e-7 of f).  Also: divergence is
+reported, a CUDA-graph solve gives the same iterate as ncs_step, and the solve
+without f* stops on the relative change of f."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from helpers import f32
+from oracle import operators as oop
+from oracle import solvers as osv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def fstar(name):
+    with open(os.path.join(ROOT, "tests", "golden", "fstar_%s_s0.json" % name)) as fh:
+        return json.load(fh)["f_star"]
+
+
+def ct64():
+    W = synth.WORKLOADS["ct64"]
+    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+    g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
+    P = osv.Problem(g, f32(pr["b"]), lam=W["lam"], alpha=0.01, beta=0.01, tv=W["tv"])
+    return W, pr, P
+
+
+@pytest.mark.parametrize("solver", ["ncs", "pdhg"])
+def test_solve_reaches_gap_checked_by_oracle(solver):
+    import paper_1810_13100_gb300 as ncs
+    W, pr, P = ct64()
+    fs = fstar("ct64")
+    plan = ncs.Plan(W["N"], W["n_angles"], W["n_det"], W["lam"], 0.01, beta=0.01, tv=W["tv"])
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(W["N"] ** 2, device="cuda")
+    fn = plan.solve if solver == "ncs" else plan.pdhg_solve
+    rep = fn(b, x, tol=1e-4, max_iter=20000, f_star=fs)
+    assert rep["status"] == 0, rep
+    assert rep["gap"] <= 1e-4
+    f_oracle = osv.objective(P, x.double().cpu().numpy().reshape(W["N"], W["N"]))
+    assert f_oracle <= fs * (1 + 1e-4 + 1e-6)
+    assert f_oracle >= fs * (1 - 1e-6)            # f* is a minimum
+    assert rep["f"] == pytest.approx(f_oracle, rel=1e-6)
+    plan.close()
+
+
+def test_ncs_needs_fewer_iterations_than_pdhg():
+    import paper_1810_13100_gb300 as ncs
+    W, pr, P = ct64()
+    fs = fstar("ct64")
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    plan = ncs.Plan(W["N"], W["n_angles"], W["n_det"], W["lam"], 0.01, beta=0.01, tv=W["tv"])
+    x = torch.zeros(W["N"] ** 2, device="cuda")
+    r_ncs = plan.solve(b, x, tol=1e-3, max_iter=20000, f_star=fs)
+    x.zero_()
+    r_pdhg = plan.pdhg_solve(b, x, tol=1e-3, max_iter=20000, f_star=fs)
+    assert r_ncs["status"] == 0 and r_pdhg["status"] == 0
+    assert r_ncs["iters"] < r_pdhg["iters"]
+    plan.close()
+
+
+def test_graph_solve_matches_step_iterates():
+    """ncs_solve (CUDA graphs of check_every iterations) and ncs_step produce the
+    same iterate after the same number of iterations."""
+    import paper_1810_13100_gb300 as ncs
+    W, pr, P = ct64()
+    N, na, nd = W["N"], W["n_angles"], W["n_det"]
+    plan = ncs.Plan(N, na, nd, W["lam"], 0.01, beta=0.01, tv=W["tv"], check_every=10)
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x1 = torch.zeros(N * N, device="cuda")
+    plan.solve(b, x1, tol=0.0, max_iter=50, f_star=-1e300)
+    x2 = torch.zeros(N * N, device="cuda")
+    u = torch.zeros(na * nd, device="cuda")
+    v = torch.zeros(2 * N * N, device="cuda")
+    plan.step(x2, u, v, None, b, n_iter=50)
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2)
+    plan.close()
+
+
+def test_solve_without_fstar_stops_on_relative_change():
+    import paper_1810_13100_gb300 as ncs
+    W, pr, P = ct64()
+    plan = ncs.Plan(W["N"], W["n_angles"], W["n_det"], W["lam"], 0.01, beta=0.01, tv=W["tv"])
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(W["N"] ** 2, device="cuda")
+    rep = plan.solve(b, x, tol=1e-6, max_iter=20000)
+    assert rep["status"] == 0 and rep["gap"] <= 1e-6 and rep["iters"] < 20000
+    plan.close()
+
+
+def test_divergence_is_reported():
+    """With the (A3) rescale switched off, NCS on this problem diverges; the solve
+    returns NCS_ERR_DIVERGED instead of a result."""
+    import paper_1810_13100_gb300 as ncs
+    W, pr, P = ct64()
+    plan = ncs.Plan(W["N"], W["n_angles"], W["n_det"], W["lam"], 0.01, beta=0.01, tv=W["tv"], a3_margin=-1.0)
+    _, rho = plan.power_bound()
+    assert rho > 1.5
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(W["N"] ** 2, device="cuda")
+    with pytest.raises(ncs.NCSError) as ei:
+        plan.solve(b, x, tol=1e-4, max_iter=20000, f_star=fstar("ct64"))
+    assert ei.value.code == -5
+    plan.close()
