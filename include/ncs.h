@@ -65,7 +65,12 @@ typedef struct {
 
 typedef enum { NCS_DATA_L2 = 0, NCS_DATA_KL = 1 } ncs_data_term;
 typedef enum { NCS_TV_ANISO = 0, NCS_TV_ISO = 1 } ncs_tv_kind;
-typedef enum { NCS_FP32 = 0, NCS_BF16_STORE = 1 } ncs_precision;
+/* Storage of the iteration state (arithmetic is FP32 and reductions FP64 in all three):
+ * NCS_FP32: everything float32;
+ * NCS_BF16_STORE: the duals u, v, s and the projector's internal images of xbar in bfloat16;
+ * NCS_BF16_DUALS: only the duals u, v, s in bfloat16.
+ * x, b and bg are float32 in every mode. */
+typedef enum { NCS_FP32 = 0, NCS_BF16_STORE = 1, NCS_BF16_DUALS = 2 } ncs_precision;
 
 /* Solver options.  Fill with ncs_options_default() and change what you need. */
 typedef struct {
@@ -77,7 +82,7 @@ typedef struct {
     ncs_data_term data;    /* NCS_DATA_L2: 1/2||Kx - b||^2; NCS_DATA_KL: Poisson likelihood (Sec. 4.2) */
     ncs_tv_kind tv;        /* anisotropic box (Sec. 4.1) or isotropic per-pixel ball */
     int nonneg;            /* 1: add the row kappa I with delta_{R+} (Sec. 4.2 remark); KL only */
-    ncs_precision prec;    /* storage precision of the iteration state */
+    ncs_precision prec;    /* storage of the iteration state (see ncs_precision) */
     double a3_margin;      /* M is rescaled to rho(M^{-1} alpha A^T A) = 1/(1+margin); default 1e-2; <0 disables */
     int power_max_iter;    /* power iteration cap (default 500) */
     double power_tol;      /* power iteration relative-change stop (default 1e-9) */
@@ -120,6 +125,9 @@ void ncs_plan_destroy(ncs_plan* plan);
  * place on the caller's state: x (N*N), u (n_angles*n_det), v (2*N*N), s (N*N, PET
  * with nonneg only, else NULL); b is the measured sinogram (CT) or the counts
  * (PET); bg is the PET background sinogram or NULL (CT: must be NULL).
+ * x, b and bg are float32.  With prec = NCS_BF16_STORE or NCS_BF16_DUALS, u, v and s
+ * point to bfloat16 arrays of the same element counts (the float* type is kept for
+ * the ABI).
  * Asynchronous on the plan's stream. */
 int ncs_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
              const float* b, const float* bg, int n_iter);
@@ -129,7 +137,7 @@ int ncs_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
 int pdhg_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
               const float* b, const float* bg, int n_iter);
 
-/* Solve with NCS from x (in: x^0, out: the result; device) and zero duals, until
+/* Solve with NCS from x (in: x^0, out: the result; device, float32) and zero duals, until
  * (f - f_star)/|f_star| <= tol (f_star finite) or the relative change of f over
  * one check interval <= tol (f_star NaN), or max_iter iterations.  The FP64
  * objective is evaluated every check_every iterations on the GPU; the loop runs

@@ -27,7 +27,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PARAMS = {
     "ct64": dict(alpha=0.01, beta=0.01, gamma=0.0),
     "ct512": dict(alpha=0.003, beta=0.003, gamma=0.0),
-    "pet256": dict(alpha=0.1, beta=0.1, gamma=0.0),
+    "pet256": dict(alpha=1.0, beta=1.0, gamma=0.0),
 }
 
 

@@ -120,17 +120,19 @@ def _check(code, what):
     return code
 
 
-def _ptr(t, name, numel=None, allow_none=False):
-    """Device pointer of a contiguous float32 CUDA tensor (None -> NULL)."""
+def _ptr(t, name, numel=None, allow_none=False, dtype=None):
+    """Device pointer of a contiguous CUDA tensor of the given dtype (default
+    float32; None -> NULL)."""
     if t is None:
         if allow_none:
             return None
         raise ValueError("%s is required" % name)
     import torch
+    dtype = torch.float32 if dtype is None else dtype
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError("%s must be a CUDA tensor" % name)
-    if t.dtype != torch.float32 or not t.is_contiguous():
-        raise TypeError("%s must be a contiguous float32 tensor" % name)
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError("%s must be a contiguous %s tensor" % (name, dtype))
     if numel is not None and t.numel() != numel:
         raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), numel))
     return ctypes.c_void_p(t.data_ptr())
@@ -172,7 +174,7 @@ class Plan:
         o.data = {"l2": 0, "kl": 1}[data]
         o.tv = {"aniso": 0, "iso": 1}[tv]
         o.nonneg = 1 if nonneg else 0
-        o.prec = {"fp32": 0, "bf16": 1}[precision]
+        o.prec = {"fp32": 0, "bf16": 1, "bf16-duals": 2}[precision]
         o.a3_margin = float(a3_margin)
         o.power_max_iter = int(power_max_iter)
         o.power_tol = float(power_tol)
@@ -194,6 +196,8 @@ class Plan:
         self.lam, self.alpha = float(lam), float(alpha)
         self.beta = float(alpha if beta is None else beta)
         self.data, self.tv, self.nonneg = data, tv, bool(nonneg)
+        # dtype of the duals u, v, s in step (x, b, bg are always float32)
+        self.state_dtype = torch.float32 if precision == "fp32" else torch.bfloat16
 
     def _enter(self):
         if self._auto:
@@ -234,8 +238,10 @@ class Plan:
 
     # -------------------------------------------------------------- iterations
     def _state_ptrs(self, x, u, v, s, b, bg):
-        return (_ptr(x, "x", self.n), _ptr(u, "u", self.m), _ptr(v, "v", 2 * self.n),
-                _ptr(s, "s", self.n, allow_none=True), _ptr(b, "b", self.m), _ptr(bg, "bg", self.m, allow_none=True))
+        d = self.state_dtype
+        return (_ptr(x, "x", self.n), _ptr(u, "u", self.m, dtype=d), _ptr(v, "v", 2 * self.n, dtype=d),
+                _ptr(s, "s", self.n, allow_none=True, dtype=d), _ptr(b, "b", self.m),
+                _ptr(bg, "bg", self.m, allow_none=True))
 
     def step(self, x, u, v, s, b, bg=None, n_iter=1):
         """n_iter NCS iterations in place on (x, u, v, s)."""

@@ -35,6 +35,9 @@ struct ncs_plan {
     int N = 0, na = 0, nd = 0;
     double lam = 0, alpha = 0, beta = 0, gamma = 0, kappa = 0, c_r = 0, h_dc = 0;
     bool kl = false, iso = false, nonneg = false;
+    bool bf = false;                 // duals u, v, s stored as bfloat16 (NCS_BF16_STORE, NCS_BF16_DUALS)
+    bool bf_img = false;             // projector images of xbar stored as bfloat16 (NCS_BF16_STORE)
+    unsigned long long* d_iter = nullptr;  // device iteration counter (stochastic rounding of bfloat16 duals)
     ncs_options opt{};
     cudaStream_t st = nullptr;
     bool own_stream = false;
@@ -195,8 +198,8 @@ int enq_K(ncs_plan* p, const float2* x2, const float2* xT2, float* y)
     return NCS_OK;
 }
 
-int enq_gather(ncs_plan* p, int mode, const float* u, const float* v, float dscale, const float* s, float kappa,
-               float* r, float* x, float* xbar, float inv_gamma, int n_ang)
+int enq_gather(ncs_plan* p, int mode, const void* u, const void* v, float dscale, const void* s, float kappa,
+               float* r, float* x, float* xbar, float inv_gamma, int n_ang, bool bf = false)
 {
     GatherArgs g{};
     g.u = u;
@@ -215,6 +218,9 @@ int enq_gather(ncs_plan* p, int mode, const float* u, const float* v, float dsca
     g.x = x;
     g.xbar = xbar;
     g.inv_gamma = inv_gamma;
+    g.sino_bf = bf ? 1 : 0;
+    g.img_bf = bf ? 1 : 0;
+    g.iter = bf ? p->d_iter : nullptr;
     CKP(NCS_KERNEL_GATHER, launch_gather(mode, g, p->st));
     return NCS_OK;
 }
@@ -228,8 +234,8 @@ int enq_solve(ncs_plan* p, const float* r, const float* table, int mode, float* 
     return NCS_OK;
 }
 
-// v+, s+ prox and xbar^T
-int enq_td_prox(ncs_plan* p, float* v, float* s)
+// v+, s+ prox and the pair images of xbar and xbar^T
+int enq_td_prox(ncs_plan* p, void* v, void* s)
 {
     TdArgs a{};
     a.x = p->d_xbar;
@@ -242,11 +248,14 @@ int enq_td_prox(ncs_plan* p, float* v, float* s)
     a.rad = (float)(p->lam * p->alpha / p->beta);
     a.ak = (float)(p->alpha * p->kappa);
     a.iso = p->iso ? 1 : 0;
+    a.img_bf = p->bf ? 1 : 0;
+    a.pair_bf = p->bf_img ? 1 : 0;
+    a.iter = p->d_iter;
     CKP(NCS_KERNEL_TD, launch_td(TD_PROX, a, p->st));
     return NCS_OK;
 }
 
-int enq_fwd_prox(ncs_plan* p, float* u, const float* b, const float* bg)
+int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg)
 {
     FwdArgs f{};
     f.img2 = p->d_xb2;
@@ -260,17 +269,20 @@ int enq_fwd_prox(ncs_plan* p, float* u, const float* b, const float* bg)
     f.bg = bg;
     f.alpha = (float)p->alpha;
     f.inv1pa = (float)(1.0 / (1.0 + p->alpha));
+    f.pair_bf = p->bf_img ? 1 : 0;
+    f.sino_bf = p->bf ? 1 : 0;
+    f.iter = p->d_iter;
     CKP(NCS_KERNEL_FWD, launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
     return NCS_OK;
 }
 
 // One NCS iteration (eq. (NCS), Sec. 4.1 / 4.2).
-int enq_ncs_iter(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg)
+int enq_ncs_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* b, const float* bg)
 {
-    const float* sv = p->nonneg ? s : nullptr;
+    const void* sv = p->nonneg ? s : nullptr;
     // r = K^T u + (beta/alpha) D^T v + kappa s
     CKS(enq_gather(p, GATHER_R, u, v, (float)(p->beta / p->alpha), sv, (float)p->kappa, p->d_r, nullptr,
-                   nullptr, 0.f, p->na));
+                   nullptr, 0.f, p->na, p->bf));
     // x+ = x - M^+ r ; xbar = 2 x+ - x
     CKS(enq_solve(p, p->d_r, p->d_invmu, 0, x, p->d_xbar, nullptr));
     // v+ = Pi(v + beta D xbar), s+ = min(0, s + alpha kappa xbar), xbar^T
@@ -281,17 +293,17 @@ int enq_ncs_iter(ncs_plan* p, float* x, float* u, float* v, float* s, const floa
 }
 
 // One PDHG iteration (eq. (PDHG)).
-int enq_pdhg_iter(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg)
+int enq_pdhg_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* b, const float* bg)
 {
-    const float* sv = p->nonneg ? s : nullptr;
+    const void* sv = p->nonneg ? s : nullptr;
     CKS(enq_gather(p, GATHER_PDHG, u, v, (float)(p->beta / p->alpha), sv, (float)p->kappa, nullptr, x,
-                   p->d_xbar, 1.0f / p->gamma_p, p->na));
+                   p->d_xbar, 1.0f / p->gamma_p, p->na, p->bf));
     CKS(enq_td_prox(p, v, s));
     CKS(enq_fwd_prox(p, u, b, bg));
     return NCS_OK;
 }
 
-// FP64 objective at x into d_scal[slot].
+// FP64 objective at x into d_scal[slot] (x, its pair images, b and bg in FP32 in every precision).
 int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, int slot)
 {
     TdArgs a{};
@@ -478,7 +490,7 @@ void free_plan(ncs_plan* p)
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
     cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s);
-    cudaFree(p->d_gpart); cudaFree(p->d_gcount);
+    cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
 }
@@ -569,6 +581,8 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     p->gparts = gather_parts(N, na);
     CKS(dalloc(&p->d_gpart, p->gparts > 1 ? (size_t)p->gparts * n : 1));
     CKS(dalloc(&p->d_gcount, gather_tiles(N)));
+    CKS(dalloc(&p->d_iter, 1));
+    CK(cudaMemsetAsync(p->d_iter, 0, sizeof(unsigned long long), p->st));
     CK(cudaMemsetAsync(p->d_gcount, 0, gather_tiles(N) * sizeof(int), p->st));
     CKS(dalloc(&p->d_part0, kMaxPartials));
     CKS(dalloc(&p->d_part1, (size_t)fwd_num_blocks(nd, na)));
@@ -741,7 +755,7 @@ int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, dou
     ncs_options o;
     if (opt) o = *opt;
     else ncs_options_default(&o);
-    if (o.prec != NCS_FP32) return NCS_ERR_UNSUPPORTED;
+    if (o.prec != NCS_FP32 && o.prec != NCS_BF16_STORE && o.prec != NCS_BF16_DUALS) return NCS_ERR_BADARG;
     if (o.nonneg && o.data != NCS_DATA_KL) return NCS_ERR_BADARG;
     if (o.power_max_iter < 1 || !(o.power_tol >= 0.0)) return NCS_ERR_BADARG;
     RadixPlan rp;
@@ -764,6 +778,8 @@ int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, dou
     p->kl = o.data == NCS_DATA_KL;
     p->iso = o.tv == NCS_TV_ISO;
     p->nonneg = o.nonneg != 0;
+    p->bf = o.prec != NCS_FP32;
+    p->bf_img = o.prec == NCS_BF16_STORE;
     p->opt = o;
     p->rp = rp;
     if (!(p->beta > 0.0) || !(p->gamma >= 0.0) || (p->nonneg && !(p->kappa > 0.0))) {

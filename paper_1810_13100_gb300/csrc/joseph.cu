@@ -48,7 +48,7 @@ __device__ __forceinline__ float kl_conj_prox(float z, float c)
     return d > 0.0f ? 1.0f - 2.0f * c / (d + root) : 1.0f + 0.5f * (d - root);
 }
 
-template <int MODE>
+template <int MODE, bool PBF, bool SBF>
 __global__ void __launch_bounds__(FWD_TB * FWD_SEG)
 k_fwd(FwdArgs g)
 {
@@ -56,7 +56,7 @@ k_fwd(FwdArgs g)
     __shared__ double dred[FWD_TB];
     const int a = blockIdx.y;
     const AngleParam p = g.ap[a];
-    const float2* __restrict__ im2 = p.row ? g.img2 : g.imgT2;
+    const void* im2 = p.row ? g.img2 : g.imgT2;
     const int pitch = pair_pitch(g.N);
     const int N = g.N;
     const int t = blockIdx.x * FWD_TB + threadIdx.x;
@@ -90,7 +90,7 @@ k_fwd(FwdArgs g)
             float k0f;
             const float w = split_weight(fmaf(p.Bhi, jf, Hr), fmaf(p.Alo, ft, fmaf(p.Blo, jf, p.Clo)), k0f);
             const int i0 = (int)k0f;
-            const float2 xv = __ldg(im2 + (size_t)j * pitch + PAIR_PAD + i0);
+            const float2 xv = St<PBF>::ld2(im2, (size_t)j * pitch + PAIR_PAD + i0);
             acc = fmaf(1.0f - w, xv.x, acc);
             acc = fmaf(w, xv.y, acc);
         }
@@ -105,20 +105,21 @@ k_fwd(FwdArgs g)
         const float y = p.W * tot;
         const size_t idx = (size_t)a * g.n_det + t;
         if (MODE == FWD_PLAIN) {
-            g.y[idx] = y;
+            St<false>::put(g.y, idx, y);
         } else if (MODE == FWD_PROX_L2) {
-            const float z = fmaf(g.alpha, y - g.b[idx], g.y[idx]);
-            g.y[idx] = z * g.inv1pa;
+            const float z = fmaf(g.alpha, y - St<false>::ld(g.b, idx), St<SBF>::get(g.y, idx));
+            St<SBF>::put_sr(g.y, idx, z * g.inv1pa, SBF ? rand16(*g.iter, idx, 1u) : 0u);
         } else if (MODE == FWD_PROX_KL) {
-            const float bgv = g.bg ? g.bg[idx] : 0.0f;
-            const float z = fmaf(g.alpha, y + bgv, g.y[idx]);
-            g.y[idx] = kl_conj_prox(z, g.alpha * g.b[idx]);
+            const float bgv = g.bg ? St<false>::ld(g.bg, idx) : 0.0f;
+            const float z = fmaf(g.alpha, y + bgv, St<SBF>::get(g.y, idx));
+            St<SBF>::put_sr(g.y, idx, kl_conj_prox(z, g.alpha * St<false>::ld(g.b, idx)),
+                            SBF ? rand16(*g.iter, idx, 1u) : 0u);
         } else if (MODE == FWD_RESID_L2) {
-            const double d = (double)y - (double)g.b[idx];
+            const double d = (double)y - (double)St<false>::ld(g.b, idx);
             term = d * d;
         } else {  // FWD_RESID_KL
-            const double mu = (double)y + (g.bg ? (double)g.bg[idx] : 0.0);
-            const double bb = (double)g.b[idx];
+            const double mu = (double)y + (g.bg ? (double)St<false>::ld(g.bg, idx) : 0.0);
+            const double bb = (double)St<false>::ld(g.b, idx);
             term = mu - bb;
             if (bb > 0.0) term += bb * log(bb / mu);
         }
@@ -154,8 +155,8 @@ struct LineEntry {
 // receives at most one "right" weight (1 - w) and one "left" weight w per
 // angle, so the two phases never write one address twice.  CHECK: test the
 // line and ray ranges per pair (edge tiles and rays beyond the detector).
-template <bool ROW, bool CHECK>
-__device__ __forceinline__ void gather_pairs(const AngleParam& p, const float* __restrict__ ua, int n_det, int N,
+template <bool ROW, bool CHECK, bool SBF>
+__device__ __forceinline__ void gather_pairs(const AngleParam& p, const void* ua, int n_det, int N,
                                              int o0, int RPL, int lane, const LineEntry* tab, float (*A)[GT + 1])
 {
     int lo = lane / RPL, r = lane - lo * RPL;
@@ -169,7 +170,7 @@ __device__ __forceinline__ void gather_pairs(const AngleParam& p, const float* _
             float k0f;
             const float w = split_weight(fmaf(p.Ahi, tf, e.Hq), fmaf(p.Alo, tf, e.Lq), k0f);
             kk = (int)k0f - o0;
-            const float Wu = p.W * __ldg(ua + t);
+            const float Wu = p.W * St<SBF>::ld(ua, t);
             vR = fmaf(-w, Wu, Wu);
             vL = w * Wu;
         }
@@ -191,8 +192,8 @@ __device__ __forceinline__ void gather_pairs(const AngleParam& p, const float* _
     }
 }
 
-template <bool ROW>
-__device__ __forceinline__ void gather_angle(const AngleParam& p, const float* __restrict__ ua, int n_det, int N,
+template <bool ROW, bool SBF>
+__device__ __forceinline__ void gather_angle(const AngleParam& p, const void* ua, int n_det, int N,
                                              int o0, int l0, int lane, LineEntry* tab, float (*A)[GT + 1])
 {
     const float lf0 = (float)l0;
@@ -217,12 +218,12 @@ __device__ __forceinline__ void gather_angle(const AngleParam& p, const float* _
     const int t_first = min(tab[0].tl, tab[GT - 1].tl);
     const int t_last = max(tab[0].tl, tab[GT - 1].tl) + RPL - 1;
     const bool inside = (l0 + GT <= N) && t_first >= 0 && t_last < n_det;
-    if (inside) gather_pairs<ROW, false>(p, ua, n_det, N, o0, RPL, lane, tab, A);
-    else gather_pairs<ROW, true>(p, ua, n_det, N, o0, RPL, lane, tab, A);
+    if (inside) gather_pairs<ROW, false, SBF>(p, ua, n_det, N, o0, RPL, lane, tab, A);
+    else gather_pairs<ROW, true, SBF>(p, ua, n_det, N, o0, RPL, lane, tab, A);
     __syncwarp();
 }
 
-template <int MODE>
+template <int MODE, bool SBF, bool IBF>
 __global__ void __launch_bounds__(GT * GW)
 k_gather(GatherArgs g)
 {
@@ -233,6 +234,7 @@ k_gather(GatherArgs g)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
     float (*A)[GT + 1] = acc[wid];
+    if (g.iter && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *g.iter += 1ull;
     for (int rr = 0; rr < GT; ++rr) A[rr][lane] = 0.0f;
     __syncwarp();
     // this block's slice of the angles; warps take whole angles round robin
@@ -241,9 +243,9 @@ k_gather(GatherArgs g)
     const int a_end = (int)(((long long)g.n_ang * (part + 1)) / P);
     for (int a = a_beg + wid; a < a_end; a += GW) {
         const AngleParam p = g.ap[a];
-        const float* __restrict__ ua = g.u + (size_t)a * g.n_det;
-        if (p.row) gather_angle<true>(p, ua, g.n_det, N, i0, j0, lane, lines[wid], A);
-        else gather_angle<false>(p, ua, g.n_det, N, j0, i0, lane, lines[wid], A);
+        const void* ua = static_cast<const char*>(g.u) + (size_t)a * g.n_det * St<SBF>::bytes;
+        if (p.row) gather_angle<true, SBF>(p, ua, g.n_det, N, i0, j0, lane, lines[wid], A);
+        else gather_angle<false, SBF>(p, ua, g.n_det, N, j0, i0, lane, lines[wid], A);
     }
     __syncthreads();
     // sum the warp tiles in a fixed order; thread -> pixels (q*8 + wid, lane)
@@ -288,16 +290,15 @@ k_gather(GatherArgs g)
         const size_t pix = (size_t)j * N + i;
         float r = tot[q];
         if (g.v) {
-            const float* vh = g.v;
-            const float* vv = g.v + (size_t)N * N;
+            const size_t NN = (size_t)N * N;
             float dt = 0.0f;
-            if (i < N - 1) dt += vh[pix];
-            if (i >= 1) dt -= vh[pix - 1];
-            if (j < N - 1) dt += vv[pix];
-            if (j >= 1) dt -= vv[pix - N];
+            if (i < N - 1) dt += St<IBF>::get(g.v, pix);
+            if (i >= 1) dt -= St<IBF>::get(g.v, pix - 1);
+            if (j < N - 1) dt += St<IBF>::get(g.v, NN + pix);
+            if (j >= 1) dt -= St<IBF>::get(g.v, NN + pix - N);
             r = fmaf(g.dscale, dt, r);
         }
-        if (g.s) r = fmaf(g.kappa, g.s[pix], r);
+        if (g.s) r = fmaf(g.kappa, St<IBF>::get(g.s, pix), r);
         if (MODE == GATHER_R) {
             g.r[pix] = r;
         } else {
@@ -316,17 +317,27 @@ int fwd_num_blocks(int n_det, int n_ang)
     return ((n_det + FWD_TB - 1) / FWD_TB) * n_ang;
 }
 
+template <bool PBF, bool SBF>
+void fwd_dispatch(int mode, const FwdArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    switch (mode) {
+        case FWD_PLAIN: k_fwd<FWD_PLAIN, PBF, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_PROX_L2: k_fwd<FWD_PROX_L2, PBF, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_PROX_KL: k_fwd<FWD_PROX_KL, PBF, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_RESID_L2: k_fwd<FWD_RESID_L2, PBF, SBF><<<grid, block, 0, st>>>(a); break;
+        default: k_fwd<FWD_RESID_KL, PBF, SBF><<<grid, block, 0, st>>>(a); break;
+    }
+}
+
 cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st)
 {
+    if (mode < FWD_PLAIN || mode > FWD_RESID_KL) return cudaErrorInvalidValue;
+    if (mode == FWD_PLAIN && a.sino_bf) return cudaErrorInvalidValue;    // y is float
     dim3 grid((a.n_det + FWD_TB - 1) / FWD_TB, a.n_ang), block(FWD_TB, FWD_SEG);
-    switch (mode) {
-        case FWD_PLAIN: k_fwd<FWD_PLAIN><<<grid, block, 0, st>>>(a); break;
-        case FWD_PROX_L2: k_fwd<FWD_PROX_L2><<<grid, block, 0, st>>>(a); break;
-        case FWD_PROX_KL: k_fwd<FWD_PROX_KL><<<grid, block, 0, st>>>(a); break;
-        case FWD_RESID_L2: k_fwd<FWD_RESID_L2><<<grid, block, 0, st>>>(a); break;
-        case FWD_RESID_KL: k_fwd<FWD_RESID_KL><<<grid, block, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+    if (a.pair_bf && a.sino_bf) fwd_dispatch<true, true>(mode, a, grid, block, st);
+    else if (a.pair_bf) fwd_dispatch<true, false>(mode, a, grid, block, st);
+    else if (a.sino_bf) fwd_dispatch<false, true>(mode, a, grid, block, st);
+    else fwd_dispatch<false, false>(mode, a, grid, block, st);
     return cudaGetLastError();
 }
 
@@ -347,13 +358,22 @@ int gather_parts(int N, int n_ang)
     return (int)p;
 }
 
+template <int MODE>
+void gather_dispatch(const GatherArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    if (a.sino_bf && a.img_bf) k_gather<MODE, true, true><<<grid, block, 0, st>>>(a);
+    else if (a.sino_bf) k_gather<MODE, true, false><<<grid, block, 0, st>>>(a);
+    else if (a.img_bf) k_gather<MODE, false, true><<<grid, block, 0, st>>>(a);
+    else k_gather<MODE, false, false><<<grid, block, 0, st>>>(a);
+}
+
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
 {
     const int b = (a.N + GT - 1) / GT;
     dim3 grid(b, b, a.parts), block(GT * GW);
     if (a.parts < 1 || (a.parts > 1 && (!a.part || !a.counters))) return cudaErrorInvalidValue;
-    if (mode == GATHER_R) k_gather<GATHER_R><<<grid, block, 0, st>>>(a);
-    else if (mode == GATHER_PDHG) k_gather<GATHER_PDHG><<<grid, block, 0, st>>>(a);
+    if (mode == GATHER_R) gather_dispatch<GATHER_R>(a, grid, block, st);
+    else if (mode == GATHER_PDHG) gather_dispatch<GATHER_PDHG>(a, grid, block, st);
     else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }

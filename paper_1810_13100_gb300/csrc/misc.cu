@@ -20,7 +20,7 @@ namespace {
 constexpr int TT = 32;      // tile side
 constexpr int TR = 8;       // block rows
 
-template <int MODE>
+template <int MODE, bool IBF, bool PBF>
 __global__ void __launch_bounds__(TT * TR)
 k_td(TdArgs g)
 {
@@ -51,8 +51,8 @@ k_td(TdArgs g)
         const float dh = hx ? xv - tile[r][c + 1] : 0.0f;
         const float dv = hy ? xv - tile[r + 1][c] : 0.0f;
         if (MODE == TD_PROX) {
-            float zh = hx ? fmaf(g.beta, dh, g.v[pix]) : 0.0f;
-            float zv = hy ? fmaf(g.beta, dv, g.v[NN + pix]) : 0.0f;
+            float zh = hx ? fmaf(g.beta, dh, St<IBF>::get(g.v, pix)) : 0.0f;
+            float zv = hy ? fmaf(g.beta, dv, St<IBF>::get(g.v, NN + pix)) : 0.0f;
             if (g.iso) {
                 const float n2 = fmaf(zh, zh, zv * zv);
                 if (n2 > g.rad * g.rad) {
@@ -64,15 +64,18 @@ k_td(TdArgs g)
                 zh = fminf(fmaxf(zh, -g.rad), g.rad);
                 zv = fminf(fmaxf(zv, -g.rad), g.rad);
             }
-            g.v[pix] = zh;
-            g.v[NN + pix] = zv;
-            if (g.s) g.s[pix] = fminf(fmaf(g.ak, xv, g.s[pix]), 0.0f);
+            const unsigned long long it = IBF ? *g.iter : 0ull;
+            St<IBF>::put_sr(g.v, pix, zh, IBF ? rand16(it, pix, 2u) : 0u);
+            St<IBF>::put_sr(g.v, NN + pix, zv, IBF ? rand16(it, pix, 3u) : 0u);
+            if (g.s)
+                St<IBF>::put_sr(g.s, pix, fminf(fmaf(g.ak, xv, St<IBF>::get(g.s, pix)), 0.0f),
+                                IBF ? rand16(it, pix, 4u) : 0u);
         } else if (MODE == TD_APPLY) {
             if (g.v) {
-                g.v[pix] = g.beta * dh;
-                g.v[NN + pix] = g.beta * dv;
+                St<IBF>::put(g.v, pix, g.beta * dh);
+                St<IBF>::put(g.v, NN + pix, g.beta * dv);
             }
-            if (g.s) g.s[pix] = g.ak * xv;
+            if (g.s) St<IBF>::put(g.s, pix, g.ak * xv);
         } else if (MODE == TD_OBJ) {
             const double a = dh, b = dv;
             tv += g.iso ? sqrt(a * a + b * b) : fabs(a) + fabs(b);
@@ -86,9 +89,9 @@ k_td(TdArgs g)
             const int r = ty + q * TR, c = tx;
             const int gj = j0 + r, gi = i0 + c;
             if (gj < N && gi < N) {
-                float2* rowp = g.x2 + (size_t)gj * P + PAIR_PAD;
-                rowp[gi] = make_float2(tile[r][c], tile[r][c + 1]);
-                if (gi == 0) rowp[-1] = make_float2(0.0f, tile[r][0]);
+                const size_t rowp = (size_t)gj * P + PAIR_PAD;
+                St<PBF>::put2(g.x2, rowp + gi, tile[r][c], tile[r][c + 1]);
+                if (gi == 0) St<PBF>::put2(g.x2, rowp - 1, 0.0f, tile[r][0]);
             }
         }
     }
@@ -97,9 +100,9 @@ k_td(TdArgs g)
         for (int q = 0; q < TT / TR; ++q) {
             const int oi = i0 + ty + q * TR, oj = j0 + tx;
             if (oi < N && oj < N) {
-                float2* rowp = g.xT2 + (size_t)oi * P + PAIR_PAD;
-                rowp[oj] = make_float2(tile[tx][ty + q * TR], tile[tx + 1][ty + q * TR]);
-                if (oj == 0) rowp[-1] = make_float2(0.0f, tile[0][ty + q * TR]);
+                const size_t rowp = (size_t)oi * P + PAIR_PAD;
+                St<PBF>::put2(g.xT2, rowp + oj, tile[tx][ty + q * TR], tile[tx + 1][ty + q * TR]);
+                if (oj == 0) St<PBF>::put2(g.xT2, rowp - 1, 0.0f, tile[0][ty + q * TR]);
             }
         }
     }
@@ -206,17 +209,26 @@ int td_num_blocks(int N)
     return b * b;
 }
 
+template <bool IBF, bool PBF>
+void td_dispatch(int mode, const TdArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    switch (mode) {
+        case TD_PROX: k_td<TD_PROX, IBF, PBF><<<grid, block, 0, st>>>(a); break;
+        case TD_APPLY: k_td<TD_APPLY, IBF, PBF><<<grid, block, 0, st>>>(a); break;
+        case TD_OBJ: k_td<TD_OBJ, IBF, PBF><<<grid, block, 0, st>>>(a); break;
+        default: k_td<TD_TRANSPOSE, IBF, PBF><<<grid, block, 0, st>>>(a); break;
+    }
+}
+
 cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st)
 {
+    if (mode < TD_PROX || mode > TD_TRANSPOSE) return cudaErrorInvalidValue;
     const int b = (a.N + TT - 1) / TT;
     dim3 grid(b, b), block(TT, TR);
-    switch (mode) {
-        case TD_PROX: k_td<TD_PROX><<<grid, block, 0, st>>>(a); break;
-        case TD_APPLY: k_td<TD_APPLY><<<grid, block, 0, st>>>(a); break;
-        case TD_OBJ: k_td<TD_OBJ><<<grid, block, 0, st>>>(a); break;
-        case TD_TRANSPOSE: k_td<TD_TRANSPOSE><<<grid, block, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-    }
+    if (a.img_bf && a.pair_bf) td_dispatch<true, true>(mode, a, grid, block, st);
+    else if (a.img_bf) td_dispatch<true, false>(mode, a, grid, block, st);
+    else if (a.pair_bf) td_dispatch<false, true>(mode, a, grid, block, st);
+    else td_dispatch<false, false>(mode, a, grid, block, st);
     return cudaGetLastError();
 }
 

@@ -2,10 +2,74 @@
 // Not part of the public C ABI (include/ncs.h).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace ncs {
+
+// Storage precision of the iteration state (FP32 arithmetic either way):
+// St<false> stores float, St<true> stores bfloat16 rounded to nearest.
+template <bool BF>
+struct St;
+
+// 16 random bits for element i of a store made at iteration ctr (SplitMix64
+// finaliser of a counter; Steele, Lea, Flood 2014).
+__device__ __forceinline__ unsigned rand16(unsigned long long ctr, size_t i, unsigned salt)
+{
+    unsigned long long z = ctr * 0x9E3779B97F4A7C15ull + (unsigned long long)i * 0xD1B54A32D192ED03ull + salt;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (unsigned)(z >> 48);
+}
+
+template <>
+struct St<false> {
+    static constexpr size_t bytes = 4;
+    __device__ static void put_sr(void* p, size_t i, float v, unsigned) { static_cast<float*>(p)[i] = v; }
+    __device__ static float ld(const void* p, size_t i) { return __ldg(static_cast<const float*>(p) + i); }
+    __device__ static float get(const void* p, size_t i) { return static_cast<const float*>(p)[i]; }
+    __device__ static void put(void* p, size_t i, float v) { static_cast<float*>(p)[i] = v; }
+    __device__ static float2 ld2(const void* p, size_t i) { return __ldg(static_cast<const float2*>(p) + i); }
+    __device__ static void put2(void* p, size_t i, float a, float b)
+    {
+        static_cast<float2*>(p)[i] = make_float2(a, b);
+    }
+};
+
+template <>
+struct St<true> {
+    static constexpr size_t bytes = 2;
+    // Stochastic rounding: add 16 random bits below the bfloat16 mantissa and
+    // truncate, so the stored value is unbiased (small increments to an
+    // accumulator survive in expectation).  Inf / NaN are stored unchanged.
+    __device__ static void put_sr(void* p, size_t i, float v, unsigned r16)
+    {
+        unsigned bits = __float_as_uint(v);
+        if ((bits & 0x7F800000u) != 0x7F800000u) bits += r16;
+        static_cast<unsigned short*>(p)[i] = (unsigned short)(bits >> 16);
+    }
+    __device__ static float ld(const void* p, size_t i)
+    {
+        return __bfloat162float(__ldg(static_cast<const __nv_bfloat16*>(p) + i));
+    }
+    __device__ static float get(const void* p, size_t i)
+    {
+        return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+    }
+    __device__ static void put(void* p, size_t i, float v)
+    {
+        static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(v);
+    }
+    __device__ static float2 ld2(const void* p, size_t i)
+    {
+        return __bfloat1622float2(__ldg(static_cast<const __nv_bfloat162*>(p) + i));
+    }
+    __device__ static void put2(void* p, size_t i, float a, float b)
+    {
+        static_cast<__nv_bfloat162*>(p)[i] = __floats2bfloat162_rn(a, b);
+    }
+};
 
 // Per-angle Joseph coefficients, FP64 on the host, rounded once.
 // A ray (a, t) crosses stepping line q (an image row, or a row of x^T for
@@ -44,13 +108,16 @@ enum FwdMode {
 };
 
 struct FwdArgs {
-    const float2* img2;  // pair image of x (row-branch angles)
-    const float2* imgT2; // pair image of x^T (column-branch angles)
+    const void* img2;    // pair image of x (row-branch angles)
+    const void* imgT2;   // pair image of x^T (column-branch angles)
     const AngleParam* ap;
     int N, n_ang, n_det;
-    float* y;            // PLAIN: output; PROX: dual u, updated in place
-    const float* b;
-    const float* bg;     // KL background or nullptr
+    void* y;             // PLAIN: output (float); PROX: dual u, updated in place
+    const float* b;      // data (float32 in every precision)
+    const float* bg;     // KL background or nullptr (float32)
+    int pair_bf;         // pair images stored as bfloat16
+    int sino_bf;         // the dual u (y in PROX modes) stored as bfloat16 (stochastic rounding)
+    const unsigned long long* iter;  // device iteration counter (random bits of the rounding)
     float alpha, inv1pa;
     double* partials;    // RESID: one partial per block (gridDim.x * gridDim.y)
 };
@@ -62,20 +129,22 @@ enum GatherMode {
 };
 
 struct GatherArgs {
-    const float* u;
+    const void* u;       // sinogram (float, or bfloat16 if sino_bf)
     const AngleParam* ap;
     int N, n_ang, n_det;
     int parts;           // angle slices per tile (gridDim.z)
     float* part;         // scratch: parts * N * N partial sums (parts > 1)
     int* counters;       // scratch: one arrival counter per 32 x 32 tile, zero between launches
-    const float* v;      // 2*N*N or nullptr
+    const void* v;       // 2*N*N or nullptr (float, or bfloat16 if img_bf)
     float dscale;
-    const float* s;      // N*N or nullptr
+    const void* s;       // N*N or nullptr (float, or bfloat16 if img_bf)
     float kappa;
+    int sino_bf, img_bf;
     float* r;            // GATHER_R output
     float* x;            // GATHER_PDHG: primal, updated in place
     float* xbar;         // GATHER_PDHG: extrapolated primal
     float inv_gamma;
+    unsigned long long* iter;  // if set, block (0,0,0) advances this device iteration counter
 };
 
 // Transpose / finite-difference pass.
@@ -88,10 +157,13 @@ enum TdMode {
 
 struct TdArgs {
     const float* x;
-    float2* x2;          // pair image of x (or nullptr)
-    float2* xT2;         // pair image of x^T (or nullptr)
-    float* v;            // 2*N*N
-    float* s;            // N*N or nullptr
+    void* x2;            // pair image of x (or nullptr)
+    void* xT2;           // pair image of x^T (or nullptr)
+    void* v;             // 2*N*N
+    void* s;             // N*N or nullptr
+    int img_bf;          // v, s stored as bfloat16 (stochastic rounding)
+    int pair_bf;         // pair images stored as bfloat16 (round to nearest)
+    const unsigned long long* iter;  // device iteration counter (random bits of the rounding)
     int N;
     float beta;          // TD_PROX: beta; TD_APPLY: dscale
     float rad;           // TV ball / box radius lambda alpha / beta
