@@ -372,6 +372,59 @@ def run_ours(args, ws, rank, local):
     plan.close()
 
 
+def run_batch(args, ws, rank, local):
+    """64 independent TV-CT slices of uneven sizes (sides drawn by seed from
+    {256, 384, 512}, round(1.4 side) angles, side + 2 bins, the 512x512 workload's
+    phantom and noise model) solved together by ncs_batch_solve.  Prints one JSON
+    line: slice-iterations per second over K iterations of every slice, per
+    precision variant."""
+    import torch
+    import paper_1810_13100_gb300 as ncs
+    import synth
+    torch.cuda.set_device(local)
+    sides = synth.batch_sides(args.seed, args.slices)
+    W = synth.WORKLOADS[WORKLOAD]
+    out = {}
+    for prec in ("fp32", "bf16"):
+        plans, bs, xs = [], [], []
+        for i, N in enumerate(sides):
+            na, nd = int(round(1.4 * N)), N + 2
+            pr = synth.ct_problem(1000 * args.seed + i, N, na, nd, W["n_ellipses"], W["noise_frac"])
+            plans.append(ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], tv=W["tv"],
+                                  precision=prec, autotune=True, check_every=CHECK_EVERY))
+            bs.append(torch.from_numpy(pr["b"].ravel()).cuda())
+            xs.append(torch.zeros(N * N, device="cuda"))
+        batch = ncs.Batch(plans)
+        batch.solve(bs, xs, tol=0.0, max_iter=max(args.warmup, 10), f_stars=[-1e300] * len(plans))
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        barrier(ws)
+        with ClockSampler(local) as clk:
+            code, reps = batch.solve(bs, xs, tol=0.0, max_iter=args.steps, f_stars=[-1e300] * len(plans))
+        barrier(ws)
+        ms = reps[0]["time_ms"]
+        t_max = reduce_max(ms, ws)
+        total = reduce_sum(args.steps * len(plans), ws)
+        pix = reduce_sum(args.steps * sum(N * N for N in sides), ws)
+        out[prec] = {"slice_iters_per_s": total / (t_max / 1000.0), "pixel_iters_per_s": pix / (t_max / 1000.0),
+                     "ms_per_batch_iteration": t_max / args.steps, "clocks": clk.summary(),
+                     "gather_parts": [p.info()["gather_parts"] for p in plans[:4]]}
+        batch.close()
+        for p in plans:
+            p.close()
+    if rank == 0:
+        line = {"metric": "batched NCS slice-iterations/s (64 uneven TV-CT slices)", "value":
+                out["fp32"]["slice_iters_per_s"], "unit": "slice-it/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out["fp32"]["ms_per_batch_iteration"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "%d slices, sides %s, round(1.4 side) angles, side + 2 bins, iso TV "
+                                       "lambda 0.005, seed %d" % (len(sides), sorted(set(sides)), args.seed),
+                           "sides": sides, "l2": "working set exceeds L2 (not flushed)"},
+                "variants": out}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,6 +437,8 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ttg-extended", type=int, default=8000)
+    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64"])
+    ap.add_argument("--slices", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -392,7 +447,9 @@ def main():
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
         return
     ws, rank, local = dist_setup()
-    if True:
+    if args.workload == "batch64":
+        run_batch(args, ws, rank, local)
+    else:
         run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist

@@ -89,6 +89,8 @@ typedef struct {
     uint64_t power_seed;   /* seed of the SplitMix64 start vector (default 0) */
     int check_every;       /* objective evaluated every T iterations in the solves (default 10) */
     void* cuda_stream;     /* cudaStream_t to run on, or NULL for a plan-owned stream */
+    int autotune;          /* 1: time the gather's angle slicing and the FFT radix orders at plan
+                              creation and keep the fastest (default 0) */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */
@@ -105,7 +107,7 @@ typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and so
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
  * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
- * check_every 10, NULL stream. */
+ * check_every 10, NULL stream, autotune 0. */
 void ncs_options_default(ncs_options* opt);
 
 /* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).
@@ -155,6 +157,31 @@ int pdhg_solve(ncs_plan* plan, const float* b, const float* bg, float* x,
  * Synchronises. */
 int ncs_power_bound(ncs_plan* plan, double* lambda_max_AtA, double* rho_M);
 
+/* ---- Batches of independent slices ---- */
+
+typedef struct ncs_batch ncs_batch;   /* opaque; a set of plans solved together */
+
+/* Group n_plans distinct plans (any sizes and geometries, same device) into a batch.
+ * The plans stay owned by the caller and must outlive the batch. */
+int ncs_batch_create(ncs_plan* const* plans, int n_plans, ncs_batch** out);
+
+/* Release the batch (not its plans; NULL is a no-op). */
+void ncs_batch_destroy(ncs_batch* batch);
+
+/* Solve every slice with NCS from its x[i] (in: x^0, out: the result) and zero duals,
+ * as ncs_solve does for one plan, with all slices in flight at once: each launch is one
+ * CUDA graph holding a branch per active slice (check_every iterations of plans[0] and
+ * the FP64 objective), forked from and joined into a batch-owned stream, so the slices'
+ * kernels run concurrently.  A slice leaves the batch when it reaches tol (against
+ * f_star[i], or the relative change when f_star is NULL or f_star[i] is NaN), diverges,
+ * or reaches max_iter; the graph is rebuilt for the remaining slices.  b[i], x[i]:
+ * device pointers per slice; bg: NULL or per-slice PET backgrounds (entries NULL for
+ * CT).  reports[i] (may be NULL) gets each slice's iterations, status, f, gap; time_ms is
+ * the batch's wall time.  Synchronises.  Returns NCS_OK if every slice converged, else
+ * an error of a slice, else NCS_NOT_CONVERGED. */
+int ncs_batch_solve(ncs_batch* batch, const float* const* b, const float* const* bg, float* const* x,
+                    double tol, int max_iter, const double* f_star, ncs_report* reports);
+
 /* ---- Operators of the plan (device pointers, asynchronous) ---- */
 
 /* y = K x, the Joseph forward projection (N*N -> n_angles*n_det). */
@@ -179,6 +206,10 @@ int ncs_objective(ncs_plan* plan, const float* x, const float* b, const float* b
  * in FP64, mu[p*N + q] for frequency p along rows and q along columns, to the
  * host array mu_host.  Synchronises. */
 int ncs_get_mu(ncs_plan* plan, double* mu_host);
+
+/* Tuning of the plan: the gather's angle slices per 32 x 32 tile and the FFT radix
+ * order (fft_radices: host array of at least 12 ints; any pointer may be NULL). */
+int ncs_plan_info(const ncs_plan* plan, int* gather_parts, int* fft_radices, int* n_radices);
 
 /* Plan sizes: N, n_angles, n_det. */
 int ncs_plan_sizes(const ncs_plan* plan, int* N, int* n_angles, int* n_det);

@@ -7,6 +7,7 @@ binding.  PyTorch supplies device memory and streams only.
 """
 from .binding import (  # noqa: F401
     Plan,
+    Batch,
     NCSError,
     load_library,
     status_string,

@@ -41,7 +41,8 @@ class Options(ctypes.Structure):
                 ("c_r", ctypes.c_double), ("kappa", ctypes.c_double),
                 ("data", ctypes.c_int), ("tv", ctypes.c_int), ("nonneg", ctypes.c_int), ("prec", ctypes.c_int),
                 ("a3_margin", ctypes.c_double), ("power_max_iter", ctypes.c_int), ("power_tol", ctypes.c_double),
-                ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("autotune", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -83,6 +84,11 @@ SIGNATURES = [
     ("ncs_kernel_name", ctypes.c_char_p, [_I]),
     ("ncs_plan_nnz", _I, [_P, _DP]),
     ("ncs_apply_KT_static", _I, [ctypes.POINTER(Geometry), _I, _P, _P, _P]),
+    ("ncs_plan_info", _I, [_P, _IP, _IP, _IP]),
+    ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
+    ("ncs_batch_destroy", None, [_P]),
+    ("ncs_batch_solve", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _DP,
+                             ctypes.POINTER(Report)]),
 ]
 
 NCS_KERNEL_COUNT = 8
@@ -152,7 +158,7 @@ class Plan:
     def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
                  power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
-                 det_spacing=1.0, det_offset=0.0, angles=None, stream=None):
+                 det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False):
         import torch
         L = load_library()
         self._L = L
@@ -180,6 +186,7 @@ class Plan:
         o.power_tol = float(power_tol)
         o.power_seed = int(power_seed)
         o.check_every = int(check_every)
+        o.autotune = 1 if autotune else 0
         # With no stream given, the plan runs on a side stream that is ordered
         # after torch's current stream on entry to every call and before it on
         # exit, so results are visible to torch without extra synchronisation.
@@ -324,8 +331,63 @@ class Plan:
         _check(self._L.ncs_plan_nnz(self._h, ctypes.byref(v)), "ncs_plan_nnz")
         return v.value
 
+    def info(self):
+        """{"gather_parts": int, "fft_radices": [int, ...]} chosen for this plan."""
+        gp, nr = ctypes.c_int(), ctypes.c_int()
+        rad = (ctypes.c_int * 12)()
+        _check(self._L.ncs_plan_info(self._h, ctypes.byref(gp), rad, ctypes.byref(nr)), "ncs_plan_info")
+        return {"gather_parts": gp.value, "fft_radices": [rad[k] for k in range(nr.value)]}
+
     def mu(self):
         import numpy as np
         out = np.empty(self.n, dtype=np.float64)
         _check(self._L.ncs_get_mu(self._h, out.ctypes.data_as(_DP)), "ncs_get_mu")
         return out.reshape(self.N, self.N)
+
+
+class Batch:
+    """Independent slices solved together (ncs_batch_solve): one CUDA graph with a
+    branch per active slice per launch.  `plans` are Plan objects with distinct
+    streams; they must outlive the batch."""
+
+    def __init__(self, plans):
+        L = load_library()
+        self._L = L
+        self.plans = list(plans)
+        arr = (_P * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(L.ncs_batch_create(arr, len(self.plans), ctypes.byref(h)), "ncs_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ncs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, xs, tol=1e-4, max_iter=2000, f_stars=None, bgs=None):
+        """Solve every slice; bs, xs (and bgs) are lists of CUDA tensors.  Returns
+        (status, [report dict per slice])."""
+        import torch
+        n = len(self.plans)
+        for p in self.plans:
+            p._enter()
+        bp = (_P * n)(*[_ptr(b, "b", p.m).value for b, p in zip(bs, self.plans)])
+        xp = (_P * n)(*[_ptr(x, "x", p.n).value for x, p in zip(xs, self.plans)])
+        gp = None
+        if bgs is not None:
+            gp = (_P * n)(*[(_ptr(g, "bg", p.m).value if g is not None else None) for g, p in zip(bgs, self.plans)])
+        fs = None
+        if f_stars is not None:
+            fs = (ctypes.c_double * n)(*[float("nan") if v is None else float(v) for v in f_stars])
+        reps = (Report * n)()
+        code = self._L.ncs_batch_solve(self._h, bp, gp, xp, float(tol), int(max_iter), fs, reps)
+        for p in self.plans:
+            p._leave()
+        _check(code, "ncs_batch_solve")
+        return code, [r.as_dict() for r in reps]

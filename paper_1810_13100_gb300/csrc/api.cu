@@ -8,6 +8,7 @@
 #include "../../include/ncs.h"
 #include "ncs_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -68,6 +69,14 @@ struct ncs_plan {
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> ev_pool;
     double nnz_K = -1.0;
+};
+
+struct ncs_batch {
+    int dev = 0;
+    std::vector<ncs_plan*> plans;
+    cudaStream_t main = nullptr;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
 };
 
 namespace {
@@ -495,6 +504,8 @@ void free_plan(ncs_plan* p)
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
 }
 
+int autotune_plan(ncs_plan* p);
+
 int build_plan(ncs_plan* p, const ncs_geometry* geom)
 {
     const int N = p->N, na = p->na, nd = p->nd;
@@ -633,10 +644,116 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
         for (double& m : p->mu) m *= f;
         CKS(upload_mu(p));
     }
+    if (p->opt.autotune) CKS(autotune_plan(p));
     return NCS_OK;
 }
 
 int check_plan(const ncs_plan* p) { return p ? NCS_OK : NCS_ERR_BADARG; }
+
+// Time `reps` launches of fn on the plan's stream (ms per launch, CUDA events).
+template <class F>
+int time_launches(ncs_plan* p, int reps, F fn, float* ms)
+{
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    int rc = NCS_OK;
+    for (int k = 0; k < 2 && rc == NCS_OK; ++k) rc = fn();      // warm-up
+    cudaEventRecord(a, p->st);
+    for (int k = 0; k < reps && rc == NCS_OK; ++k) rc = fn();
+    cudaEventRecord(b, p->st);
+    cudaEventSynchronize(b);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *ms = t / reps;
+    return rc;
+}
+
+// Autotuner: the gather's number of angle slices (half, same, double the default)
+// and the order of the FFT radices (distinct permutations), each timed on the plan's
+// own sizes with CUDA events; the fastest is kept.
+int autotune_plan(ncs_plan* p)
+{
+    const int base = p->gparts;
+    int cand[3] = {std::max(1, base / 2), base, std::min(std::min(64, p->na), base * 2)};
+    const int cmax = std::max(cand[2], base);
+    if (cmax > 1) {
+        float* bigger = nullptr;
+        CKS(dalloc(&bigger, (size_t)cmax * NN(p)));
+        cudaFree(p->d_gpart);
+        p->d_gpart = bigger;
+    }
+    float *y = nullptr, *xo = nullptr, *xo2 = nullptr;
+    CKS(dalloc(&y, MM(p)));
+    int rc = dalloc(&xo, NN(p));
+    if (rc == NCS_OK) rc = dalloc(&xo2, NN(p));
+    if (rc == NCS_OK && cudaMemsetAsync(y, 0, MM(p) * sizeof(float), p->st) != cudaSuccess) rc = NCS_ERR_CUDA;
+    if (rc == NCS_OK && cudaMemsetAsync(xo, 0, NN(p) * sizeof(float), p->st) != cudaSuccess) rc = NCS_ERR_CUDA;
+    float best = 1e30f;
+    int best_parts = base;
+    for (int c = 0; c < 3 && rc == NCS_OK; ++c) {
+        if (c > 0 && cand[c] == cand[c - 1]) continue;
+        p->gparts = cand[c];
+        float ms = 0.f;
+        rc = time_launches(p, 5, [&]() {
+            return enq_gather(p, GATHER_R, y, nullptr, 0.f, nullptr, 0.f, xo, nullptr, nullptr, 0.f, p->na);
+        }, &ms);
+        if (ms < best) { best = ms; best_parts = cand[c]; }
+    }
+    p->gparts = best_parts;
+    // FFT radix orders
+    RadixPlan rp0 = p->rp, best_rp = p->rp;
+    std::vector<int> r(rp0.r, rp0.r + rp0.n);
+    std::sort(r.begin(), r.end());
+    best = 1e30f;
+    int tried = 0;
+    do {
+        if (rc != NCS_OK || tried >= 8) break;
+        for (int k = 0; k < rp0.n; ++k) p->rp.r[k] = r[k];
+        float ms = 0.f;
+        rc = time_launches(p, 5, [&]() { return enq_solve(p, xo, p->d_invmu, 1, nullptr, nullptr, xo2); }, &ms);
+        if (ms < best) { best = ms; best_rp = p->rp; }
+        ++tried;
+    } while (std::next_permutation(r.begin(), r.end()));
+    p->rp = best_rp;
+    cudaFree(y);
+    cudaFree(xo);
+    cudaFree(xo2);
+    return rc;
+}
+
+// n_it iterations of NCS (kind 0) or PDHG (kind 1) on the plan's solver state, then
+// the FP64 objective at x copied to the plan's pinned host slot.
+int enq_solve_block(ncs_plan* p, int kind, const float* b, const float* bg, float* x, int n_it)
+{
+    for (int k = 0; k < n_it; ++k) {
+        if (kind == 0) CKS(enq_ncs_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
+        else CKS(enq_pdhg_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
+    }
+    CKS(enq_objective(p, x, b, bg, 0));
+    CK(cudaMemcpyAsync(p->h_pin, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, p->st));
+    return NCS_OK;
+}
+
+// Solver state zeroed for a new solve (and gamma_P for PDHG).
+int prepare_solve(ncs_plan* p, int kind)
+{
+    CKS(ensure_state(p));
+    if (kind == 1) CKS(ensure_gamma_p(p));
+    CK(cudaMemsetAsync(p->d_u, 0, MM(p) * sizeof(float), p->st));
+    CK(cudaMemsetAsync(p->d_v, 0, 2 * NN(p) * sizeof(float), p->st));
+    CK(cudaMemsetAsync(p->d_s, 0, NN(p) * sizeof(float), p->st));
+    return NCS_OK;
+}
+
+// Gap measure of a solve: (f - f*)/|f*|, or the relative change of f when f* is NaN.
+double solve_gap(double f, double f_prev, double f_star)
+{
+    if (std::isfinite(f_star)) return (f - f_star) / std::fabs(f_star);
+    return std::isfinite(f_prev) ? std::fabs(f - f_prev) / std::fabs(f) : std::numeric_limits<double>::quiet_NaN();
+}
 
 int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* x, double tol, int max_iter,
                  double f_star, ncs_report* rep)
@@ -644,21 +761,9 @@ int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* 
     if (!b || !x || max_iter < 1 || !(tol >= 0.0)) return NCS_ERR_BADARG;
     if (!p->kl && bg) return NCS_ERR_BADARG;
     CK(cudaSetDevice(p->dev));
-    CKS(ensure_state(p));
-    if (kind == 1) CKS(ensure_gamma_p(p));
-    CK(cudaMemsetAsync(p->d_u, 0, MM(p) * sizeof(float), p->st));
-    CK(cudaMemsetAsync(p->d_v, 0, 2 * NN(p) * sizeof(float), p->st));
-    CK(cudaMemsetAsync(p->d_s, 0, NN(p) * sizeof(float), p->st));
+    CKS(prepare_solve(p, kind));
     const int T = p->opt.check_every > 0 ? p->opt.check_every : 10;
-    auto enq_block = [&](int n_it) -> int {
-        for (int k = 0; k < n_it; ++k) {
-            if (kind == 0) CKS(enq_ncs_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
-            else CKS(enq_pdhg_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
-        }
-        CKS(enq_objective(p, x, b, bg, 0));
-        CK(cudaMemcpyAsync(p->h_pin, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, p->st));
-        return NCS_OK;
-    };
+    auto enq_block = [&](int n_it) -> int { return enq_solve_block(p, kind, b, bg, x, n_it); };
     // CUDA graph of T iterations + objective, cached per (kind, pointers)
     GraphCache& G = p->graph;
     const void* key[4] = {b, bg, x, nullptr};
@@ -694,8 +799,7 @@ int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* 
         it += n_it;
         f = p->h_pin[0];
         if (!std::isfinite(f)) { status = NCS_ERR_DIVERGED; break; }
-        if (std::isfinite(f_star)) gap = (f - f_star) / std::fabs(f_star);
-        else gap = std::isfinite(f_prev) ? std::fabs(f - f_prev) / std::fabs(f) : gap;
+        gap = solve_gap(f, f_prev, f_star);
         if (std::isfinite(gap) && gap <= tol) { status = NCS_OK; break; }
         f_prev = f;
     }
@@ -742,6 +846,7 @@ void ncs_options_default(ncs_options* o)
     o->power_seed = 0;
     o->check_every = 10;
     o->cuda_stream = nullptr;
+    o->autotune = 0;
 }
 
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,
@@ -929,6 +1034,161 @@ int ncs_plan_sizes(const ncs_plan* p, int* N, int* n_angles, int* n_det)
     if (n_angles) *n_angles = p->na;
     if (n_det) *n_det = p->nd;
     return NCS_OK;
+}
+
+int ncs_plan_info(const ncs_plan* p, int* gather_parts, int* fft_radices, int* n_radices)
+{
+    CKS(check_plan(p));
+    if (gather_parts) *gather_parts = p->gparts;
+    if (n_radices) *n_radices = p->rp.n;
+    if (fft_radices)
+        for (int k = 0; k < p->rp.n; ++k) fft_radices[k] = p->rp.r[k];
+    return NCS_OK;
+}
+
+int ncs_batch_create(ncs_plan* const* plans, int n_plans, ncs_batch** out)
+{
+    if (!out) return NCS_ERR_BADARG;
+    *out = nullptr;
+    if (!plans || n_plans < 1) return NCS_ERR_BADARG;
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return NCS_ERR_BADARG;
+        if (plans[i]->dev != plans[0]->dev) return NCS_ERR_BADARG;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return NCS_ERR_BADARG;
+    }
+    ncs_batch* B = new (std::nothrow) ncs_batch();
+    if (!B) return NCS_ERR_NOMEM;
+    B->dev = plans[0]->dev;
+    B->plans.assign(plans, plans + n_plans);
+    B->join.assign(n_plans, nullptr);
+    bool ok = cudaSetDevice(B->dev) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&B->main, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int i = 0; ok && i < n_plans; ++i)
+        ok = cudaEventCreateWithFlags(&B->join[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        ncs_batch_destroy(B);
+        return NCS_ERR_CUDA;
+    }
+    *out = B;
+    return NCS_OK;
+}
+
+void ncs_batch_destroy(ncs_batch* B)
+{
+    if (!B) return;
+    cudaSetDevice(B->dev);
+    if (B->main) cudaStreamSynchronize(B->main);
+    for (auto e : B->join)
+        if (e) cudaEventDestroy(e);
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->main) cudaStreamDestroy(B->main);
+    delete B;
+}
+
+int ncs_batch_solve(ncs_batch* B, const float* const* b, const float* const* bg, float* const* x, double tol,
+                    int max_iter, const double* f_star, ncs_report* reports)
+{
+    if (!B || !b || !x || max_iter < 1 || !(tol >= 0.0)) return NCS_ERR_BADARG;
+    const int n = (int)B->plans.size();
+    for (int i = 0; i < n; ++i) {
+        if (!b[i] || !x[i]) return NCS_ERR_BADARG;
+        if (!B->plans[i]->kl && bg && bg[i]) return NCS_ERR_BADARG;
+    }
+    CK(cudaSetDevice(B->dev));
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    std::vector<int> status(n, NCS_NOT_CONVERGED), iters(n, 0), active;
+    std::vector<double> f(n, nan), f_prev(n, nan), gap(n, nan);
+    for (int i = 0; i < n; ++i) {
+        ncs_plan* p = B->plans[i];
+        CKS(prepare_solve(p, 0));
+        CK(cudaEventRecord(B->join[i], p->st));
+        CK(cudaStreamWaitEvent(B->main, B->join[i], 0));
+        active.push_back(i);
+    }
+    const int T = B->plans[0]->opt.check_every > 0 ? B->plans[0]->opt.check_every : 10;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, B->main));
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> graph_set;
+    int graph_nit = 0, done = 0, rc = NCS_OK;
+    while (!active.empty() && rc == NCS_OK) {
+        const int n_it = std::min(T, max_iter - done);
+        if (!exec || graph_set != active || graph_nit != n_it) {
+            // one graph: a branch per active slice, forked from and joined into the batch stream
+            if (exec) { cudaGraphExecDestroy(exec); exec = nullptr; }
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(B->main, cudaStreamCaptureModeThreadLocal));
+            cudaEventRecord(B->fork, B->main);
+            for (int i : active) {
+                ncs_plan* p = B->plans[i];
+                p->capturing = true;
+                if (cudaStreamWaitEvent(p->st, B->fork, 0) != cudaSuccess) rc = NCS_ERR_CUDA;
+                if (rc == NCS_OK) rc = enq_solve_block(p, 0, b[i], bg ? bg[i] : nullptr, x[i], n_it);
+                p->capturing = false;
+                if (rc == NCS_OK && (cudaEventRecord(B->join[i], p->st) != cudaSuccess ||
+                                     cudaStreamWaitEvent(B->main, B->join[i], 0) != cudaSuccess))
+                    rc = NCS_ERR_CUDA;
+                if (rc != NCS_OK) break;
+            }
+            cudaError_t e = cudaStreamEndCapture(B->main, &graph);
+            if (rc != NCS_OK || e != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                if (rc == NCS_OK) rc = NCS_ERR_CUDA;
+                break;
+            }
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) { cudaGetLastError(); rc = NCS_ERR_CUDA; break; }
+            graph_set = active;
+            graph_nit = n_it;
+        }
+        if (cudaGraphLaunch(exec, B->main) != cudaSuccess || cudaStreamSynchronize(B->main) != cudaSuccess) {
+            cudaGetLastError();
+            rc = NCS_ERR_CUDA;
+            break;
+        }
+        done += n_it;
+        std::vector<int> still;
+        for (int i : active) {
+            ncs_plan* p = B->plans[i];
+            iters[i] = done;
+            f[i] = p->h_pin[0];
+            if (!std::isfinite(f[i])) { status[i] = NCS_ERR_DIVERGED; continue; }
+            gap[i] = solve_gap(f[i], f_prev[i], f_star ? f_star[i] : nan);
+            if (std::isfinite(gap[i]) && gap[i] <= tol) { status[i] = NCS_OK; continue; }
+            f_prev[i] = f[i];
+            if (done < max_iter) still.push_back(i);
+        }
+        active.swap(still);
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaEventRecord(e1, B->main);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != NCS_OK) return rc;
+    int worst = NCS_OK;
+    for (int i = 0; i < n; ++i) {
+        if (reports) {
+            reports[i].iters = iters[i];
+            reports[i].status = status[i];
+            reports[i].time_ms = ms;
+            reports[i].f = f[i];
+            reports[i].gap = gap[i];
+            reports[i].rho = B->plans[i]->rho;
+        }
+        if (status[i] < 0) worst = status[i];
+        else if (worst == NCS_OK && status[i] != NCS_OK) worst = status[i];
+    }
+    return worst;
 }
 
 int ncs_profile_enable(ncs_plan* p, int on)
