@@ -91,6 +91,8 @@ typedef struct {
     void* cuda_stream;     /* cudaStream_t to run on, or NULL for a plan-owned stream */
     int autotune;          /* 1: time the gather's angle slicing and the FFT radix orders at plan
                               creation and keep the fastest (default 0) */
+    int warm_dual;         /* 1: the solves start the data dual at u^0 = K x^0 - b, consistent with the
+                              given x^0 (L2 data term, FP32 storage); 0: zero duals (default) */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */
@@ -107,7 +109,7 @@ typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and so
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
  * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
- * check_every 10, NULL stream, autotune 0. */
+ * check_every 10, NULL stream, autotune 0, warm_dual 0. */
 void ncs_options_default(ncs_options* opt);
 
 /* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).
@@ -139,7 +141,8 @@ int ncs_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
 int pdhg_step(ncs_plan* plan, float* x, float* u, float* v, float* s,
               const float* b, const float* bg, int n_iter);
 
-/* Solve with NCS from x (in: x^0, out: the result; device, float32) and zero duals, until
+/* Solve with NCS from x (in: x^0, out: the result; device, float32) and zero duals (or the
+ * consistent data dual of ncs_options.warm_dual), until
  * (f - f_star)/|f_star| <= tol (f_star finite) or the relative change of f over
  * one check interval <= tol (f_star NaN), or max_iter iterations.  The FP64
  * objective is evaluated every check_every iterations on the GPU; the loop runs
@@ -194,6 +197,12 @@ int ncs_apply_KT(ncs_plan* plan, const float* y, float* x);
 int ncs_apply_D(ncs_plan* plan, const float* x, float* v);
 int ncs_apply_DT(ncs_plan* plan, const float* v, float* x);
 
+/* Filtered backprojection (not in the paper; a warm start for the solves):
+ * x = (pi / n_angles) K^T q with q = tau (h * b) row by row, h the Ram-Lak kernel of
+ * Kak and Slaney for bin pitch tau (h(0) = 1/(4 tau^2), h(n) = -1/(n^2 pi^2 tau^2) for odd n,
+ * 0 for even n != 0).  b: n_angles*n_det, x: N*N, float32 device pointers.  Asynchronous. */
+int ncs_fbp(ncs_plan* plan, const float* b, float* x);
+
 /* out = M^{-1} r = F^{-1} diag(mu)^{-1} F r with the plan's (rescaled) mu (Sec. 2). */
 int ncs_apply_Minv(ncs_plan* plan, const float* r, float* out);
 
@@ -245,6 +254,40 @@ const char* ncs_kernel_name(int kernel_class);
  * FP32 arithmetic the kernels use (the work of one application of K or K^T is
  * 2 * nnz flops).  Computed once per plan. */
 int ncs_plan_nnz(ncs_plan* plan, double* nnz);
+
+/* ---- Learned warm start (not in the paper; only x^0 changes, so convergence is untouched) ---- */
+
+typedef struct ncs_unet ncs_unet;   /* opaque U-Net for one H x W single-channel image */
+
+/* A U-Net with `levels` resolution levels (channels base, 2 base, ... per level; two 3x3
+ * convolutions + ReLU per level and side; 2x2 average pooling down, nearest 2x upsampling and
+ * concatenation with the skip connection up; a 1x1 head) whose output is added to its input:
+ * y = x + net(x).  Convolutions run on the tensor cores with bfloat16 operands and FP32
+ * accumulation; weights are kept in FP32 and initialised with He's normal from `seed`.
+ * H and W must be multiples of 2^(levels-1).  Errors: NCS_ERR_BADARG, NCS_ERR_UNSUPPORTED,
+ * NCS_ERR_NOMEM. */
+int ncs_unet_create(int H, int W, int levels, int base_channels, uint64_t seed, ncs_unet** out);
+void ncs_unet_destroy(ncs_unet* net);
+
+/* Number of parameters.  Order: per convolution in creation order (encoder levels top down,
+ * two convolutions each; decoder levels bottom up, two each) the weights [Cout][3][3][Cin]
+ * then the biases [Cout]; last the head weights [base] and its bias. */
+size_t ncs_unet_num_params(const ncs_unet* net);
+
+/* Copy the FP32 parameters to (set = 0) or from (set = 1) the host array (num_params floats).
+ * Synchronises. */
+int ncs_unet_params(ncs_unet* net, float* host, int set);
+
+/* y = x + net(x) for one image (device float32 arrays of H*W).  Synchronises. */
+int ncs_unet_forward(ncs_unet* net, const float* x, float* y);
+
+/* Loss mean((x + net(x) - target)^2) and its gradient with respect to every parameter
+ * (grad_host: num_params floats, may be NULL).  Synchronises. */
+int ncs_unet_gradient(ncs_unet* net, const float* x, const float* target, double* loss, float* grad_host);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the loss of one (x, target) pair;
+ * *loss (if not NULL) gets the loss before the step (then synchronises). */
+int ncs_unet_train_step(ncs_unet* net, const float* x, const float* target, float lr, double* loss);
 
 /* ---- Backprojection without device allocation ---- */
 

@@ -42,7 +42,7 @@ class Options(ctypes.Structure):
                 ("data", ctypes.c_int), ("tv", ctypes.c_int), ("nonneg", ctypes.c_int), ("prec", ctypes.c_int),
                 ("a3_margin", ctypes.c_double), ("power_max_iter", ctypes.c_int), ("power_tol", ctypes.c_double),
                 ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("warm_dual", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -85,6 +85,14 @@ SIGNATURES = [
     ("ncs_plan_nnz", _I, [_P, _DP]),
     ("ncs_apply_KT_static", _I, [ctypes.POINTER(Geometry), _I, _P, _P, _P]),
     ("ncs_plan_info", _I, [_P, _IP, _IP, _IP]),
+    ("ncs_fbp", _I, [_P, _P, _P]),
+    ("ncs_unet_create", _I, [_I, _I, _I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
+    ("ncs_unet_destroy", None, [_P]),
+    ("ncs_unet_num_params", ctypes.c_size_t, [_P]),
+    ("ncs_unet_params", _I, [_P, ctypes.POINTER(ctypes.c_float), _I]),
+    ("ncs_unet_forward", _I, [_P, _P, _P]),
+    ("ncs_unet_gradient", _I, [_P, _P, _P, _DP, ctypes.POINTER(ctypes.c_float)]),
+    ("ncs_unet_train_step", _I, [_P, _P, _P, ctypes.c_float, _DP]),
     ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     ("ncs_batch_destroy", None, [_P]),
     ("ncs_batch_solve", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _DP,
@@ -158,7 +166,7 @@ class Plan:
     def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
                  power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
-                 det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False):
+                 det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False, warm_dual=False):
         import torch
         L = load_library()
         self._L = L
@@ -187,6 +195,7 @@ class Plan:
         o.power_seed = int(power_seed)
         o.check_every = int(check_every)
         o.autotune = 1 if autotune else 0
+        o.warm_dual = 1 if warm_dual else 0
         # With no stream given, the plan runs on a side stream that is ordered
         # after torch's current stream on entry to every call and before it on
         # exit, so results are visible to torch without extra synchronisation.
@@ -303,6 +312,12 @@ class Plan:
         self._call("ncs_apply_DT", self._L.ncs_apply_DT, self._h, _ptr(v, "v", 2 * self.n), _ptr(x, "x", self.n))
         return x
 
+    def fbp(self, b, x=None):
+        """Ram-Lak filtered backprojection of the sinogram b."""
+        x = self._out(x, self.n, b)
+        self._call("ncs_fbp", self._L.ncs_fbp, self._h, _ptr(b, "b", self.m), _ptr(x, "x", self.n))
+        return x
+
     def apply_Minv(self, r, out=None):
         out = self._out(out, self.n, r)
         self._call("ncs_apply_Minv", self._L.ncs_apply_Minv, self._h, _ptr(r, "r", self.n), _ptr(out, "out", self.n))
@@ -391,3 +406,69 @@ class Batch:
             p._leave()
         _check(code, "ncs_batch_solve")
         return code, [r.as_dict() for r in reps]
+
+
+class UNet:
+    """The warm-start U-Net of include/ncs.h (y = x + net(x)) for H x W images."""
+
+    def __init__(self, H, W, levels=4, base=32, seed=0):
+        L = load_library()
+        self._L = L
+        h = ctypes.c_void_p()
+        _check(L.ncs_unet_create(int(H), int(W), int(levels), int(base), int(seed), ctypes.byref(h)),
+               "ncs_unet_create")
+        self._h = h
+        self.H, self.W, self.levels, self.base = int(H), int(W), int(levels), int(base)
+        self.n_params = int(L.ncs_unet_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ncs_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(self._L.ncs_unet_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 0),
+               "ncs_unet_params")
+        return out
+
+    def set_params(self, p):
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(self._L.ncs_unet_params(self._h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), 1),
+               "ncs_unet_params")
+
+    def forward(self, x, y=None):
+        import torch
+        torch.cuda.current_stream().synchronize()
+        y = torch.empty(self.H * self.W, dtype=torch.float32, device=x.device) if y is None else y
+        _check(self._L.ncs_unet_forward(self._h, _ptr(x, "x", self.H * self.W), _ptr(y, "y", self.H * self.W)),
+               "ncs_unet_forward")
+        return y
+
+    def gradient(self, x, target):
+        import numpy as np
+        import torch
+        torch.cuda.current_stream().synchronize()
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self._L.ncs_unet_gradient(self._h, _ptr(x, "x", self.H * self.W), _ptr(target, "t", self.H * self.W),
+                                         ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "ncs_unet_gradient")
+        return loss.value, g
+
+    def train_step(self, x, target, lr):
+        import torch
+        torch.cuda.current_stream().synchronize()
+        loss = ctypes.c_double()
+        _check(self._L.ncs_unet_train_step(self._h, _ptr(x, "x", self.H * self.W), _ptr(target, "t", self.H * self.W),
+                                           float(lr), ctypes.byref(loss)), "ncs_unet_train_step")
+        return loss.value

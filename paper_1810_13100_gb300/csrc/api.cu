@@ -39,6 +39,8 @@ struct ncs_plan {
     bool bf = false;                 // duals u, v, s stored as bfloat16 (NCS_BF16_STORE, NCS_BF16_DUALS)
     bool bf_img = false;             // projector images of xbar stored as bfloat16 (NCS_BF16_STORE)
     unsigned long long* d_iter = nullptr;  // device iteration counter (stochastic rounding of bfloat16 duals)
+    float* d_q = nullptr;            // filtered sinogram of ncs_fbp (allocated on first use)
+    double ds = 1.0;                 // detector pitch
     ncs_options opt{};
     cudaStream_t st = nullptr;
     bool own_stream = false;
@@ -499,7 +501,7 @@ void free_plan(ncs_plan* p)
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
     cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s);
-    cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter);
+    cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter); cudaFree(p->d_q);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
 }
@@ -518,6 +520,7 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     }
     // per-angle Joseph coefficients in FP64, rounded once
     const double ds = (geom->det_spacing > 0.0) ? geom->det_spacing : 1.0;
+    p->ds = ds;
     const double cN = 0.5 * (N - 1);
     const double s0 = -0.5 * (nd - 1) * ds + geom->det_offset;
     p->h_ap.resize(na);
@@ -738,11 +741,18 @@ int enq_solve_block(ncs_plan* p, int kind, const float* b, const float* bg, floa
 }
 
 // Solver state zeroed for a new solve (and gamma_P for PDHG).
-int prepare_solve(ncs_plan* p, int kind)
+int prepare_solve(ncs_plan* p, int kind, const float* b, const float* x)
 {
     CKS(ensure_state(p));
     if (kind == 1) CKS(ensure_gamma_p(p));
-    CK(cudaMemsetAsync(p->d_u, 0, MM(p) * sizeof(float), p->st));
+    if (p->opt.warm_dual && !p->kl) {
+        // dual start consistent with x^0: u^0 = K x^0 - b, the gradient of 1/2||.||^2 at K x^0 - b
+        CKS(enq_pairs(p, x, p->d_tmp2, p->d_tmpT2));
+        CKS(enq_K(p, p->d_tmp2, p->d_tmpT2, p->d_u));
+        CK(launch_axpy(-1.0f, b, p->d_u, MM(p), p->st));
+    } else {
+        CK(cudaMemsetAsync(p->d_u, 0, MM(p) * sizeof(float), p->st));
+    }
     CK(cudaMemsetAsync(p->d_v, 0, 2 * NN(p) * sizeof(float), p->st));
     CK(cudaMemsetAsync(p->d_s, 0, NN(p) * sizeof(float), p->st));
     return NCS_OK;
@@ -761,7 +771,7 @@ int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* 
     if (!b || !x || max_iter < 1 || !(tol >= 0.0)) return NCS_ERR_BADARG;
     if (!p->kl && bg) return NCS_ERR_BADARG;
     CK(cudaSetDevice(p->dev));
-    CKS(prepare_solve(p, kind));
+    CKS(prepare_solve(p, kind, b, x));
     const int T = p->opt.check_every > 0 ? p->opt.check_every : 10;
     auto enq_block = [&](int n_it) -> int { return enq_solve_block(p, kind, b, bg, x, n_it); };
     // CUDA graph of T iterations + objective, cached per (kind, pointers)
@@ -847,6 +857,7 @@ void ncs_options_default(ncs_options* o)
     o->check_every = 10;
     o->cuda_stream = nullptr;
     o->autotune = 0;
+    o->warm_dual = 0;
 }
 
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,
@@ -862,6 +873,7 @@ int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, dou
     else ncs_options_default(&o);
     if (o.prec != NCS_FP32 && o.prec != NCS_BF16_STORE && o.prec != NCS_BF16_DUALS) return NCS_ERR_BADARG;
     if (o.nonneg && o.data != NCS_DATA_KL) return NCS_ERR_BADARG;
+    if (o.warm_dual && o.prec != NCS_FP32) return NCS_ERR_BADARG;
     if (o.power_max_iter < 1 || !(o.power_tol >= 0.0)) return NCS_ERR_BADARG;
     RadixPlan rp;
     if (nx % 2 != 0 || nx > 4096 || !factor_radices(nx, &rp)) return NCS_ERR_UNSUPPORTED;
@@ -999,6 +1011,18 @@ int ncs_apply_DT(ncs_plan* p, const float* v, float* x)
     return enq_gather(p, GATHER_R, nullptr, v, 1.0f, nullptr, 0.f, x, nullptr, nullptr, 0.f, 0);
 }
 
+int ncs_fbp(ncs_plan* p, const float* b, float* x)
+{
+    CKS(check_plan(p));
+    if (!b || !x) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    if (!p->d_q) CKS(dalloc(&p->d_q, MM(p)));
+    CK(launch_ramp(b, p->d_q, p->na, p->nd, (float)p->ds, p->st));
+    CKS(enq_gather(p, GATHER_R, p->d_q, nullptr, 0.f, nullptr, 0.f, x, nullptr, nullptr, 0.f, p->na));
+    CK(launch_scale(x, NN(p), (float)(M_PI / p->na), p->st));
+    return NCS_OK;
+}
+
 int ncs_apply_Minv(ncs_plan* p, const float* r, float* out)
 {
     CKS(check_plan(p));
@@ -1103,7 +1127,7 @@ int ncs_batch_solve(ncs_batch* B, const float* const* b, const float* const* bg,
     std::vector<double> f(n, nan), f_prev(n, nan), gap(n, nan);
     for (int i = 0; i < n; ++i) {
         ncs_plan* p = B->plans[i];
-        CKS(prepare_solve(p, 0));
+        CKS(prepare_solve(p, 0, b[i], x[i]));
         CK(cudaEventRecord(B->join[i], p->st));
         CK(cudaStreamWaitEvent(B->main, B->join[i], 0));
         active.push_back(i);

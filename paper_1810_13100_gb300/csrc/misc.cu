@@ -193,6 +193,35 @@ __global__ void k_splitmix(float* x, size_t n, uint64_t seed)
     }
 }
 
+// Ram-Lak filtering of one sinogram row per block (Kak & Slaney's discrete ramp
+// kernel for bin pitch tau: h(0) = 1/(4 tau^2), h(n) = 0 for even n != 0,
+// h(n) = -1/(n^2 pi^2 tau^2) for odd n), q = tau (h * b), as a direct sum.
+__global__ void k_ramp(const float* __restrict__ b, float* __restrict__ q, int n_det, float inv_tau)
+{
+    extern __shared__ float sm[];
+    float* row = sm;                 // n_det values
+    float* c = sm + n_det;           // c[k] = 1 / (2k+1)^2
+    const float* br = b + (size_t)blockIdx.x * n_det;
+    for (int i = threadIdx.x; i < n_det; i += blockDim.x) {
+        row[i] = br[i];
+        const float n = (float)(2 * i + 1);
+        c[i] = 1.0f / (n * n);
+    }
+    __syncthreads();
+    constexpr float kInvPi2 = 0.10132118364233777f;   // 1 / pi^2
+    for (int t = threadIdx.x; t < n_det; t += blockDim.x) {
+        float acc = 0.0f;
+        for (int k = 0; 2 * k + 1 <= t || t + 2 * k + 1 < n_det; ++k) {
+            const int n = 2 * k + 1;
+            float pair = 0.0f;
+            if (t - n >= 0) pair += row[t - n];
+            if (t + n < n_det) pair += row[t + n];
+            acc = fmaf(c[k], pair, acc);
+        }
+        q[(size_t)blockIdx.x * n_det + t] = inv_tau * fmaf(-kInvPi2, acc, 0.25f * row[t]);
+    }
+}
+
 int grid_for(size_t n)
 {
     size_t g = (n + 255) / 256;
@@ -261,6 +290,18 @@ cudaError_t launch_scale(float* a, size_t n, float alpha, cudaStream_t st)
 cudaError_t launch_axpy(float a, const float* x, float* y, size_t n, cudaStream_t st)
 {
     k_axpy<<<grid_for(n), 256, 0, st>>>(a, x, y, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ramp(const float* b, float* q, int n_ang, int n_det, float tau, cudaStream_t st)
+{
+    const size_t smem = (size_t)2 * n_det * sizeof(float);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_ramp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k_ramp<<<n_ang, 256, smem, st>>>(b, q, n_det, 1.0f / tau);
     return cudaGetLastError();
 }
 

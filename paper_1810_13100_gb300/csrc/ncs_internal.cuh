@@ -206,6 +206,8 @@ cudaError_t launch_finalize(const double* p0, int n0, double c0, const double* p
 cudaError_t launch_scale_by_rsqrt(const float* x, float* y, size_t n, const double* nrm2, cudaStream_t st);
 // a = alpha * a
 cudaError_t launch_scale(float* a, size_t n, float alpha, cudaStream_t st);
+// Ram-Lak filtered sinogram q = tau (h * b), one row per angle
+cudaError_t launch_ramp(const float* b, float* q, int n_ang, int n_det, float tau, cudaStream_t st);
 // SplitMix64 uniforms in [-1, 1)
 cudaError_t launch_splitmix(float* x, size_t n, uint64_t seed, cudaStream_t st);
 // y = a*x + y ; y = x

@@ -1,0 +1,116 @@
+"""GPU parity of the warm-start parts (not in the paper) against the FP64 oracle:
+the Ram-Lak filtered backprojection, the consistent dual start u^0 = K x^0 - b,
+and the U-Net's forward output and parameter gradient (the oracle emulates the
+GPU's bfloat16 rounding points, so the remaining differences are FP32 versus
+FP64 accumulation and rare one-ulp bfloat16 rounding flips)."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import f32, oracle_scaled_mu, rel_l2, to_np
+from oracle import cnn as ocnn
+from oracle import fbp as ofbp
+from oracle import operators as oop
+from oracle import solvers as osv
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("N,na,nd,sp", [(96, 140, 130, 1.0), (512, 720, 730, 1.0), (64, 50, 61, 1.5)])
+def test_fbp_parity(N, na, nd, sp):
+    import paper_1810_13100_gb300 as ncs
+    pr = synth.ct_problem(2, N, na, nd, 8, 0.01, det_spacing=sp)
+    g = oop.Geometry(N, na, nd, spacing=sp)
+    plan = ncs.Plan(N, na, nd, 0.01, 1.0, det_spacing=sp, power_max_iter=2)
+    x = plan.fbp(torch.from_numpy(pr["b"].ravel()).cuda())
+    ref = ofbp.fbp(f32(pr["b"]), g)
+    assert rel_l2(to_np(x), ref) <= 2e-5
+    plan.close()
+
+
+def test_warm_dual_start_parity():
+    """From x^0 (a seeded image) with u^0 = K x^0 - b, 10 NCS iterations on the GPU
+    match the oracle's iterations from the same start."""
+    import paper_1810_13100_gb300 as ncs
+    N, na, nd = 96, 140, 130
+    lam, alpha, beta = 0.3, 1.0, 3.0
+    pr = synth.ct_problem(3, N, na, nd, 8, 0.01)
+    g = oop.Geometry(N, na, nd)
+    P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv="iso")
+    x0 = f32(pr["x_true"] + 0.05 * np.random.default_rng(0).standard_normal((N, N)))
+    plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv="iso", warm_dual=True)
+    x = torch.from_numpy(x0.ravel().astype(np.float32)).cuda()
+    plan.solve(torch.from_numpy(pr["b"].ravel()).cuda(), x, tol=0.0, max_iter=10, f_star=-1e300)
+    mus, _ = oracle_scaled_mu(N, na, nd, alpha, beta, 0.0, "iso")
+    st = osv.zero_state(P)
+    st.x = x0.copy()
+    st.u = oop.K(x0, g) - P.b
+    st = osv.run(P, st, 10, osv.circulant_Minv(mus))
+    assert rel_l2(to_np(x), st.x) <= 2e-4
+    plan.close()
+
+
+def rand_params(levels, base, seed):
+    rng = np.random.default_rng(seed)
+    convs, c = ocnn.layout(levels, base)
+    parts = []
+    for cin, cout in convs:
+        parts.append(rng.standard_normal(cout * 9 * cin) * np.sqrt(2.0 / (9 * cin)))
+        parts.append(rng.uniform(-0.05, 0.05, cout))
+    parts.append(rng.standard_normal(c[0]) * 0.1)
+    parts.append(np.array([0.01]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def smooth_image(H, seed):
+    rng = np.random.default_rng(seed)
+    yy, xx = np.meshgrid(np.linspace(-1, 1, H), np.linspace(-1, 1, H), indexing="ij")
+    img = np.zeros((H, H))
+    for _ in range(5):
+        cx, cy, r, v = rng.uniform(-0.6, 0.6), rng.uniform(-0.6, 0.6), rng.uniform(0.1, 0.5), rng.uniform(0.2, 1)
+        img += v * (((xx - cx) ** 2 + (yy - cy) ** 2) < r * r)
+    return (img + 0.05 * rng.standard_normal((H, H))).astype(np.float32)
+
+
+@pytest.mark.parametrize("levels,base,H", [(3, 8, 32), (4, 8, 64), (2, 32, 32)])
+def test_unet_forward_and_gradient_parity(levels, base, H):
+    import paper_1810_13100_gb300 as ncs
+    net = ncs.UNet(H, H, levels=levels, base=base, seed=1)
+    assert net.n_params == ocnn.n_params(levels, base)
+    p = rand_params(levels, base, 7)
+    net.set_params(p)
+    x = smooth_image(H, 1)
+    t = smooth_image(H, 2)
+    xg = torch.from_numpy(x.ravel()).cuda()
+    tg = torch.from_numpy(t.ravel()).cuda()
+    y = to_np(net.forward(xg)).reshape(H, H)
+    loss, grad = net.gradient(xg, tg)
+    oracle = ocnn.UNetOracle(levels, base, emulate=True)
+    loss_ref, grad_ref, y_ref = oracle.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    out_err = rel_l2(y - x, y_ref - x)
+    grad_err = rel_l2(grad, grad_ref)
+    print("levels %d base %d H %d: output rel L2 %.2e, gradient rel L2 %.2e, loss %.6e vs %.6e"
+          % (levels, base, H, out_err, grad_err, loss, loss_ref))
+    assert out_err <= 1e-2
+    assert loss == pytest.approx(loss_ref, rel=1e-3)
+    assert grad_err <= 3e-2
+    # every convolution's weight gradient separately
+    convs, c = ocnn.layout(levels, base)
+    off = 0
+    for cin, cout in convs:
+        nw = cout * 9 * cin
+        assert rel_l2(grad[off:off + nw], grad_ref[off:off + nw]) <= 6e-2
+        off += nw + cout
+    net.close()
+
+
+def test_unet_training_decreases_loss():
+    import paper_1810_13100_gb300 as ncs
+    H = 64
+    net = ncs.UNet(H, H, levels=4, base=8, seed=3)
+    x = torch.from_numpy(smooth_image(H, 5).ravel()).cuda()
+    t = torch.from_numpy((smooth_image(H, 5) * 0.8 + 0.1).ravel()).cuda()
+    losses = [net.train_step(x, t, 1e-3) for _ in range(60)]
+    assert losses[-1] < 0.5 * losses[0], losses[::10]
+    net.close()

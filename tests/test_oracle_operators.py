@@ -161,3 +161,24 @@ def test_D2TD2_dominated_by_periodic_laplacian():
     Lt = ci.Ltilde_matrix(N)
     P = np.kron(np.eye(N), Lt) + np.kron(Lt, np.eye(N))
     assert np.linalg.eigvalsh(P - D2.T @ D2).min() >= -1e-12
+
+
+def test_ramlak_zero_dc_gain_and_fbp_reconstructs_a_disk():
+    """The Ram-Lak kernel sums to zero (its transfer function vanishes at DC:
+    1/4 - (2/pi^2) sum_{odd n} 1/n^2 = 0), and FBP of the exact sinogram of a disk
+    returns the disk (inside ~1, outside ~0)."""
+    from oracle import fbp
+    h = fbp.ramlak(200001)
+    assert abs(h.sum()) < 1e-5
+    N, na, nd = 128, 180, 184
+    disk = Ellipses(np.array([0.1]), np.array([-0.05]), np.array([0.5]), np.array([0.5]),
+                    np.array([0.0]), np.array([1.0]))
+    g = op.Geometry(N, na, nd)
+    sino = synth.radon_ellipses(disk, N, synth.angles(na), synth.det_centres(nd))
+    rec = fbp.fbp(sino, g)
+    truth = synth.rasterize(disk, N)
+    from scipy.ndimage import binary_erosion
+    inside = binary_erosion(truth > 0.5, iterations=3)
+    outside = binary_erosion(truth < 0.5, iterations=3)
+    assert abs(rec[inside].mean() - 1.0) < 0.03
+    assert abs(rec[outside].mean()) < 0.03
