@@ -55,11 +55,13 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def load_fstar(workload, seed):
+def load_golden(workload, seed):
+    """The oracle's reference run for the workload (f*, and a fingerprint of the
+    sinogram it was computed for), or None."""
     path = os.path.join(ROOT, "tests", "golden", "fstar_%s_s%d.json" % (workload, seed))
     try:
         with open(path) as fh:
-            return json.load(fh)["f_star"]
+            return json.load(fh)
     except Exception:
         return None
 
@@ -164,11 +166,23 @@ def barrier(ws):
         dist.barrier()
 
 
-def make_inputs(seed):
+def make_inputs(seed, project):
+    """The seeded workload: b = project(x_true) + noise (synth's recipe)."""
     import synth
     W = synth.WORKLOADS[WORKLOAD]
-    pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+    pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"], project)
     return W, pr
+
+
+def gpu_projector(plan, dev):
+    """x -> K x with the library's projector (the benchmark's inputs are made on the GPU)."""
+    import numpy as np
+    import torch
+
+    def project(x):
+        t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32).ravel()).to(dev)
+        return plan.apply_K(t).cpu().numpy().astype(np.float64)
+    return project
 
 
 # ------------------------------------------------------------------ CPU oracle leg
@@ -178,7 +192,9 @@ def oracle_rate(seed, budget_s=15.0, min_iters=2):
     sample of the workload (iterations from the zero state)."""
     import numpy as np
     from oracle import circulant as oci, operators as oop, solvers as osv
-    W, pr = make_inputs(seed)
+    import synth
+    W0 = synth.WORKLOADS[WORKLOAD]
+    W, pr = make_inputs(seed, oop.projector(W0["N"], W0["n_angles"], W0["n_det"]))
     g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
     P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=NCS_PARAMS["alpha"],
                     beta=NCS_PARAMS["beta"], tv=W["tv"])
@@ -233,11 +249,13 @@ def run_ours(args, ws, rank, local):
     import paper_1810_13100_gb300 as ncs
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    W, pr = make_inputs(args.seed + rank)
+    import synth
+    W = synth.WORKLOADS[WORKLOAD]
     N, na, nd = W["N"], W["n_angles"], W["n_det"]
     n, m = N * N, na * nd
     plan = ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], gamma=NCS_PARAMS["gamma"],
                     tv=W["tv"], check_every=CHECK_EVERY)
+    W, pr = make_inputs(args.seed + rank, gpu_projector(plan, dev))
     b = torch.from_numpy(pr["b"].ravel()).to(dev)
     x = torch.zeros(n, device=dev)
     u = torch.zeros(m, device=dev)
@@ -325,9 +343,16 @@ def run_ours(args, ws, rank, local):
 
     # ---- time to 1e-4 gap, NCS vs PDHG (same GPU, same inputs, zero start)
     ttg = None
-    f_star = load_fstar(WORKLOAD, args.seed + rank)
+    gold = load_golden(WORKLOAD, args.seed + rank)
+    f_star = gold["f_star"] if gold else None
     if not args.skip_ttg and f_star is not None:
         ttg = {"tol": TTG_TOL, "cap": TTG_CAP, "f_star": f_star}
+        if "b_sum" in gold:
+            # the oracle's f* belongs to the sinogram made with its own K; this run's b
+            # (made with the library's K) must agree to float32 rounding
+            bd = b.double()
+            ttg["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
+                                 "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
         xs = torch.zeros(n, device=dev)
         rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
         ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
@@ -389,9 +414,10 @@ def run_batch(args, ws, rank, local):
         plans, bs, xs = [], [], []
         for i, N in enumerate(sides):
             na, nd = int(round(1.4 * N)), N + 2
-            pr = synth.ct_problem(1000 * args.seed + i, N, na, nd, W["n_ellipses"], W["noise_frac"])
             plans.append(ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], tv=W["tv"],
                                   precision=prec, autotune=True, check_every=CHECK_EVERY))
+            pr = synth.ct_problem(1000 * args.seed + i, N, na, nd, W["n_ellipses"], W["noise_frac"],
+                                  gpu_projector(plans[-1], "cuda"))
             bs.append(torch.from_numpy(pr["b"].ravel()).cuda())
             xs.append(torch.zeros(N * N, device="cuda"))
         batch = ncs.Batch(plans)

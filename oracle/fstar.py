@@ -37,11 +37,13 @@ def problem(workload: str, seed: int):
     g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
     p = PARAMS[workload]
     if W["kind"] == "ct":
-        pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+        pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"],
+                              project=lambda x: oop.K(x, g))
         P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=p["alpha"], beta=p["beta"],
                         tv=W["tv"])
     else:
-        pr = synth.pet_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"])
+        pr = synth.pet_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"],
+                               project=lambda x: oop.K(x, g))
         P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=p["alpha"], beta=p["beta"],
                         tv=W["tv"], kind="pet", kappa=1.0, r_bg=pr["r_bg"].astype(np.float64))
     return P, p
@@ -77,7 +79,9 @@ def run(workload: str, seed: int, iters: int, checkpoint: str | None, every: int
     last = [h for h in hist if h[0] >= hist[-1][0] - 1000]
     out = dict(workload=workload, seed=seed, f_star=f_star, iterations=hist[-1][0], rho=rho,
                params=p, decrease_last_1000=last[0][1] - last[-1][1],
-               note="FP64 oracle NCS (Sec. 4.1/4.2 updates) from zero; f_star is the lowest objective seen")
+               b_sum=float(P.b.sum()), b_sumsq=float((P.b * P.b).sum()),
+               note="FP64 oracle NCS (Sec. 4.1/4.2 updates) from zero; f_star is the lowest objective seen; "
+                    "b = K x_true + noise with the oracle's K; b_sum / b_sumsq fingerprint that b")
     path = golden_path(workload, seed)
     with open(path, "w") as fh:
         json.dump(out, fh, indent=1)

@@ -66,6 +66,13 @@ def K(x: np.ndarray, g: Geometry) -> np.ndarray:
     return y
 
 
+def projector(N: int, n_angles: int, n_det: int, spacing: float = 1.0, offset: float = 0.0):
+    """x -> K x for the default angles: the projector passed to the seeded input
+    generator, which makes b = K x_true + noise."""
+    g = Geometry(N, n_angles, n_det, spacing=spacing, offset=offset)
+    return lambda x: K(x, g)
+
+
 def KT(y: np.ndarray, g: Geometry) -> np.ndarray:
     """Exact transpose x = K^T y of the Joseph projector (float64, N x N)."""
     y = np.ascontiguousarray(y, dtype=np.float64).reshape(g.n_angles, g.n_det)

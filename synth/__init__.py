@@ -2,9 +2,10 @@
 
 This module is shared by the FP64 oracle, the tests and the benchmark.  It holds
 none of the method's arithmetic (no discrete projector, no finite differences,
-no circulant solve, no proximal map): the measured data are the exact line
-integrals of an ellipse phantom, so no discretised projector is needed to make
-them.
+no circulant solve, no proximal map): the measured data b = K x_true + noise are
+made with a projector that the caller passes in (the oracle's K in the tests and
+in oracle/fstar.py, the library's K in the benchmark and the warm-start
+pipeline).
 
 Conventions (the paper's Radon transform, Sec. 2, eq. (radon-def)):
   * image x[j, i], N x N, row-major; pixel centre (u, v) = (i - (N-1)/2, (N-1)/2 - j)
@@ -20,6 +21,8 @@ from .phantom import (  # noqa: F401
     radon_ellipses,
     angles,
     det_centres,
+    ct_phantom,
+    ct_data,
     ct_problem,
     pet_problem,
     WORKLOADS,

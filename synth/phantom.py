@@ -1,10 +1,14 @@
-"""Seeded ellipse phantoms, their exact parallel-beam sinograms, and noise.
+"""Seeded ellipse phantoms, their exact parallel-beam line integrals, and noise.
 
 Recipe (the stand-in for the paper's patient / XCAT / PET data of Sec. 5, which
 are not available): x_true is a sum of random ellipses in a [-1, 1]^2 frame,
-b is the exact line integral of the same ellipses along every ray (pixel units)
-plus Gaussian noise (CT) or a Poisson draw (PET).  Every array is rounded once
-to float32 so that the GPU path and the FP64 oracle consume identical values.
+rasterised at the pixel centres and rounded to float32; the measured data are
+b = K x_true + Gaussian noise (CT, sigma = a fraction of max(K x_true)) or a
+Poisson draw with mean s K x_true + r (PET).  K is the CALLER's projector (this
+module holds none): the tests pass the FP64 oracle's, the benchmark the
+library's.  The exact line integrals of the ellipses (`radon_ellipses`) serve
+the tests that pin the projector.  Every returned array is rounded once to
+float32 so the GPU path and the FP64 oracle consume identical values.
 """
 from __future__ import annotations
 
@@ -103,40 +107,55 @@ def _f32(a: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
 
 
-def ct_problem(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int,
-               noise_frac: float, det_spacing: float = 1.0, det_offset: float = 0.0) -> dict:
-    """Seeded TV-CT instance: b = exact projection of the phantom + N(0, sigma^2)
-    with sigma = noise_frac * max(exact projection).  Arrays are float32."""
+def ct_phantom(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int):
+    """First half of a CT instance: (x_true as float32 (N, N), z) with z the seeded
+    standard normal draws of shape (n_angles, n_det) that become the noise.  Draw
+    order: the ellipses, then z."""
     rng = np.random.default_rng(seed)
     ell = draw_ellipses(rng, n_ellipses)
-    x_true = rasterize(ell, N)
-    th = angles(n_angles)
-    sino = radon_ellipses(ell, N, th, det_centres(n_det, det_spacing, det_offset))
-    sigma = noise_frac * float(sino.max())
-    b = sino + rng.normal(0.0, sigma, size=sino.shape)
+    x_true = _f32(rasterize(ell, N))
+    z = rng.standard_normal((n_angles, n_det))
+    return x_true, z
+
+
+def ct_data(Kx: np.ndarray, z: np.ndarray, noise_frac: float):
+    """Second half: b = K x_true + sigma z with sigma = noise_frac * max(K x_true),
+    rounded to float32.  Returns (b, sigma)."""
+    Kx = np.asarray(Kx, dtype=np.float64).reshape(z.shape)
+    sigma = noise_frac * float(Kx.max())
+    return _f32(Kx + sigma * z), sigma
+
+
+def ct_problem(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int,
+               noise_frac: float, project, det_spacing: float = 1.0, det_offset: float = 0.0) -> dict:
+    """Seeded TV-CT instance: b = project(x_true) + N(0, sigma^2) with
+    sigma = noise_frac * max(project(x_true)).  `project` maps the float32 image
+    (N, N) to its (n_angles, n_det) sinogram with the given detector spacing and
+    offset.  Arrays are float32."""
+    x_true, z = ct_phantom(seed, N, n_angles, n_det, n_ellipses)
+    b, sigma = ct_data(project(x_true), z, noise_frac)
     return dict(kind="ct", seed=seed, N=N, n_angles=n_angles, n_det=n_det,
                 det_spacing=det_spacing, det_offset=det_offset,
-                x_true=_f32(x_true), b=_f32(b), sigma=sigma)
+                x_true=x_true, b=b, sigma=sigma)
 
 
-def pet_problem(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int,
+def pet_problem(seed: int, N: int, n_angles: int, n_det: int, n_ellipses: int, project,
                 total_counts: float = 1e6, bg_frac: float = 0.1) -> dict:
-    """Seeded TV-PET instance: y ~ Poisson(s*P + r) where P is the exact
-    projection of the activity phantom, s scales sum(s*P) to total_counts and
-    the uniform background r is bg_frac times the mean of s*P.  Arrays float32;
-    r_bg is a full sinogram-shaped array (uniform)."""
+    """Seeded TV-PET instance: y ~ Poisson(s P + r) with P = project(x_true) of
+    the activity phantom, s scaling sum(s P) to total_counts and the uniform
+    background r = bg_frac times the mean of s P.  Arrays float32 (x_true is
+    returned times s, the image the data measure); r_bg is sinogram-shaped."""
     rng = np.random.default_rng(seed)
     ell = draw_ellipses(rng, n_ellipses)
-    x_true = rasterize(ell, N)
-    th = angles(n_angles)
-    sino = radon_ellipses(ell, N, th, det_centres(n_det))
-    scale = total_counts / float(sino.sum())
-    mean_counts = scale * sino
+    x0 = _f32(rasterize(ell, N))
+    P = np.asarray(project(x0), dtype=np.float64).reshape(n_angles, n_det)
+    scale = total_counts / float(P.sum())
+    mean_counts = scale * P
     r = bg_frac * float(mean_counts.mean())
     y = rng.poisson(mean_counts + r).astype(np.float64)
     return dict(kind="pet", seed=seed, N=N, n_angles=n_angles, n_det=n_det,
                 det_spacing=1.0, det_offset=0.0,
-                x_true=_f32(x_true * scale), b=_f32(y),
+                x_true=_f32(x0.astype(np.float64) * scale), b=_f32(y),
                 r_bg=_f32(np.full_like(y, r)), scale=scale, r=r)
 
 

@@ -1,5 +1,6 @@
 """Shared helpers for the tests: layout conversions between the library's
-device arrays and the oracle's, and error measures.  No method arithmetic."""
+device arrays and the oracle's, error measures, and the oracle's projector for
+the seeded input generator.  No method arithmetic of their own."""
 import numpy as np
 
 
@@ -51,3 +52,9 @@ def oracle_scaled_mu(N, na, nd, alpha, beta, gamma, tv, kappa=0.0, kind="ct"):
         mus, rho = osv.a3_scaled_mu(P, mu0)
         _MU_CACHE[key] = (mus, rho)
     return _MU_CACHE[key]
+
+
+def oproj(N, na, nd, spacing=1.0, offset=0.0):
+    """The oracle's K for synth.ct_problem / pet_problem (b = K x_true + noise)."""
+    from oracle import operators as oop
+    return oop.projector(N, na, nd, spacing=spacing, offset=offset)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import f32, oracle_scaled_mu, rel_l2, to_np
+from helpers import f32, oproj, oracle_scaled_mu, rel_l2, to_np
 from oracle import circulant as oci
 from oracle import operators as oop
 from oracle import solvers as osv
@@ -26,7 +26,7 @@ SLICES = [(48, 60, 70, "aniso", 3), (96, 140, 130, "iso", 4), (64, 90, 92, "anis
 
 def make(N, na, nd, tv, seed, **kw):
     import paper_1810_13100_gb300 as ncs
-    pr = synth.ct_problem(seed, N, na, nd, 8, 0.01)
+    pr = synth.ct_problem(seed, N, na, nd, 8, 0.01, oproj(N, na, nd))
     plan = ncs.Plan(N, na, nd, 0.05, 0.01, beta=0.01, tv=tv, **kw)
     return plan, torch.from_numpy(pr["b"].ravel()).cuda()
 
@@ -54,7 +54,8 @@ def test_batch_iterates_equal_single_solves():
 def test_batch_solve_to_gap_checked_by_oracle():
     import paper_1810_13100_gb300 as ncs
     W = synth.WORKLOADS["ct64"]
-    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"],
+                          oproj(W["N"], W["n_angles"], W["n_det"]))
     with open(os.path.join(ROOT, "tests", "golden", "fstar_ct64_s0.json")) as fh:
         fs = json.load(fh)["f_star"]
     p0 = ncs.Plan(W["N"], W["n_angles"], W["n_det"], W["lam"], 0.01, beta=0.01, tv=W["tv"])

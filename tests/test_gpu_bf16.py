@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import oracle_scaled_mu, rel_l2, to_np, v_to_oracle
+from helpers import oproj, oracle_scaled_mu, rel_l2, to_np, v_to_oracle
 from oracle import operators as oop
 from oracle import solvers as osv
 
@@ -36,14 +36,14 @@ def test_bf16_iterations_against_oracle(kind, tv):
     g = oop.Geometry(N, na, nd)
     if kind == "ct":
         lam, alpha, beta = 0.3, 1.0, 3.0
-        pr = synth.ct_problem(1, N, na, nd, 8, 0.01)
+        pr = synth.ct_problem(1, N, na, nd, 8, 0.01, oproj(N, na, nd))
         b_t, b64 = f32(pr["b"])
         P = osv.Problem(g, b64.reshape(na, nd), lam=lam, alpha=alpha, beta=beta, tv=tv)
         plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, precision="bf16")
         bg_t, kappa = None, 0.0
     else:
         lam, alpha, beta = 0.02, 0.1, 0.1
-        pr = synth.pet_problem(1, N, na, nd, 8, total_counts=2e5)
+        pr = synth.pet_problem(1, N, na, nd, 8, oproj(N, na, nd), total_counts=2e5)
         b_t, b64 = f32(pr["b"])
         bg_t, bg64 = f32(pr["r_bg"])
         P = osv.Problem(g, b64.reshape(na, nd), lam=lam, alpha=alpha, beta=beta, kind="pet", tv=tv, kappa=1.0,
@@ -93,7 +93,8 @@ def test_bf16_solve_objective_floor(prec):
     the duals (NCS_BF16_DUALS) leaves a lower floor."""
     import paper_1810_13100_gb300 as ncs
     W = synth.WORKLOADS["ct64"]
-    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"],
+                          oproj(W["N"], W["n_angles"], W["n_det"]))
     with open(os.path.join(ROOT, "tests", "golden", "fstar_ct64_s0.json")) as fh:
         fs = json.load(fh)["f_star"]
     g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import f32, oracle_scaled_mu, rel_l2, to_np, v_to_oracle
+from helpers import f32, oproj, oracle_scaled_mu, rel_l2, to_np, v_to_oracle
 from oracle import circulant as oci
 from oracle import operators as oop
 from oracle import solvers as osv
@@ -27,13 +27,13 @@ def run_pair(kind, N, na, nd, tv, lam, alpha, beta, iters, solver="ncs", seed=0,
     import paper_1810_13100_gb300 as ncs
     g = oop.Geometry(N, na, nd)
     if kind == "pet":
-        pr = synth.pet_problem(seed, N, na, nd, 8, total_counts=2e5)
+        pr = synth.pet_problem(seed, N, na, nd, 8, oproj(N, na, nd), total_counts=2e5)
         P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, kind="pet", tv=tv, kappa=1.0,
                         r_bg=f32(pr["r_bg"]))
         plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, data="kl", nonneg=True, gamma=gamma)
         bg = torch.from_numpy(pr["r_bg"].ravel()).cuda()
     else:
-        pr = synth.ct_problem(seed, N, na, nd, 8, 0.01)
+        pr = synth.ct_problem(seed, N, na, nd, 8, 0.01, oproj(N, na, nd))
         P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv=tv)
         plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, gamma=gamma)
         bg = None

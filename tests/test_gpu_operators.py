@@ -12,7 +12,7 @@ import math
 import numpy as np
 import pytest
 
-from helpers import f32, oracle_scaled_mu, rel_l2, to_np, v_from_oracle, v_to_oracle
+from helpers import f32, oproj, oracle_scaled_mu, rel_l2, to_np, v_from_oracle, v_to_oracle
 from oracle import circulant as oci
 from oracle import operators as oop
 from oracle import solvers as osv
@@ -142,14 +142,14 @@ def test_objective_parity(kind):
     N, na, nd = 96, 140, 130
     g = oop.Geometry(N, na, nd)
     if kind == "pet":
-        pr = synth.pet_problem(3, N, na, nd, 8, total_counts=1e5)
+        pr = synth.pet_problem(3, N, na, nd, 8, oproj(N, na, nd), total_counts=1e5)
         P = osv.Problem(g, f32(pr["b"]), lam=0.02, alpha=0.1, beta=0.1, kind="pet", kappa=1.0,
                         r_bg=f32(pr["r_bg"]))
         plan = plan_for(N, na, nd, lam=0.02, alpha=0.1, data="kl", nonneg=True, power_max_iter=2)
         x = f32(np.random.default_rng(0).uniform(-0.2, 1.0, (N, N)) * pr["x_true"].max())
         bg = torch.from_numpy(pr["r_bg"].ravel()).cuda()
     else:
-        pr = synth.ct_problem(3, N, na, nd, 8, 0.01)
+        pr = synth.ct_problem(3, N, na, nd, 8, 0.01, oproj(N, na, nd))
         tv = kind.split("_")[1]
         P = osv.Problem(g, f32(pr["b"]), lam=0.3, alpha=1.0, beta=1.0, tv=tv)
         plan = plan_for(N, na, nd, lam=0.3, tv=tv, power_max_iter=2)

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import f32
+from helpers import f32, oproj
 from oracle import operators as oop
 from oracle import solvers as osv
 
@@ -31,7 +31,8 @@ def fstar(name):
 
 def ct64():
     W = synth.WORKLOADS["ct64"]
-    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"])
+    pr = synth.ct_problem(0, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"],
+                          oproj(W["N"], W["n_angles"], W["n_det"]))
     g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
     P = osv.Problem(g, f32(pr["b"]), lam=W["lam"], alpha=0.01, beta=0.01, tv=W["tv"])
     return W, pr, P

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from helpers import f32, oracle_scaled_mu, rel_l2, to_np
+from helpers import f32, oproj, oracle_scaled_mu, rel_l2, to_np
 from oracle import cnn as ocnn
 from oracle import fbp as ofbp
 from oracle import operators as oop
@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("N,na,nd,sp", [(96, 140, 130, 1.0), (512, 720, 730, 1.0), (64, 50, 61, 1.5)])
 def test_fbp_parity(N, na, nd, sp):
     import paper_1810_13100_gb300 as ncs
-    pr = synth.ct_problem(2, N, na, nd, 8, 0.01, det_spacing=sp)
+    pr = synth.ct_problem(2, N, na, nd, 8, 0.01, oproj(N, na, nd, spacing=sp), det_spacing=sp)
     g = oop.Geometry(N, na, nd, spacing=sp)
     plan = ncs.Plan(N, na, nd, 0.01, 1.0, det_spacing=sp, power_max_iter=2)
     x = plan.fbp(torch.from_numpy(pr["b"].ravel()).cuda())
@@ -35,7 +35,7 @@ def test_warm_dual_start_parity():
     import paper_1810_13100_gb300 as ncs
     N, na, nd = 96, 140, 130
     lam, alpha, beta = 0.3, 1.0, 3.0
-    pr = synth.ct_problem(3, N, na, nd, 8, 0.01)
+    pr = synth.ct_problem(3, N, na, nd, 8, 0.01, oproj(N, na, nd))
     g = oop.Geometry(N, na, nd)
     P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv="iso")
     x0 = f32(pr["x_true"] + 0.05 * np.random.default_rng(0).standard_normal((N, N)))

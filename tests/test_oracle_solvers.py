@@ -17,13 +17,14 @@ from oracle import circulant as ci
 from oracle import operators as op
 from oracle import solvers as so
 import synth
+from helpers import oproj
 
 N, NA, ND = 16, 24, 26
 
 
 @pytest.fixture(scope="module")
 def ct16():
-    pr = synth.ct_problem(0, N, NA, ND, 5, 0.01)
+    pr = synth.ct_problem(0, N, NA, ND, 5, 0.01, oproj(N, NA, ND))
     return op.Geometry(N, NA, ND), pr["b"]
 
 
@@ -85,7 +86,7 @@ def ct16_solution(ct16):
     g, b = ct16
     P = so.Problem(g, b, lam=0.5, alpha=1.0, beta=3.0, tv="aniso")
     mus, _ = so.a3_scaled_mu(P, ci.mu_table(g, 1.0, 3.0, 0.0))
-    st = so.run(P, so.zero_state(P), 1800, so.circulant_Minv(mus))
+    st = so.run(P, so.zero_state(P), 3500, so.circulant_Minv(mus))
     return P, mus, st
 
 
@@ -141,7 +142,7 @@ def test_pdhg_converges_to_same_minimiser(ct16, ct16_solution):
 def test_pet_kkt_at_ncs_limit():
     """TV-PET with the nonnegativity row (Sec. 4.2): at the limit the data dual is
     the likelihood gradient 1 - b/(K x + r), A^T u = 0, s <= 0, s x = 0, x >= 0."""
-    pp = synth.pet_problem(0, 16, 24, 17, 5, total_counts=1e4)
+    pp = synth.pet_problem(0, 16, 24, 17, 5, oproj(16, 24, 17), total_counts=1e4)
     g = op.Geometry(16, 24, 17)
     P = so.Problem(g, pp["b"], lam=0.02, alpha=0.1, beta=0.1, kind="pet", kappa=1.0, r_bg=pp["r_bg"])
     mus, _ = so.a3_scaled_mu(P, ci.mu_table(g, 0.1, 0.1, 0.0, kappa=1.0))
