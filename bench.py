@@ -421,6 +421,7 @@ def run_batch(args, ws, rank, local):
             bs.append(torch.from_numpy(pr["b"].ravel()).cuda())
             xs.append(torch.zeros(N * N, device="cuda"))
         batch = ncs.Batch(plans)
+        lanes = batch.tune_lanes(bs, xs, iters=max(args.warmup, 10))     # untimed setup
         batch.solve(bs, xs, tol=0.0, max_iter=max(args.warmup, 10), f_stars=[-1e300] * len(plans))
         for x in xs:
             x.zero_()
@@ -434,7 +435,7 @@ def run_batch(args, ws, rank, local):
         total = reduce_sum(args.steps * len(plans), ws)
         pix = reduce_sum(args.steps * sum(N * N for N in sides), ws)
         out[prec] = {"slice_iters_per_s": total / (t_max / 1000.0), "pixel_iters_per_s": pix / (t_max / 1000.0),
-                     "ms_per_batch_iteration": t_max / args.steps, "clocks": clk.summary(),
+                     "ms_per_batch_iteration": t_max / args.steps, "clocks": clk.summary(), "lanes": lanes,
                      "gather_parts": [p.info()["gather_parts"] for p in plans[:4]]}
         batch.close()
         for p in plans:

@@ -171,6 +171,20 @@ int ncs_batch_create(ncs_plan* const* plans, int n_plans, ncs_batch** out);
 /* Release the batch (not its plans; NULL is a no-op). */
 void ncs_batch_destroy(ncs_batch* batch);
 
+/* At most `lanes` slices of the batch in flight at once (0, the default: all).  Each
+ * launch then chains the slices into `lanes` sequences, largest slice first onto the
+ * least loaded sequence, so fewer slices share the L2 cache at a time.  Errors:
+ * NCS_ERR_BADARG for a negative count. */
+int ncs_batch_set_lanes(ncs_batch* batch, int lanes);
+
+/* Times `iters` NCS iterations of every slice (after one untimed solve of the same
+ * length that builds the graph) with 0 (all), 1, 2, 4, 8 and 16 lanes (those below the
+ * slice count), keeps the fastest as the batch's lane count and returns it in
+ * *lanes_out (may be NULL).  The solves start from and overwrite x; reset x before the
+ * real solve.  Synchronises.  Errors: those of ncs_batch_solve. */
+int ncs_batch_tune_lanes(ncs_batch* batch, const float* const* b, const float* const* bg, float* const* x,
+                         int iters, int* lanes_out);
+
 /* Solve every slice with NCS from its x[i] (in: x^0, out: the result) and zero duals,
  * as ncs_solve does for one plan, with all slices in flight at once: each launch is one
  * CUDA graph holding a branch per active slice (check_every iterations of plans[0] and

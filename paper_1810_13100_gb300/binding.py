@@ -95,6 +95,9 @@ SIGNATURES = [
     ("ncs_unet_train_step", _I, [_P, _P, _P, ctypes.c_float, _DP]),
     ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     ("ncs_batch_destroy", None, [_P]),
+    ("ncs_batch_set_lanes", _I, [_P, _I]),
+    ("ncs_batch_tune_lanes", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _I,
+                                  ctypes.POINTER(_I)]),
     ("ncs_batch_solve", _I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), _D, _I, _DP,
                              ctypes.POINTER(Report)]),
 ]
@@ -373,6 +376,28 @@ class Batch:
         h = ctypes.c_void_p()
         _check(L.ncs_batch_create(arr, len(self.plans), ctypes.byref(h)), "ncs_batch_create")
         self._h = h
+
+    def set_lanes(self, lanes):
+        """At most `lanes` slices in flight at once (0 = all)."""
+        _check(self._L.ncs_batch_set_lanes(self._h, int(lanes)), "ncs_batch_set_lanes")
+
+    def tune_lanes(self, bs, xs, iters=20, bgs=None):
+        """Pick the fastest lane count by timed solves (ncs_batch_tune_lanes); xs are
+        overwritten.  Returns the lane count."""
+        n = len(self.plans)
+        for p in self.plans:
+            p._enter()
+        bp = (_P * n)(*[_ptr(b, "b", p.m).value for b, p in zip(bs, self.plans)])
+        xp = (_P * n)(*[_ptr(x, "x", p.n).value for x, p in zip(xs, self.plans)])
+        gp = None
+        if bgs is not None:
+            gp = (_P * n)(*[(_ptr(g, "bg", p.m).value if g is not None else None) for g, p in zip(bgs, self.plans)])
+        lanes = ctypes.c_int()
+        code = self._L.ncs_batch_tune_lanes(self._h, bp, gp, xp, int(iters), ctypes.byref(lanes))
+        for p in self.plans:
+            p._leave()
+        _check(code, "ncs_batch_tune_lanes")
+        return lanes.value
 
     def close(self):
         if getattr(self, "_h", None):

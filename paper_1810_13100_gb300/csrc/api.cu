@@ -79,6 +79,7 @@ struct ncs_batch {
     cudaStream_t main = nullptr;
     cudaEvent_t fork = nullptr;
     std::vector<cudaEvent_t> join;
+    int lanes = 0;   // slices in flight at once (0 = all)
 };
 
 namespace {
@@ -1100,6 +1101,38 @@ int ncs_batch_create(ncs_plan* const* plans, int n_plans, ncs_batch** out)
     return NCS_OK;
 }
 
+int ncs_batch_set_lanes(ncs_batch* B, int lanes)
+{
+    if (!B || lanes < 0) return NCS_ERR_BADARG;
+    B->lanes = lanes;
+    return NCS_OK;
+}
+
+int ncs_batch_tune_lanes(ncs_batch* B, const float* const* b, const float* const* bg, float* const* x, int iters,
+                         int* lanes_out)
+{
+    if (!B || !b || !x || iters < 1) return NCS_ERR_BADARG;
+    const int n = (int)B->plans.size();
+    std::vector<int> cand = {0};
+    for (int l = 1; l < n && l <= 16; l *= 2) cand.push_back(l);
+    std::vector<ncs_report> rep(n);
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    std::vector<double> fs(n, nan);
+    int best = 0;
+    double best_ms = std::numeric_limits<double>::infinity();
+    for (int l : cand) {
+        B->lanes = l;
+        // a first short solve builds and warms the graph; the second is timed
+        int rc = ncs_batch_solve(B, b, bg, x, 0.0, iters, fs.data(), rep.data());
+        if (rc == NCS_OK || rc == NCS_NOT_CONVERGED) rc = ncs_batch_solve(B, b, bg, x, 0.0, iters, fs.data(), rep.data());
+        if (rc != NCS_OK && rc != NCS_NOT_CONVERGED) return rc;
+        if (rep[0].time_ms < best_ms) { best_ms = rep[0].time_ms; best = l; }
+    }
+    B->lanes = best;
+    if (lanes_out) *lanes_out = best;
+    return NCS_OK;
+}
+
 void ncs_batch_destroy(ncs_batch* B)
 {
     if (!B) return;
@@ -1148,10 +1181,26 @@ int ncs_batch_solve(ncs_batch* B, const float* const* b, const float* const* bg,
             cudaGraph_t graph = nullptr;
             CK(cudaStreamBeginCapture(B->main, cudaStreamCaptureModeThreadLocal));
             cudaEventRecord(B->fork, B->main);
-            for (int i : active) {
+            // With a lane limit each slice waits for the previous slice of its lane
+            // (lanes filled largest slice first, each to the least loaded lane).
+            std::vector<int> order(active), after(n, -1);
+            if (B->lanes > 0 && (int)active.size() > B->lanes) {
+                auto cost = [&](int i) { return (double)NN(B->plans[i]) + (double)MM(B->plans[i]); };
+                std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cost(a) > cost(c); });
+                std::vector<double> load(B->lanes, 0.0);
+                std::vector<int> last(B->lanes, -1);
+                for (int i : order) {
+                    const int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                    after[i] = last[l];
+                    last[l] = i;
+                    load[l] += cost(i);
+                }
+            }
+            for (int i : order) {
                 ncs_plan* p = B->plans[i];
                 p->capturing = true;
-                if (cudaStreamWaitEvent(p->st, B->fork, 0) != cudaSuccess) rc = NCS_ERR_CUDA;
+                cudaEvent_t dep = after[i] >= 0 ? B->join[after[i]] : B->fork;
+                if (cudaStreamWaitEvent(p->st, dep, 0) != cudaSuccess) rc = NCS_ERR_CUDA;
                 if (rc == NCS_OK) rc = enq_solve_block(p, 0, b[i], bg ? bg[i] : nullptr, x[i], n_it);
                 p->capturing = false;
                 if (rc == NCS_OK && (cudaEventRecord(B->join[i], p->st) != cudaSuccess ||

@@ -51,6 +51,35 @@ def test_batch_iterates_equal_single_solves():
         p.close()
 
 
+def test_batch_lanes_keep_iterates_bitwise():
+    """With 1 or 2 lanes (slices chained so fewer run at once) and with the tuned lane
+    count, every slice's iterate after 35 iterations equals the all-concurrent one."""
+    import paper_1810_13100_gb300 as ncs
+    made = [make(*s) for s in SLICES + [(64, 90, 92, "iso", 7)]]
+    plans = [m[0] for m in made]
+    bs = [m[1] for m in made]
+    batch = ncs.Batch(plans)
+    ref = [torch.zeros(p.n, device="cuda") for p in plans]
+    batch.solve(bs, ref, tol=0.0, max_iter=35, f_stars=[-1e300] * len(plans))
+    for lanes in (1, 2, "tuned"):
+        if lanes == "tuned":
+            tmp = [torch.zeros(p.n, device="cuda") for p in plans]
+            got = batch.tune_lanes(bs, tmp, iters=10)
+            assert got in (0, 1, 2, 4)
+        else:
+            batch.set_lanes(lanes)
+        xs = [torch.zeros(p.n, device="cuda") for p in plans]
+        code, reps = batch.solve(bs, xs, tol=0.0, max_iter=35, f_stars=[-1e300] * len(plans))
+        torch.cuda.synchronize()
+        assert all(r["iters"] == 35 for r in reps)
+        assert all(torch.equal(a, c) for a, c in zip(xs, ref)), lanes
+    with pytest.raises(ncs.NCSError):
+        batch.set_lanes(-1)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def test_batch_solve_to_gap_checked_by_oracle():
     import paper_1810_13100_gb300 as ncs
     W = synth.WORKLOADS["ct64"]
