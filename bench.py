@@ -244,6 +244,33 @@ def run_reference(args, ws, rank):
 
 # ------------------------------------------------------------------ GPU leg
 
+def cufft_reference(N, dev, iters=200):
+    """The circulant solve done with cuFFT through torch.fft (rfft2, multiply by a
+    1/mu-shaped table, irfft2 into x - Delta), timed with CUDA events on torch's
+    stream; a reference for the hand-written FFT kernels only, not used by the path."""
+    import torch
+    r = torch.randn(N, N, device=dev)
+    x = torch.randn(N, N, device=dev)
+    inv = torch.rand(N, N // 2 + 1, device=dev)
+
+    def once():
+        d = torch.fft.irfft2(torch.fft.rfft2(r) * inv, s=(N, N))
+        x.sub_(d)
+
+    for _ in range(10):
+        once()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        once()
+    e1.record()
+    torch.cuda.synchronize()
+    return {"cufft_ms": e0.elapsed_time(e1) / iters,
+            "what": "torch.fft.rfft2 -> complex multiply by a table -> irfft2 -> x -= Delta (cuFFT), %dx%d FP32, "
+                    "L2-warm, CUDA events; ours_ms = the three hand-written FFT kernels per iteration" % (N, N)}
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1810_13100_gb300 as ncs
@@ -341,31 +368,59 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": reduce_sum(k_e2e, ws) / reduce_max(dt, ws), "unit": "it/s",
                "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 4 * n}
 
-    # ---- time to 1e-4 gap, NCS vs PDHG (same GPU, same inputs, zero start)
+    # ---- time to 1e-4 gap, NCS vs PDHG (same GPU, same inputs, zero start), on every
+    # seed of the workload that has the oracle's f* (this rank's seed first)
     ttg = None
-    gold = load_golden(WORKLOAD, args.seed + rank)
-    f_star = gold["f_star"] if gold else None
-    if not args.skip_ttg and f_star is not None:
-        ttg = {"tol": TTG_TOL, "cap": TTG_CAP, "f_star": f_star}
-        if "b_sum" in gold:
-            # the oracle's f* belongs to the sinogram made with its own K; this run's b
-            # (made with the library's K) must agree to float32 rounding
-            bd = b.double()
-            ttg["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
-                                 "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
-        xs = torch.zeros(n, device=dev)
-        rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
-        ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-        if rep["status"] != 0 and args.ttg_extended:
+    if not args.skip_ttg:
+        seeds = [args.seed + rank] + [sd for sd in range(5) if sd != args.seed + rank]
+        runs = []
+        pplan = None
+        for sd in seeds:
+            gold = load_golden(WORKLOAD, sd)
+            if not gold:
+                continue
+            f_star = gold["f_star"]
+            bs = b if sd == args.seed + rank else torch.from_numpy(
+                make_inputs(sd, gpu_projector(plan, dev))[1]["b"].ravel()).to(dev)
+            run = {"seed": sd, "f_star": f_star, "oracle_iters": gold.get("iterations")}
+            if "b_sum" in gold:
+                # the oracle's f* belongs to the sinogram made with its own K; this run's b
+                # (made with the library's K) must agree to float32 rounding
+                bd = bs.double()
+                run["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
+                                     "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
+            xs = torch.zeros(n, device=dev)
+            rep = plan.solve(bs, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
+            run["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+            if rep["status"] != 0 and args.ttg_extended:
+                xs.zero_()
+                rep = plan.solve(bs, xs, tol=TTG_TOL, max_iter=args.ttg_extended, f_star=f_star)
+                run["ncs_extended"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+            if pplan is None:
+                pplan = ncs.Plan(N, na, nd, W["lam"], PDHG_PARAMS["alpha"], beta=PDHG_PARAMS["beta"], tv=W["tv"],
+                                 check_every=CHECK_EVERY)
             xs.zero_()
-            rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=args.ttg_extended, f_star=f_star)
-            ttg["ncs_extended"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-        pplan = ncs.Plan(N, na, nd, W["lam"], PDHG_PARAMS["alpha"], beta=PDHG_PARAMS["beta"], tv=W["tv"],
-                         check_every=CHECK_EVERY)
-        xs.zero_()
-        rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
-        ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-        pplan.close()
+            rep = pplan.pdhg_solve(bs, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
+            run["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+            runs.append(run)
+        if pplan is not None:
+            pplan.close()
+        if runs:
+            import statistics
+            ok = [r["ncs"] for r in runs if r["ncs"]["status"] == 0]
+            ttg = {"tol": TTG_TOL, "cap": TTG_CAP, "seeds": [r["seed"] for r in runs], "runs": runs,
+                   "ncs_converged": len(ok),
+                   "ncs_median_ms": statistics.median(r["time_ms"] for r in ok) if ok else None,
+                   "ncs_median_iters": statistics.median(r["iters"] for r in ok) if ok else None,
+                   "pdhg_converged": sum(1 for r in runs if r["pdhg"]["status"] == 0),
+                   "pdhg_median_gap_at_cap": statistics.median(r["pdhg"]["gap"] for r in runs)}
+
+    # ---- cuFFT as a timing reference for the hand-written FFT solve (A2, A3)
+    fft_ref = None
+    if rank == 0:
+        fft_ref = cufft_reference(N, dev)
+        ours = [kern[k] for k in ("fft_rows_fwd", "fft_cols_solve", "fft_rows_inv") if k in kern and kern[k][1]]
+        fft_ref["ours_ms"] = sum(v[0] / v[1] for v in ours) if len(ours) == 3 else None
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -391,7 +446,7 @@ def run_ours(args, ws, rank, local):
             "kernels_ms_per_launch": {k: (v[0] / v[1] if v[1] else None) for k, v in kern.items()},
             "kernel_share": {k: v[0] / max(1e-12, sum(w[0] for w in kern.values())) for k, v in kern.items()},
             "gpu_launches": launches,
-            "e2e": e2e, "time_to_gap": ttg, "cpu_baseline": cpu, "clocks": clk_sum,
+            "e2e": e2e, "time_to_gap": ttg, "cpu_baseline": cpu, "clocks": clk_sum, "fft_reference": fft_ref,
         }
         print(json.dumps(line), flush=True)
     plan.close()

@@ -118,7 +118,11 @@ void ncs_options_default(ncs_options* opt);
  * bound rho = lambda_max(M^{-1} alpha A^T A) of assumption (A3) (Sec. 3) with FP64
  * reductions, and rescales M so that (A3) holds with the margin.  Synchronises.
  * lambda > 0 is the TV weight, alpha > 0 the dual step.
- * Errors: NCS_ERR_BADARG, NCS_ERR_UNSUPPORTED, NCS_ERR_NOMEM, NCS_ERR_CUDA. */
+ * Errors: NCS_ERR_BADARG, NCS_ERR_UNSUPPORTED (also for a user angle whose ray spacing
+ * along the stepped axis, det_spacing / max(|cos|, |sin|), exceeds 1 by less than twice
+ * the FP32 rounding of a crossing difference, ~3e-7 at N = 512: the exact-transpose
+ * gather's two-phase shared-memory sums need rays at least one pixel apart in FP32),
+ * NCS_ERR_NOMEM, NCS_ERR_CUDA. */
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha,
                     const ncs_options* opt, ncs_plan** out);
 

@@ -569,6 +569,15 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
         // H = A_hi t + B_hi q + C_hi is exact only while every partial sum stays below 2^14
         if (std::fabs(hi(A)) * (nd - 1) + std::fabs(hi(B)) * (N - 1) + std::fabs(hi(C)) >= 16384.0)
             return NCS_ERR_UNSUPPORTED;
+        // the gather's two-phase shared-memory sums need consecutive rays to cross a line
+        // at least one pixel apart in FP32 as well: |A| exactly 1, or clear of 1 by twice the rounding of the
+        // difference of two evaluated crossings, 2 (1 + 2 L_max) 2^-24
+        {
+            const double Lmax = std::fabs(A - hi(A)) * (nd - 1) + std::fabs(B - hi(B)) * (N - 1) +
+                                std::fabs(C - hi(C));
+            const double tol = 2.0 * 2.0 * (1.0 + 2.0 * Lmax) * std::ldexp(1.0, -24);
+            if (std::fabs(A) != 1.0 && std::fabs(A) < 1.0 + tol) return NCS_ERR_UNSUPPORTED;
+        }
         q.row = row;
         q.pad0 = q.pad1 = q.pad2 = 0;
     }

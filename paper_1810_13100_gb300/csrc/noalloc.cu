@@ -96,6 +96,12 @@ bool angle_table(const ncs_geometry* geom, int N, std::vector<AngleParam>& ap)
             A = -ds / sn; B = c / sn; C = cN - (s0 + cN * c) / sn; W = 1.0 / std::fabs(sn); invA = -sn / ds;
         }
         if (std::fabs(hi(A)) * (nd - 1) + std::fabs(hi(B)) * (N - 1) + std::fabs(hi(C)) >= 16384.0) return false;
+        {   // rays at least one pixel apart in FP32 (the bound of ncs_plan_create)
+            const double Lmax = std::fabs(A - hi(A)) * (nd - 1) + std::fabs(B - hi(B)) * (N - 1) +
+                                std::fabs(C - hi(C));
+            if (std::fabs(A) != 1.0 && std::fabs(A) < 1.0 + 4.0 * (1.0 + 2.0 * Lmax) * std::ldexp(1.0, -24))
+                return false;
+        }
         AngleParam& q = ap[a];
         q.Ahi = (float)hi(A); q.Alo = (float)(A - hi(A));
         q.Bhi = (float)hi(B); q.Blo = (float)(B - hi(B));

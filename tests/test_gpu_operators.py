@@ -96,6 +96,17 @@ def test_user_angles_with_exact_ties():
     assert rel_l2(to_np(xt), oop.KT(yv, g)) <= TOL
 
 
+def test_angle_too_close_to_an_axis_is_rejected():
+    """Rays 1/cos(1e-4) - 1 = 5e-9 pixels over one pixel apart: in FP32 two rays could
+    share a crossing pixel, so the plan refuses the geometry instead of computing a
+    K^T that is not K's transpose; a ray spacing of exactly one (theta = 0) is fine."""
+    import paper_1810_13100_gb300 as ncs
+    with pytest.raises(ncs.NCSError) as e:
+        plan_for(32, 3, 46, angles=[0.0, 1e-4, 1.0], power_max_iter=2)
+    assert e.value.code == -2
+    plan_for(32, 3, 46, angles=[0.0, 1e-2, 1.0], power_max_iter=2).close()
+
+
 @pytest.mark.parametrize("N", [8, 48, 96, 512])
 def test_finite_differences_parity(N):
     rng = np.random.default_rng(N)
