@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "ct512"
 # NCS / PDHG parameters for this workload, tuned on the {1,3} x 10^p grid (Sec. 5)
-NCS_PARAMS = dict(alpha=0.003, beta=0.003, gamma=0.0)
+NCS_PARAMS = dict(alpha=0.01, beta=0.01, gamma=0.0)
 PDHG_PARAMS = dict(alpha=0.001, beta=0.001)
 CHECK_EVERY = 10
 TTG_TOL = 1e-4
