@@ -55,13 +55,18 @@ static double col_cross(int N, double c, double s, double st, int i)
     return cN - v;
 }
 
+/* Below this many (line, ray) steps a call runs on one thread: the thread start-up
+ * would cost more than the work.  Each output entry is summed by one thread in the
+ * same order either way, so the results do not depend on the thread count. */
+#define OMP_MIN_WORK 2000000L
+
 void oracle_joseph_forward(int N, int n_ang, int n_det,
                            const double* cos_t, const double* sin_t, const int* row_branch,
                            double spacing, double offset,
                            const double* x, double* y)
 {
     double cd = 0.5 * (n_det - 1);
-#pragma omp parallel for schedule(dynamic)
+#pragma omp parallel for schedule(dynamic) if ((long)N * n_ang * n_det > OMP_MIN_WORK)
     for (int a = 0; a < n_ang; ++a) {
         double c = cos_t[a], s = sin_t[a];
         for (int t = 0; t < n_det; ++t) {
@@ -99,7 +104,7 @@ void oracle_joseph_transpose(int N, int n_ang, int n_det,
     double cd = 0.5 * (n_det - 1);
     memset(x, 0, sizeof(double) * (size_t)N * N);
     /* rays stepped over rows: each thread owns one image row */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if ((long)N * n_ang * n_det > OMP_MIN_WORK)
     for (int j = 0; j < N; ++j) {
         for (int a = 0; a < n_ang; ++a) {
             if (!row_branch[a]) continue;
@@ -117,7 +122,7 @@ void oracle_joseph_transpose(int N, int n_ang, int n_det,
         }
     }
     /* rays stepped over columns: each thread owns one image column */
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(static) if ((long)N * n_ang * n_det > OMP_MIN_WORK)
     for (int i = 0; i < N; ++i) {
         for (int a = 0; a < n_ang; ++a) {
             if (row_branch[a]) continue;

@@ -223,7 +223,7 @@ def main(argv=None):
     ap.add_argument("--ellipses", type=int, default=20)
     ap.add_argument("--noise", type=float, default=0.005)
     ap.add_argument("--lam", type=float, default=0.005)
-    ap.add_argument("--alpha", type=float, default=0.003)
+    ap.add_argument("--alpha", type=float, default=0.01)
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--base", type=int, default=32)
     ap.add_argument("--pairs", type=int, default=2000)
