@@ -232,16 +232,34 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int chunks, size_t 
     }
 }
 
-// bias gradient partials: part[chunk][co] = sum over the chunk's pixels of g[p][co]
+// bias gradient partials: part[chunk][co] = sum over the chunk's pixels of g[p][co].
+// With C < blockDim.x the block's threads form L = blockDim.x / C pixel lanes per
+// channel (consecutive threads read consecutive channels of one pixel) and the lanes
+// are summed in lane order; with C >= blockDim.x each thread sums whole channels.
 __global__ void k_colsum(const bf16* __restrict__ g, int ldg, int offg, int HW, int C, int chunk, float* part)
 {
-    const int ch = blockIdx.x;
-    const int co = threadIdx.x;
-    if (co >= C) return;
-    const int pbeg = ch * chunk, pend = min(HW, pbeg + chunk);
+    __shared__ float red[256];
+    const int pbeg = blockIdx.x * chunk, pend = min(HW, pbeg + chunk);
+    if (C >= (int)blockDim.x) {
+        for (int co = threadIdx.x; co < C; co += blockDim.x) {
+            float s = 0.0f;
+            for (int p = pbeg; p < pend; ++p) s += __bfloat162float(g[(size_t)p * ldg + offg + co]);
+            part[(size_t)blockIdx.x * C + co] = s;
+        }
+        return;
+    }
+    const int L = (int)blockDim.x / C;
+    const int co = threadIdx.x % C, lp = threadIdx.x / C;
     float s = 0.0f;
-    for (int p = pbeg; p < pend; ++p) s += __bfloat162float(g[(size_t)p * ldg + offg + co]);
-    part[(size_t)ch * C + co] = s;
+    if (lp < L)
+        for (int p = pbeg + lp; p < pend; p += L) s += __bfloat162float(g[(size_t)p * ldg + offg + co]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int q = 0; q < L; ++q) t += red[q * C + threadIdx.x];
+        part[(size_t)blockIdx.x * C + threadIdx.x] = t;
+    }
 }
 
 // gm = bf16(gin * (y > 0)) (relu) or bf16(gin)
@@ -615,7 +633,9 @@ int backward(ncs_unet* n, const float* x, const float* t, double* loss)
     auto& l0 = n->L[0];
     // head
     {
-        const int C = l0.c, blocks = 64, threads = 128;
+        // per-thread partials [threads][C + 1] within the default 48 KB of shared memory
+        const int C = l0.c, blocks = 64;
+        const int threads = std::max(32, std::min(128, (int)(48 * 1024 / ((C + 1) * sizeof(float))) / 32 * 32));
         const size_t smem = (size_t)threads * (C + 1) * sizeof(float);
         k_head_bwd<<<blocks, threads, smem, n->st>>>(n->dy, l0.out, C, n->w + n->head_w, HW0, l0.g_out, n->part);
         UCK(cudaGetLastError());

@@ -73,7 +73,7 @@ def smooth_image(H, seed):
     return (img + 0.05 * rng.standard_normal((H, H))).astype(np.float32)
 
 
-@pytest.mark.parametrize("levels,base,H", [(3, 8, 32), (4, 8, 64), (2, 32, 32)])
+@pytest.mark.parametrize("levels,base,H", [(3, 8, 32), (4, 8, 64), (2, 32, 32), (2, 160, 8)])
 def test_unet_forward_and_gradient_parity(levels, base, H):
     import paper_1810_13100_gb300 as ncs
     net = ncs.UNet(H, H, levels=levels, base=base, seed=1)
