@@ -523,6 +523,71 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def unet_conv_flops(H, W, levels, base):
+    """FLOPs of one forward pass of the U-Net's 3x3 convolutions (2 per multiply-add)."""
+    c = [base << l for l in range(levels)]
+    f = 0
+    for l in range(levels):
+        hw = (H >> l) * (W >> l)
+        f += 2 * 9 * hw * (1 if l == 0 else c[l - 1]) * c[l] + 2 * 9 * hw * c[l] * c[l]
+    for l in range(levels - 1):
+        hw = (H >> l) * (W >> l)
+        f += 2 * 9 * hw * (c[l + 1] + c[l]) * c[l] + 2 * 9 * hw * c[l] * c[l]
+    return f
+
+
+def run_unet(args, ws, rank, local):
+    """Train steps of the warm-start U-Net (4 levels, base 32, 512x512; forward, backward
+    and Adam in the library's kernels) on a seeded phantom with noise as input and the
+    phantom as target.  One JSON line: train steps/s, with a tensor-core roofline of the
+    convolutions (forward + data gradient + weight gradient) against the measured bf16 peak."""
+    import numpy as np
+    import torch
+    import paper_1810_13100_gb300 as ncs
+    import synth
+    torch.cuda.set_device(local)
+    H, levels, base = 512, 4, 32
+    x_true, z = synth.ct_phantom(args.seed + rank, H, 1, H * H, 20)
+    xin = torch.from_numpy((x_true.ravel() + 0.05 * z.ravel()).astype(np.float32)).cuda()
+    tgt = torch.from_numpy(x_true.ravel()).cuda()
+    net = ncs.UNet(H, H, levels=levels, base=base, seed=args.seed)
+    for _ in range(max(args.warmup, 3)):
+        net.train_step(xin, tgt, 1e-4)
+    torch.cuda.synchronize()
+    barrier(ws)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            net.train_step(xin, tgt, 1e-4)        # synchronises (reads the loss)
+        dt = time.perf_counter() - t0
+    barrier(ws)
+    t_max = reduce_max(dt, ws)
+    steps = reduce_sum(args.steps, ws)
+    ff = unet_conv_flops(H, H, levels, base)
+    # backward: data gradient of every convolution but the first, and every weight gradient
+    first = 2 * 9 * H * H * 1 * base
+    flops = ff + (ff - first) + ff
+    peaks, kind = load_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    ach = flops / (t_max / args.steps) / 1e12
+    t1 = time.perf_counter()
+    for _ in range(20):
+        net.forward(xin)
+    fwd_ms = (time.perf_counter() - t1) / 20 * 1e3
+    net.close()
+    if rank == 0:
+        line = {"metric": "U-Net train steps/s (warm start: 4 levels, base 32, 512x512, bf16 tensor cores)",
+                "value": steps / t_max, "unit": "step/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": 1000.0 * t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": "U-Net 4 levels / base 32 on a 512x512 seeded phantom, Adam, batch 1"},
+                "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                             "traffic": None, "work": "%.4g conv FLOP per train step (forward %.4g)" % (flops, ff),
+                             "peak_kind": "%s (bf16 burst)" % kind},
+                "forward_ms": fwd_ms, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,7 +602,7 @@ def main():
     ap.add_argument("--ttg-extended", type=int, default=8000)
     ap.add_argument("--pdhg-extended", type=int, default=20000,
                     help="PDHG iteration cap on the first seed when it misses the gap within the cap")
-    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64"])
+    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet"])
     ap.add_argument("--slices", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -549,6 +614,8 @@ def main():
     ws, rank, local = dist_setup()
     if args.workload == "batch64":
         run_batch(args, ws, rank, local)
+    elif args.workload == "unet":
+        run_unet(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
