@@ -307,6 +307,14 @@ int ncs_unet_gradient(ncs_unet* net, const float* x, const float* target, double
  * *loss (if not NULL) gets the loss before the step (then synchronises). */
 int ncs_unet_train_step(ncs_unet* net, const float* x, const float* target, float lr, double* loss);
 
+/* Which kernel computes the 3x3 convolutions (forward and data gradient): 1 (the default)
+ * the tcgen05 tensor-core path (accumulators in tensor memory) for every convolution whose
+ * input and output channel counts are multiples of 16, the mma.sync path for the others;
+ * 0 the mma.sync path for all.  The weight gradient always uses mma.sync.  Forward,
+ * gradient and train step return NCS_ERR_TIMEOUT if a tensor-core completion wait gave up
+ * (the results of that call are then invalid).  Errors: NCS_ERR_BADARG. */
+int ncs_unet_set_conv_path(ncs_unet* net, int tensor_cores);
+
 /* ---- Backprojection without device allocation ---- */
 
 /* Largest sizes ncs_apply_KT_static accepts. */

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("ncs_unet_forward", _I, [_P, _P, _P]),
     ("ncs_unet_gradient", _I, [_P, _P, _P, _DP, ctypes.POINTER(ctypes.c_float)]),
     ("ncs_unet_train_step", _I, [_P, _P, _P, ctypes.c_float, _DP]),
+    ("ncs_unet_set_conv_path", _I, [_P, _I]),
     ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     ("ncs_batch_destroy", None, [_P]),
     ("ncs_batch_set_lanes", _I, [_P, _I]),
@@ -489,6 +490,10 @@ class UNet:
                                          ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                "ncs_unet_gradient")
         return loss.value, g
+
+    def set_conv_path(self, tensor_cores=True):
+        """tcgen05 tensor-core convolutions (True, the default) or the mma.sync path (False)."""
+        _check(self._L.ncs_unet_set_conv_path(self._h, 1 if tensor_cores else 0), "ncs_unet_set_conv_path")
 
     def train_step(self, x, target, lr):
         import torch

@@ -15,6 +15,8 @@
 #include "../../include/ncs.h"
 #include "ncs_internal.cuh"
 
+#include <cuda.h>           // CUtensorMap and its enums (the encoder is fetched from the driver at run time)
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled_v12000
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -93,6 +95,7 @@ struct ConvArgs {
     int ldo, offo, out_f32;
     int H, W, Cin, Cout;
     int relu;
+    int* err;             // set to 1 if a tensor-core wait gave up (tcgen05 path)
 };
 
 // out = act(conv3x3(in, w) + bias), zero padding.
@@ -152,6 +155,234 @@ __global__ void __launch_bounds__(128) k_conv3x3(ConvArgs a)
                 else static_cast<bf16*>(a.out)[o] = __float2bfloat16_rn(v);
             }
 }
+
+// ---------------------------------------------------------------------------
+// The same convolution on the 5th-generation tensor cores (tcgen05): an implicit GEMM
+// D[pixel][co] = sum over (tap, ci) of in[pixel + tap][ci] * w[co][tap][ci], with a
+// 128-pixel x BN-channel FP32 accumulator in tensor memory.  Per stage the block
+// stages 64 input channels of one tap (A: 128 x 64, B: BN x 64 bf16, double buffered)
+// in shared memory in the canonical no-swizzle K-major layout (8-row x 16-byte core
+// matrices; LBO = 128 B between the two core matrices of a 16-wide K slab, SBO = 256 B
+// between 8-row groups); one thread issues the K = 16 MMAs and commits them to the
+// stage's mbarrier, which frees the buffer two stages later.  Needs Cin and Cout
+// multiples of 16.
+constexpr int TC_M = 128;                   // pixels per block (MMA M)
+constexpr int TC_KC = 64;                   // input channels per stage
+constexpr unsigned TC_WAIT_LIMIT = 1u << 22; // mbarrier polls (each suspends briefly) before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;                        // descriptor version of the sm_100 family; no swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase)
+{
+    for (unsigned it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok) : "r"(bar), "r"(phase) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Operands arrive by TMA: the input as a 3-D tensor [H][W][Cin] (box: 8 channels x Wb
+// pixels x Rb rows, Rb * Wb = 128 output pixels of the tile; the tap's -1 / +1 pixel
+// offsets are coordinates, and the copy's zero fill outside the tensor is the
+// convolution's zero padding), the weights as a 2-D tensor [Cout][9 Cin] (box: 8 x BN).
+// Each 8-channel box lands as 8-row x 16-byte core matrices stacked along M (or N), so
+// a K = 16 slab is two boxes: LBO = the box size, SBO = 128 B.  A ring of TC_S stages:
+// warp 0 lane 0 issues the copies (full barrier, transaction bytes), warp 1 lane 0 the
+// MMAs, whose commit frees the stage (empty barrier); a final commit releases the
+// epilogue (all four warps read their 32 TMEM lanes).
+struct TcArgs {
+    int H, W, Cin, Cout, BN, ncols, Rb, Wb;
+    const float* bias;
+    void* out;
+    int ldo, offo, out_f32, relu;
+    int* err;
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar) : "memory");
+}
+
+constexpr int TC_S = 4;   // pipeline stages
+
+size_t tc_stage_bytes(int BN) { return (size_t)TC_M * TC_KC * 2 + (size_t)BN * TC_KC * 2; }
+
+__global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUtensorMap tin,
+                                                   const __grid_constant__ CUtensorMap tw, TcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long full[TC_S], empty[TC_S], done;
+    __shared__ uint32_t s_taddr;
+    __shared__ volatile int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int BN = a.BN;
+    const uint32_t a_bytes = TC_M * TC_KC * 2;
+    const uint32_t st_bytes = a_bytes + (uint32_t)BN * TC_KC * 2;
+    const int HW = a.H * a.W;
+    const int p0 = blockIdx.x * TC_M, co0 = blockIdx.y * BN;
+    const int y0 = p0 / a.W, x0 = p0 - y0 * a.W;
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < TC_S; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(a.ncols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const int nch = (a.Cin + TC_KC - 1) / TC_KC;
+    const int stages = 9 * nch;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: TMA copies of stage `it` into ring slot it % TC_S
+            for (int it = 0; it < stages; ++it) {
+                const int s = it % TC_S;
+                if (it >= TC_S && !tc_wait(smem_u32(&empty[s]), (uint32_t)((it / TC_S) - 1) & 1u)) {
+                    s_fail = 1;
+                    break;
+                }
+                if (s_fail) break;
+                const int kk = it / nch, c0 = (it - kk * nch) * TC_KC;
+                const int ng = min(TC_KC, a.Cin - c0) / 8;
+                const uint32_t bytes = (uint32_t)ng * (2048u + (uint32_t)BN * 16u);
+                const uint32_t fb = smem_u32(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
+                const uint32_t As = smem_u32(sm + (size_t)s * st_bytes), Bs = As + a_bytes;
+                const int dy = kk / 3 - 1, dx = kk % 3 - 1;
+                for (int g = 0; g < ng; ++g) {
+                    tma_load_3d(As + (uint32_t)g * 2048u, &tin, c0 + 8 * g, x0 + dx, y0 + dy, fb);
+                    tma_load_2d(Bs + (uint32_t)g * (uint32_t)BN * 16u, &tw, kk * a.Cin + c0 + 8 * g, co0, fb);
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer: K = 16 slabs of each stage into the TMEM accumulator
+            const uint32_t idesc = tc_idesc(TC_M, BN);
+            bool ok = true;
+            for (int it = 0; it < stages; ++it) {
+                const int s = it % TC_S;
+                if (!tc_wait(smem_u32(&full[s]), (uint32_t)(it / TC_S) & 1u)) {
+                    s_fail = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int kk = it / nch, c0 = (it - kk * nch) * TC_KC;
+                const int nk = min(TC_KC, a.Cin - c0) / 16;
+                const uint32_t As = smem_u32(sm + (size_t)s * st_bytes), Bs = As + a_bytes;
+                for (int j = 0; j < nk; ++j) {
+                    const uint64_t ad = tc_smem_desc(As + (uint32_t)j * 4096u, 2048u, 128u);
+                    const uint64_t bd = tc_smem_desc(Bs + (uint32_t)j * 2u * (uint32_t)BN * 16u, (uint32_t)BN * 16u, 128u);
+                    const uint32_t accum = (it > 0 || j > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                        ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&empty[s])) : "memory");
+            }
+            if (ok)
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(smem_u32(&done)) : "memory");
+        }
+        __syncwarp();
+    }
+    if (tid == 0 && !s_fail && !tc_wait(smem_u32(&done), 0u)) s_fail = 1;
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!s_fail) {
+        const int pp = p0 + warp * 32 + lane;           // TMEM lane = A row = pixel of the tile
+        const bool pvec = !a.out_f32 && ((a.ldo | a.offo | co0) & 7) == 0;
+        for (int c = 0; c < BN; c += 16) {
+            uint32_t r[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (pp >= HW) continue;
+            float v[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int co = co0 + c + k;
+                float t = __uint_as_float(r[k]);
+                if (co < a.Cout && a.bias) t += a.bias[co];
+                v[k] = a.relu ? fmaxf(t, 0.0f) : t;
+            }
+            const size_t o = (size_t)pp * a.ldo + a.offo + co0 + c;
+            if (pvec && co0 + c + 16 <= a.Cout) {
+                union { uint4 q[2]; bf16 h[16]; } u;
+#pragma unroll
+                for (int k = 0; k < 16; ++k) u.h[k] = __float2bfloat16_rn(v[k]);
+                *reinterpret_cast<uint4*>(static_cast<bf16*>(a.out) + o) = u.q[0];
+                *reinterpret_cast<uint4*>(static_cast<bf16*>(a.out) + o + 8) = u.q[1];
+            } else {
+                for (int k = 0; k < 16 && co0 + c + k < a.Cout; ++k) {
+                    if (a.out_f32) static_cast<float*>(a.out)[o + k] = v[k];
+                    else static_cast<bf16*>(a.out)[o + k] = __float2bfloat16_rn(v[k]);
+                }
+            }
+        }
+    } else if (tid == 0 && a.err) {
+        atomicExch(a.err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(a.ncols) : "memory");
+}
+
+// Output-channel tile of the tensor-core path for a (Cin, Cout) convolution, or 0 when
+// it does not apply.
+int tc_bn(int Cin, int Cout)
+{
+    if (Cin % 16 || Cout % 16 || Cin < 16) return 0;
+    if (Cout <= 256) return Cout;
+    if (Cout % 256 == 0) return 256;
+    if (Cout % 128 == 0) return 128;
+    return 0;
+}
+
 
 struct WgradArgs {
     const bf16* g;        // g[p * ldg + offg + co] (masked gradient of the conv output)
@@ -485,6 +716,8 @@ struct ncs_unet {
     bf16* gm = nullptr;             // masked bf16 gradient scratch
     float* gtmp = nullptr;          // FP32 gradient scratch
     long long step = 0;
+    int* d_err = nullptr;           // tensor-core wait gave up (checked after each call)
+    int tc = 1;                     // convolutions on tcgen05 where the channel counts allow
     cudaStream_t st = nullptr;
 };
 
@@ -516,6 +749,71 @@ int ualloc(T** p, size_t n)
         if (s_ < 0) return s_;     \
     } while (0)
 
+// The driver's tensor-map encoder (fetched once through the runtime; null if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            f = nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }();
+    return fn;
+}
+
+int launch_conv(ncs_unet* n, ConvArgs a)
+{
+    a.err = n->d_err;
+    const int HW = a.H * a.W;
+    int BN = n->tc ? tc_bn(a.Cin, a.Cout) : 0;
+    int Wb = 0, Rb = 0;
+    if (BN) {
+        if (a.W % TC_M == 0) { Wb = TC_M; Rb = 1; }
+        else if (TC_M % a.W == 0) { Wb = a.W; Rb = TC_M / a.W; }
+        if (!Wb || ((a.ldi | a.offi) & 7) || !tmap_encoder()) BN = 0;
+    }
+    if (BN) {
+        // smaller channel tiles while the grid would not give every SM two blocks
+        const int tiles = (HW + TC_M - 1) / TC_M;
+        while (BN > 64 && tiles * (a.Cout / BN) < 2 * 152 && (BN / 2) % 16 == 0 && a.Cout % (BN / 2) == 0) BN /= 2;
+        const auto enc = tmap_encoder();
+        CUtensorMap tin, tw;
+        const cuuint32_t es[3] = {1, 1, 1};
+        const cuuint64_t gdi[3] = {(cuuint64_t)a.Cin, (cuuint64_t)a.W, (cuuint64_t)a.H};
+        const cuuint64_t gsi[2] = {(cuuint64_t)a.ldi * 2, (cuuint64_t)a.W * a.ldi * 2};
+        const cuuint32_t bxi[3] = {8, (cuuint32_t)Wb, (cuuint32_t)Rb};
+        const cuuint64_t gdw[2] = {(cuuint64_t)9 * a.Cin, (cuuint64_t)a.Cout};
+        const cuuint64_t gsw[1] = {(cuuint64_t)9 * a.Cin * 2};
+        const cuuint32_t bxw[2] = {8, (cuuint32_t)BN};
+        const CUresult r1 = enc(&tin, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(a.in + a.offi), gdi, gsi,
+                                bxi, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const CUresult r2 = enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(a.w), gdw, gsw, bxw, es,
+                                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r1 == CUDA_SUCCESS && r2 == CUDA_SUCCESS) {
+            TcArgs t{};
+            t.H = a.H; t.W = a.W; t.Cin = a.Cin; t.Cout = a.Cout; t.BN = BN;
+            t.ncols = BN <= 32 ? 32 : BN <= 64 ? 64 : BN <= 128 ? 128 : 256;
+            t.Rb = Rb; t.Wb = Wb;
+            t.bias = a.bias; t.out = a.out; t.ldo = a.ldo; t.offo = a.offo; t.out_f32 = a.out_f32; t.relu = a.relu;
+            t.err = a.err;
+            dim3 grid(tiles, a.Cout / BN);
+            k_conv3x3_tc<<<grid, 128, TC_S * tc_stage_bytes(BN), n->st>>>(tin, tw, t);
+            UCK(cudaGetLastError());
+            return NCS_OK;
+        }
+    }
+    dim3 grid((HW + CM - 1) / CM, (a.Cout + CN - 1) / CN);
+    k_conv3x3<<<grid, 128, 0, n->st>>>(a);
+    UCK(cudaGetLastError());
+    return NCS_OK;
+}
+
 int conv_fwd(ncs_unet* n, const ncs_unet::Conv& c, const bf16* in, int ldi, int offi, void* out, int ldo, int offo,
              int out_f32, int H, int W, const bf16* wts, int Cin, int Cout, const float* bias, int relu)
 {
@@ -525,10 +823,7 @@ int conv_fwd(ncs_unet* n, const ncs_unet::Conv& c, const bf16* in, int ldi, int 
     a.out = out; a.ldo = ldo; a.offo = offo; a.out_f32 = out_f32;
     a.H = H; a.W = W; a.Cin = Cin; a.Cout = Cout; a.relu = relu;
     (void)c;
-    dim3 grid((H * W + CM - 1) / CM, (Cout + CN - 1) / CN);
-    k_conv3x3<<<grid, 128, 0, n->st>>>(a);
-    UCK(cudaGetLastError());
-    return NCS_OK;
+    return launch_conv(n, a);
 }
 
 // Backward of one conv: g_out (FP32, HW x Cout, dense) -> masked bf16 -> dW, db (into n->grad), g_in (optional)
@@ -563,9 +858,7 @@ int conv_bwd(ncs_unet* n, const ncs_unet::Conv& c, const float* g_out, const bf1
         d.w = c.wf; d.bias = nullptr;
         d.out = g_in; d.ldo = ld_gin; d.offo = off_gin; d.out_f32 = 1;
         d.H = H; d.W = W; d.Cin = c.Cout; d.Cout = c.Cin; d.relu = 0;
-        dim3 g2((HW + CM - 1) / CM, (c.Cin + CN - 1) / CN);
-        k_conv3x3<<<g2, 128, 0, n->st>>>(d);
-        UCK(cudaGetLastError());
+        UCKS(launch_conv(n, d));
     }
     return NCS_OK;
 }
@@ -712,6 +1005,7 @@ void free_unet(ncs_unet* n)
     }
     cudaFree(n->w); cudaFree(n->m); cudaFree(n->v); cudaFree(n->grad); cudaFree(n->xin);
     cudaFree(n->y); cudaFree(n->dy); cudaFree(n->part); cudaFree(n->dpart); cudaFree(n->gm); cudaFree(n->gtmp);
+    cudaFree(n->d_err);
     if (n->h_pin) cudaFreeHost(n->h_pin);
     if (n->st) cudaStreamDestroy(n->st);
 }
@@ -805,10 +1099,24 @@ int build_unet(ncs_unet* n, uint64_t seed)
     UCKS(ualloc(&n->y, (size_t)n->H * n->W));
     UCKS(ualloc(&n->dy, (size_t)n->H * n->W));
     UCKS(ualloc(&n->dpart, 256));
+    UCKS(ualloc(&n->d_err, 1));
+    UCK(cudaMemsetAsync(n->d_err, 0, sizeof(int), n->st));
+    UCK(cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(TC_S * tc_stage_bytes(256))));
     if (cudaMallocHost((void**)&n->h_pin, 4 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return NCS_ERR_NOMEM; }
     UCKS(refresh_weights(n));
     UCK(cudaStreamSynchronize(n->st));
     return NCS_OK;
+}
+
+// NCS_ERR_TIMEOUT (and the flag cleared) if a tensor-core wait gave up since the last check.
+int check_err(ncs_unet* n)
+{
+    int h = 0;
+    UCK(cudaMemcpyAsync(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->st));
+    UCK(cudaStreamSynchronize(n->st));
+    if (!h) return NCS_OK;
+    UCK(cudaMemsetAsync(n->d_err, 0, sizeof(int), n->st));
+    return NCS_ERR_TIMEOUT;
 }
 
 }  // namespace
@@ -861,8 +1169,7 @@ int ncs_unet_forward(ncs_unet* n, const float* x, float* y)
     UCK(cudaSetDevice(n->dev));
     UCKS(forward(n, x));
     UCK(cudaMemcpyAsync(y, n->y, (size_t)n->H * n->W * sizeof(float), cudaMemcpyDeviceToDevice, n->st));
-    UCK(cudaStreamSynchronize(n->st));
-    return NCS_OK;
+    return check_err(n);
 }
 
 int ncs_unet_gradient(ncs_unet* n, const float* x, const float* target, double* loss, float* grad_host)
@@ -871,11 +1178,8 @@ int ncs_unet_gradient(ncs_unet* n, const float* x, const float* target, double* 
     UCK(cudaSetDevice(n->dev));
     UCKS(forward(n, x));
     UCKS(backward(n, x, target, loss));
-    if (grad_host) {
-        UCK(cudaMemcpyAsync(grad_host, n->grad, n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->st));
-        UCK(cudaStreamSynchronize(n->st));
-    }
-    return NCS_OK;
+    if (grad_host) UCK(cudaMemcpyAsync(grad_host, n->grad, n->n_params * sizeof(float), cudaMemcpyDeviceToHost, n->st));
+    return check_err(n);
 }
 
 int ncs_unet_train_step(ncs_unet* n, const float* x, const float* target, float lr, double* loss)
@@ -891,7 +1195,13 @@ int ncs_unet_train_step(ncs_unet* n, const float* x, const float* target, float 
                                                    nullptr);
     UCK(cudaGetLastError());
     UCKS(refresh_weights(n));
-    if (!loss) UCK(cudaStreamSynchronize(n->st));
+    return check_err(n);
+}
+
+int ncs_unet_set_conv_path(ncs_unet* n, int tensor_cores)
+{
+    if (!n || (tensor_cores != 0 && tensor_cores != 1)) return NCS_ERR_BADARG;
+    n->tc = tensor_cores;
     return NCS_OK;
 }
 

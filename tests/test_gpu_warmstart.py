@@ -148,3 +148,28 @@ def test_learned_start_needs_fewer_iterations_than_fbp_and_zero():
     ws.close()
     for p in plans:
         p.close()
+
+
+def test_unet_tensor_core_path_matches_mma_sync_path():
+    """The tcgen05 convolutions (tensor-memory accumulators) against the mma.sync ones on
+    the 4-level, base-32 512x512 network: same forward output and gradient up to FP32
+    accumulation order (both round the same bf16 operands)."""
+    import paper_1810_13100_gb300 as ncs
+    H = 512
+    x = torch.from_numpy(smooth_image(H, 3).ravel()).cuda()
+    t = torch.from_numpy(smooth_image(H, 4).ravel()).cuda()
+    net = ncs.UNet(H, H, levels=4, base=32, seed=5)
+    p = rand_params(4, 32, 11)
+    net.set_params(p)
+    net.set_conv_path(False)
+    y0 = to_np(net.forward(x))
+    l0, g0 = net.gradient(x, t)
+    net.set_conv_path(True)
+    y1 = to_np(net.forward(x))
+    l1, g1 = net.gradient(x, t)
+    xin = to_np(x)
+    print("tc vs mma.sync: output %.2e, gradient %.2e" % (rel_l2(y1 - xin, y0 - xin), rel_l2(g1, g0)))
+    assert rel_l2(y1 - xin, y0 - xin) <= 5e-3
+    assert l1 == pytest.approx(l0, rel=1e-3)
+    assert rel_l2(g1, g0) <= 2e-2
+    net.close()
