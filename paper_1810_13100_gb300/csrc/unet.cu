@@ -232,7 +232,8 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
 
 constexpr int TC_S = 4;   // pipeline stages
 
-size_t tc_stage_bytes(int BN) { return (size_t)TC_M * TC_KC * 2 + (size_t)BN * TC_KC * 2; }
+// ring-slot bytes for channel tile BN when at most kcm input channels are staged
+size_t tc_stage_bytes(int BN, int kcm) { return ((size_t)TC_M + (size_t)BN) * (size_t)kcm * 2; }
 
 __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUtensorMap tin,
                                                    const __grid_constant__ CUtensorMap tw, TcArgs a)
@@ -243,8 +244,9 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
     __shared__ volatile int s_fail;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int BN = a.BN;
-    const uint32_t a_bytes = TC_M * TC_KC * 2;
-    const uint32_t st_bytes = a_bytes + (uint32_t)BN * TC_KC * 2;
+    const int kcm = min(TC_KC, a.Cin);                 // channels a stage holds at most
+    const uint32_t a_bytes = (uint32_t)TC_M * kcm * 2;
+    const uint32_t st_bytes = a_bytes + (uint32_t)BN * kcm * 2;
     const int HW = a.H * a.W;
     const int p0 = blockIdx.x * TC_M, co0 = blockIdx.y * BN;
     const int y0 = p0 / a.W, x0 = p0 - y0 * a.W;
@@ -803,7 +805,7 @@ int launch_conv(ncs_unet* n, ConvArgs a)
             t.bias = a.bias; t.out = a.out; t.ldo = a.ldo; t.offo = a.offo; t.out_f32 = a.out_f32; t.relu = a.relu;
             t.err = a.err;
             dim3 grid(tiles, a.Cout / BN);
-            k_conv3x3_tc<<<grid, 128, TC_S * tc_stage_bytes(BN), n->st>>>(tin, tw, t);
+            k_conv3x3_tc<<<grid, 128, TC_S * tc_stage_bytes(BN, std::min(TC_KC, a.Cin)), n->st>>>(tin, tw, t);
             UCK(cudaGetLastError());
             return NCS_OK;
         }
@@ -1101,7 +1103,8 @@ int build_unet(ncs_unet* n, uint64_t seed)
     UCKS(ualloc(&n->dpart, 256));
     UCKS(ualloc(&n->d_err, 1));
     UCK(cudaMemsetAsync(n->d_err, 0, sizeof(int), n->st));
-    UCK(cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(TC_S * tc_stage_bytes(256))));
+    UCK(cudaFuncSetAttribute(k_conv3x3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(TC_S * tc_stage_bytes(256, TC_KC))));
     if (cudaMallocHost((void**)&n->h_pin, 4 * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return NCS_ERR_NOMEM; }
     UCKS(refresh_weights(n));
     UCK(cudaStreamSynchronize(n->st));
