@@ -523,6 +523,74 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+PET_NCS = dict(alpha=1.0, beta=1.0)      # {1,3} x 10^p grid (Sec. 5)
+PET_PDHG = dict(alpha=0.1, beta=0.3)
+
+
+def run_pet(args, ws, rank, local):
+    """The 256x256 TV-PET workload (180 angles, 257 bins, 15-ellipse activity, 1e6 counts,
+    10% uniform background, KL data term, anisotropic TV lambda 0.02, nonnegativity): NCS
+    iterations/s, and NCS and PDHG from zero to the 1e-4 relative gap against the oracle's f*."""
+    import numpy as np
+    import torch
+    import paper_1810_13100_gb300 as ncs
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = synth.WORKLOADS["pet256"]
+    N, na, nd = W["N"], W["n_angles"], W["n_det"]
+    seed = args.seed + rank
+    plan = ncs.Plan(N, na, nd, W["lam"], PET_NCS["alpha"], beta=PET_NCS["beta"], data="kl", tv=W["tv"],
+                    nonneg=True, check_every=CHECK_EVERY)
+    pr = synth.pet_problem(seed, N, na, nd, W["n_ellipses"], gpu_projector(plan, dev))
+    b = torch.from_numpy(pr["b"].ravel()).to(dev)
+    bg = torch.from_numpy(pr["r_bg"].ravel()).to(dev)
+    n, m = N * N, na * nd
+    x = torch.zeros(n, device=dev); u = torch.zeros(m, device=dev)
+    v = torch.zeros(2 * n, device=dev); sv = torch.zeros(n, device=dev)
+    plan.step(x, u, v, sv, b, bg, n_iter=max(args.warmup, 3))
+    torch.cuda.synchronize()
+    barrier(ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(plan.stream)
+        plan.step(x, u, v, sv, b, bg, n_iter=args.steps)
+        e1.record(plan.stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    t_max = reduce_max(e0.elapsed_time(e1), ws)
+    rate = reduce_sum(args.steps, ws) / (t_max / 1000.0)
+    ttg = None
+    gold = load_golden("pet256", seed)
+    if gold and not args.skip_ttg:
+        fs = gold["f_star"]
+        ttg = {"tol": TTG_TOL, "f_star": fs, "oracle_iters": gold.get("iterations")}
+        if "b_sum" in gold:
+            bd = b.double()
+            ttg["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
+                                 "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
+        xs = torch.zeros(n, device=dev)
+        rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=20000, f_star=fs, bg=bg)
+        ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        pplan = ncs.Plan(N, na, nd, W["lam"], PET_PDHG["alpha"], beta=PET_PDHG["beta"], data="kl", tv=W["tv"],
+                         nonneg=True, check_every=CHECK_EVERY)
+        xs.zero_()
+        rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=60000, f_star=fs, bg=bg)
+        ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        pplan.close()
+    plan.close()
+    if rank == 0:
+        line = {"metric": "TV-PET NCS iterations/s and time to the 1e-4 gap vs PDHG (256x256)", "value": rate,
+                "unit": "it/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "256x256 TV-PET, 180 angles x 257 bins, 15 ellipses, 1e6 counts, 10%% "
+                                       "background, KL + aniso TV lambda 0.02 + nonnegativity, seed %d" % seed,
+                           "ncs": PET_NCS, "pdhg": PET_PDHG, "l2": "resident (not flushed)"},
+                "time_to_gap": ttg, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def unet_conv_flops(H, W, levels, base):
     """FLOPs of one forward pass of the U-Net's 3x3 convolutions (2 per multiply-add)."""
     c = [base << l for l in range(levels)]
@@ -602,7 +670,7 @@ def main():
     ap.add_argument("--ttg-extended", type=int, default=8000)
     ap.add_argument("--pdhg-extended", type=int, default=20000,
                     help="PDHG iteration cap on the first seed when it misses the gap within the cap")
-    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet"])
+    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256"])
     ap.add_argument("--slices", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -616,6 +684,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.workload == "unet":
         run_unet(args, ws, rank, local)
+    elif args.workload == "pet256":
+        run_pet(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
