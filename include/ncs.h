@@ -260,6 +260,11 @@ int ncs_plan_sizes(const ncs_plan* plan, int* N, int* n_angles, int* n_det);
  * Synchronises. */
 int ncs_profile_enable(ncs_plan* plan, int on);
 
+/* As ncs_profile_enable, for the kernel classes whose bit (1 << NCS_KERNEL_*) is set in
+ * mask only (0: off), so a timed region can carry the events of one kernel alone.
+ * Synchronises. */
+int ncs_profile_enable_mask(ncs_plan* plan, unsigned mask);
+
 /* Sum of the recorded kernel durations (ms) and launch counts per class into
  * ms[NCS_KERNEL_COUNT] and launches[NCS_KERNEL_COUNT] (host arrays), then clear
  * the record.  Synchronises. */

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("ncs_plan_sizes", _I, [_P, _IP, _IP, _IP]),
     ("ncs_status_string", ctypes.c_char_p, [_I]),
     ("ncs_profile_enable", _I, [_P, _I]),
+    ("ncs_profile_enable_mask", _I, [_P, ctypes.c_uint]),
     ("ncs_profile_read", _I, [_P, _DP, _IP]),
     ("ncs_kernel_name", ctypes.c_char_p, [_I]),
     ("ncs_plan_nnz", _I, [_P, _DP]),
@@ -336,6 +337,14 @@ class Plan:
     def profile(self, on=True):
         """Turn per-kernel CUDA-event timing on or off (clears the record)."""
         self._call("ncs_profile_enable", self._L.ncs_profile_enable, self._h, 1 if on else 0)
+
+    def profile_mask(self, classes):
+        """Time only the named kernel classes (ncs_kernel_name names); clears the record."""
+        mask = 0
+        for k in range(NCS_KERNEL_COUNT):
+            if self._L.ncs_kernel_name(k).decode() in classes:
+                mask |= 1 << k
+        self._call("ncs_profile_enable_mask", self._L.ncs_profile_enable_mask, self._h, mask)
 
     def profile_read(self):
         """{kernel name: (total ms, launches)} since the last read, then cleared."""

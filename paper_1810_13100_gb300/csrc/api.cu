@@ -65,7 +65,7 @@ struct ncs_plan {
     float gamma_p = 0.0f;
     GraphCache graph;
     // per-kernel event timing (ncs_profile_enable / ncs_profile_read)
-    bool prof = false;
+    unsigned prof = 0;            // bit k: kernel class k is timed
     bool capturing = false;
     struct Rec { int cls; cudaEvent_t a, b; };
     std::vector<Rec> recs;
@@ -125,7 +125,7 @@ struct ProfScope {
     cudaEvent_t a = nullptr;
     ProfScope(ncs_plan* p_, int cls_) : p(p_), cls(cls_)
     {
-        if (p->prof && !p->capturing && p->recs.size() < kMaxProfRecords) {
+        if (((p->prof >> cls) & 1u) && !p->capturing && p->recs.size() < kMaxProfRecords) {
             a = prof_event(p);
             if (a) cudaEventRecord(a, p->st);
         }
@@ -1273,15 +1273,20 @@ int ncs_batch_solve(ncs_batch* B, const float* const* b, const float* const* bg,
     return worst;
 }
 
-int ncs_profile_enable(ncs_plan* p, int on)
+int ncs_profile_enable_mask(ncs_plan* p, unsigned mask)
 {
     CKS(check_plan(p));
     CK(cudaSetDevice(p->dev));
     CK(cudaStreamSynchronize(p->st));
     for (auto& r : p->recs) { p->ev_pool.push_back(r.a); p->ev_pool.push_back(r.b); }
     p->recs.clear();
-    p->prof = on != 0;
+    p->prof = mask & ((1u << NCS_KERNEL_COUNT) - 1u);
     return NCS_OK;
+}
+
+int ncs_profile_enable(ncs_plan* p, int on)
+{
+    return ncs_profile_enable_mask(p, on ? ~0u : 0u);
 }
 
 int ncs_profile_read(ncs_plan* p, double* ms, int* launches)
