@@ -56,6 +56,7 @@ struct ncs_plan {
     float2 *d_xb2 = nullptr, *d_xbT2 = nullptr, *d_tmp2 = nullptr, *d_tmpT2 = nullptr;
     float2* d_spec = nullptr;
     double *d_part0 = nullptr, *d_part1 = nullptr, *d_scal = nullptr, *h_pin = nullptr;
+    float* d_kx = nullptr;        // running K x of a solve (L2 data)
     float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
     int gparts = 1;                  // angle slices of the gather
     float* d_gpart = nullptr;        // gather scratch: gparts * N * N partial sums
@@ -267,7 +268,8 @@ int enq_td_prox(ncs_plan* p, void* v, void* s)
     return NCS_OK;
 }
 
-int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg)
+int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg, float* kx = nullptr,
+                 double* partials = nullptr)
 {
     FwdArgs f{};
     f.img2 = p->d_xb2;
@@ -284,12 +286,16 @@ int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg)
     f.pair_bf = p->bf_img ? 1 : 0;
     f.sino_bf = p->bf ? 1 : 0;
     f.iter = p->d_iter;
+    f.kx = p->kl ? nullptr : kx;
+    f.partials = f.kx ? partials : nullptr;
     CKP(NCS_KERNEL_FWD, launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
     return NCS_OK;
 }
 
-// One NCS iteration (eq. (NCS), Sec. 4.1 / 4.2).
-int enq_ncs_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* b, const float* bg)
+// One NCS iteration (eq. (NCS), Sec. 4.1 / 4.2).  kx (solves with L2 data): the running
+// K x, advanced to K x+; partials: where the data term at K x+ goes (check iterations).
+int enq_ncs_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* b, const float* bg,
+                 float* kx = nullptr, double* partials = nullptr)
 {
     const void* sv = p->nonneg ? s : nullptr;
     // r = K^T u + (beta/alpha) D^T v + kappa s
@@ -300,18 +306,19 @@ int enq_ncs_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* 
     // v+ = Pi(v + beta D xbar), s+ = min(0, s + alpha kappa xbar), xbar^T
     CKS(enq_td_prox(p, v, s));
     // u+ = prox_{alpha g1*}(u + alpha (K xbar - b))
-    CKS(enq_fwd_prox(p, u, b, bg));
+    CKS(enq_fwd_prox(p, u, b, bg, kx, partials));
     return NCS_OK;
 }
 
-// One PDHG iteration (eq. (PDHG)).
-int enq_pdhg_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* b, const float* bg)
+// One PDHG iteration (eq. (PDHG)); kx, partials as for NCS (xbar = 2 x+ - x here too).
+int enq_pdhg_iter(ncs_plan* p, float* x, void* u, void* v, void* s, const float* b, const float* bg,
+                  float* kx = nullptr, double* partials = nullptr)
 {
     const void* sv = p->nonneg ? s : nullptr;
     CKS(enq_gather(p, GATHER_PDHG, u, v, (float)(p->beta / p->alpha), sv, (float)p->kappa, nullptr, x,
                    p->d_xbar, 1.0f / p->gamma_p, p->na, p->bf));
     CKS(enq_td_prox(p, v, s));
-    CKS(enq_fwd_prox(p, u, b, bg));
+    CKS(enq_fwd_prox(p, u, b, bg, kx, partials));
     return NCS_OK;
 }
 
@@ -479,6 +486,7 @@ int ensure_state(ncs_plan* p)
     if (!p->d_u) CKS(dalloc(&p->d_u, MM(p)));
     if (!p->d_v) CKS(dalloc(&p->d_v, 2 * NN(p)));
     if (!p->d_s) CKS(dalloc(&p->d_s, NN(p)));
+    if (!p->kl && !p->d_kx) CKS(dalloc(&p->d_kx, MM(p)));
     return NCS_OK;
 }
 
@@ -501,7 +509,7 @@ void free_plan(ncs_plan* p)
     cudaFree(p->d_xbar); cudaFree(p->d_r); cudaFree(p->d_tmp);
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
-    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s);
+    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s); cudaFree(p->d_kx);
     cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter); cudaFree(p->d_q);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
@@ -737,15 +745,38 @@ int autotune_plan(ncs_plan* p)
     return rc;
 }
 
+// The TV term of the objective at x, added to the data-term partials already in d_part1
+// (left by the forward pass of the last iteration), into d_scal[slot].
+int enq_objective_tv(ncs_plan* p, const float* x, int slot)
+{
+    TdArgs a{};
+    a.x = x;
+    a.x2 = p->d_tmp2;
+    a.xT2 = p->d_tmpT2;
+    a.clamp = 0;
+    a.N = p->N;
+    a.iso = p->iso ? 1 : 0;
+    a.partials = p->d_part0;
+    CKP(NCS_KERNEL_TD, launch_td(TD_OBJ, a, p->st));
+    CKP(NCS_KERNEL_REDUCE, launch_finalize(p->d_part1, fwd_num_blocks(p->nd, p->na), 0.5, p->d_part0,
+                       td_num_blocks(p->N), p->lam, p->d_scal + slot, p->st));
+    return NCS_OK;
+}
+
 // n_it iterations of NCS (kind 0) or PDHG (kind 1) on the plan's solver state, then
 // the FP64 objective at x copied to the plan's pinned host slot.
 int enq_solve_block(ncs_plan* p, int kind, const float* b, const float* bg, float* x, int n_it)
 {
+    // L2 data: the last iteration's forward pass leaves K x+ and the data term's partials
+    // (Sec. 4.1 objective without another projection); the TV term is summed here
+    float* kx = p->kl ? nullptr : p->d_kx;
     for (int k = 0; k < n_it; ++k) {
-        if (kind == 0) CKS(enq_ncs_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
-        else CKS(enq_pdhg_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg));
+        double* part = (kx && k == n_it - 1) ? p->d_part1 : nullptr;
+        if (kind == 0) CKS(enq_ncs_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg, kx, part));
+        else CKS(enq_pdhg_iter(p, x, p->d_u, p->d_v, p->d_s, b, bg, kx, part));
     }
-    CKS(enq_objective(p, x, b, bg, 0));
+    if (kx) CKS(enq_objective_tv(p, x, 0));
+    else CKS(enq_objective(p, x, b, bg, 0));
     CK(cudaMemcpyAsync(p->h_pin, p->d_scal, sizeof(double), cudaMemcpyDeviceToHost, p->st));
     return NCS_OK;
 }
@@ -765,6 +796,11 @@ int prepare_solve(ncs_plan* p, int kind, const float* b, const float* x)
     }
     CK(cudaMemsetAsync(p->d_v, 0, 2 * NN(p) * sizeof(float), p->st));
     CK(cudaMemsetAsync(p->d_s, 0, NN(p) * sizeof(float), p->st));
+    if (!p->kl) {
+        // running K x of the solve, starting at K x^0
+        CKS(enq_pairs(p, x, p->d_tmp2, p->d_tmpT2));
+        CKS(enq_K(p, p->d_tmp2, p->d_tmpT2, p->d_kx));
+    }
     return NCS_OK;
 }
 

@@ -6,7 +6,8 @@
 // segment; both taps of a step come from one 8-byte load of the pair image.  Partial sums of the segments are combined in shared memory in a
 // fixed order, then a fused epilogue applies prox_{alpha g*} to the data dual
 // (Sec. 4.1: divide by 1 + alpha; Sec. 4.2: the closed-form S(u; c)), or
-// reduces the data term of the objective in FP64.
+// reduces the data term of the objective in FP64.  With L2 data the prox epilogue can
+// also carry the running K x of a solve and the FP64 data term at K x+.
 //
 // K^T (gather, no atomics on data): a block owns a 32 x 32 pixel tile and a
 // slice of the angles.  Each warp takes whole angles and walks the (ray, line)
@@ -107,8 +108,16 @@ k_fwd(FwdArgs g)
         if (MODE == FWD_PLAIN) {
             St<false>::put(g.y, idx, y);
         } else if (MODE == FWD_PROX_L2) {
-            const float z = fmaf(g.alpha, y - St<false>::ld(g.b, idx), St<SBF>::get(g.y, idx));
+            const float bv = St<false>::ld(g.b, idx);
+            const float z = fmaf(g.alpha, y - bv, St<SBF>::get(g.y, idx));
             St<SBF>::put_sr(g.y, idx, z * g.inv1pa, SBF ? rand16(*g.iter, idx, 1u) : 0u);
+            if (g.kx) {
+                // x+ = (xbar + x) / 2, so K x+ = (K xbar + K x) / 2 without another projection
+                const float kxp = 0.5f * (y + g.kx[idx]);
+                g.kx[idx] = kxp;
+                const double d = (double)kxp - (double)bv;
+                term = d * d;
+            }
         } else if (MODE == FWD_PROX_KL) {
             const float bgv = g.bg ? St<false>::ld(g.bg, idx) : 0.0f;
             const float z = fmaf(g.alpha, y + bgv, St<SBF>::get(g.y, idx));
@@ -124,7 +133,7 @@ k_fwd(FwdArgs g)
             if (bb > 0.0) term += bb * log(bb / mu);
         }
     }
-    if (MODE == FWD_RESID_L2 || MODE == FWD_RESID_KL) {
+    if (MODE == FWD_RESID_L2 || MODE == FWD_RESID_KL || (MODE == FWD_PROX_L2 && g.partials)) {
         if (threadIdx.y == 0) dred[threadIdx.x] = term;
         __syncthreads();
         if (threadIdx.y == 0 && threadIdx.x < 32) {

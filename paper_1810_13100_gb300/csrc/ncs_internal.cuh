@@ -119,7 +119,9 @@ struct FwdArgs {
     int sino_bf;         // the dual u (y in PROX modes) stored as bfloat16 (stochastic rounding)
     const unsigned long long* iter;  // device iteration counter (random bits of the rounding)
     float alpha, inv1pa;
-    double* partials;    // RESID: one partial per block (gridDim.x * gridDim.y)
+    double* partials;    // RESID: one partial per block (gridDim.x * gridDim.y); PROX_L2 with kx:
+                         // the same partials of the data term at the running K x+
+    float* kx;           // PROX_L2 or nullptr: running K x, updated to (K xbar + K x) / 2 = K x+
 };
 
 // Gather epilogues.
