@@ -151,15 +151,28 @@ def evaluate(plans, ws: WarmStart | None, sinograms, tol: float = 1e-4, cap: int
         if ws is not None:
             starts["learned"] = [ws.x0(b) for b in bs]
         f0 = {name: [plans[0].objective(x, b) for x, b in zip(xs, bs)] for name, xs in starts.items()}
-        out = {}
+        out, wall = {}, {}
         for name, xs in starts.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             out[name] = solve_batch(plans, batch, bs, xs, tol, cap, f_stars=f_ref)
+            torch.cuda.synchronize()
+            wall[name] = (time.perf_counter() - t0) * 1e3 / len(bs)
+        prep = {"zero": 0.0, "fbp": 0.0, "learned": 0.0}
+        if ws is not None:
+            # the learned start's own cost per slice (FBP + network), timed separately
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for bb in bs:
+                ws.x0(bb)
+            torch.cuda.synchronize()
+            prep["learned"] = (time.perf_counter() - t0) * 1e3 / len(bs)
         for j in range(len(bs)):
             row = {"f_ref": f_ref[j]}
             for name in starts:
                 r = out[name][j]
                 row[name] = {"iters": r["iters"] if r["status"] == 0 else None, "gap0": (f0[name][j] - f_ref[j]) / f_ref[j],
-                             "gap": r["gap"]}
+                             "gap": r["gap"], "batch_ms_per_slice": wall[name] + prep.get(name, 0.0)}
             res.append(row)
         if log:
             log("evaluated %d (%s)" % (len(res), "  ".join(
@@ -283,7 +296,8 @@ def main(argv=None):
             ok = [i for i in its if i is not None]
             summ[nm] = {"converged": len(ok), "of": len(its), "mean_iters": float(np.mean(ok)) if ok else None,
                         "median_iters": float(np.median(ok)) if ok else None,
-                        "mean_gap0": float(np.mean([r[nm]["gap0"] for r in res]))}
+                        "mean_gap0": float(np.mean([r[nm]["gap0"] for r in res])),
+                        "batch_ms_per_slice": float(np.mean([r[nm]["batch_ms_per_slice"] for r in res]))}
         if "learned" in names:
             pair = [(r["zero"]["iters"], r["learned"]["iters"]) for r in res
                     if r["zero"]["iters"] and r["learned"]["iters"]]
