@@ -220,6 +220,20 @@ def oracle_rate(seed, budget_s=15.0, min_iters=2):
                 per_iter=times)
 
 
+def oracle_rate_one_core(seed, budget_s=5.0):
+    """oracle_rate in a child process with OMP_NUM_THREADS=1 (None if it fails)."""
+    import subprocess
+    code = ("import json, bench; r = bench.oracle_rate(%d, budget_s=%r); r.pop('per_iter'); print(json.dumps(r))"
+            % (seed, float(budget_s)))
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=600)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def run_reference(args, ws, rank):
     """The reference arm: the FP64 oracle as it stands, on the host cores."""
     if rank != 0:
@@ -447,6 +461,20 @@ def run_ours(args, ws, rank, local):
         ours = [kern[k] for k in ("fft_rows_fwd", "fft_cols_solve", "fft_rows_inv") if k in kern and kern[k][1]]
         fft_ref["ours_ms"] = sum(v[0] / v[1] for v in ours) if len(ours) == 3 else None
 
+    # ---- algorithmic bytes of the streaming kernels (FP32 state read / written once) and the
+    # projector pair's taps per second, from their event-timed durations
+    hs = 8 * (N // 2 + 1) * N                       # half spectrum, complex64
+    pair = 8 * N * (N + 8)                          # one pair image
+    stream_bytes = {"fft_rows_fwd": 4 * n + hs, "fft_cols_solve": 2 * hs + hs // 2,
+                    "fft_rows_inv": hs + 12 * n, "tv_prox_transpose": 20 * n + 2 * pair}
+    bandwidth = {}
+    for k, nb in stream_bytes.items():
+        if k in kern and kern[k][1]:
+            t = kern[k][0] / kern[k][1] / 1000.0
+            bandwidth[k] = {"bytes_per_launch": nb, "gbs": nb / t / 1e9, "frac_of_hbm": nb / t / 1e9 / hbm}
+    taps = {k: nnz / (kern[k][0] / kern[k][1] / 1000.0) for k in ("joseph_gather", "joseph_fwd")
+            if k in kern and kern[k][1]}
+
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -454,6 +482,14 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": r["rate"], "unit": "it/s", "cores": r["cores"], "kind": "oracle",
                "sample": "%d FP64 oracle NCS iterations of the 512x512 workload from zero (%.1f s)"
                          % (r["iters"], r["seconds"])}
+        one = oracle_rate_one_core(args.seed, budget_s=max(3.0, args.cpu_seconds / 3))
+        if one:
+            cpu["one_core"] = {"value": one["rate"], "unit": "it/s", "cores": 1,
+                               "sample": "%d FP64 oracle NCS iterations, OMP_NUM_THREADS=1 (%.1f s)"
+                                         % (one["iters"], one["seconds"])}
+        if ttg and ttg.get("ncs_median_iters"):
+            cpu["time_to_gap_s_estimate"] = ttg["ncs_median_iters"] / r["rate"]
+            cpu["time_to_gap_estimate_kind"] = "the GPU's iterations to the 1e-4 gap / the oracle's iterations per second"
 
     if rank == 0:
         line = {
@@ -472,6 +508,7 @@ def run_ours(args, ws, rank, local):
             "kernel_share": {k: v[0] / max(1e-12, sum(w[0] for w in kern.values())) for k, v in kern.items()},
             "gpu_launches": launches,
             "e2e": e2e, "time_to_gap": ttg, "cpu_baseline": cpu, "clocks": clk_sum, "fft_reference": fft_ref,
+            "streaming_kernels": bandwidth, "projector_taps_per_s": taps,
         }
         print(json.dumps(line), flush=True)
     plan.close()
