@@ -320,6 +320,12 @@ int ncs_unet_train_step(ncs_unet* net, const float* x, const float* target, floa
  * (the results of that call are then invalid).  Errors: NCS_ERR_BADARG. */
 int ncs_unet_set_conv_path(ncs_unet* net, int tensor_cores);
 
+/* Failure-path test: the tensor-core convolutions of the next forward, gradient or train
+ * step issue no MMAs and give up their completion waits after 4096 polls, so that call
+ * returns NCS_ERR_TIMEOUT with invalid results; the device context stays usable and later
+ * calls are unaffected.  (Nothing else arms this.)  Errors: NCS_ERR_BADARG. */
+int ncs_unet_inject_wait_timeout(ncs_unet* net);
+
 /* ---- Backprojection without device allocation ---- */
 
 /* Largest sizes ncs_apply_KT_static accepts. */

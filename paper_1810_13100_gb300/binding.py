@@ -95,6 +95,7 @@ SIGNATURES = [
     ("ncs_unet_gradient", _I, [_P, _P, _P, _DP, ctypes.POINTER(ctypes.c_float)]),
     ("ncs_unet_train_step", _I, [_P, _P, _P, ctypes.c_float, _DP]),
     ("ncs_unet_set_conv_path", _I, [_P, _I]),
+    ("ncs_unet_inject_wait_timeout", _I, [_P]),
     ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     ("ncs_batch_destroy", None, [_P]),
     ("ncs_batch_set_lanes", _I, [_P, _I]),
@@ -499,6 +500,10 @@ class UNet:
                                          ctypes.byref(loss), g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
                "ncs_unet_gradient")
         return loss.value, g
+
+    def inject_wait_timeout(self):
+        """Failure-path test: the next forward / gradient / train step returns NCS_ERR_TIMEOUT."""
+        _check(self._L.ncs_unet_inject_wait_timeout(self._h), "ncs_unet_inject_wait_timeout")
 
     def set_conv_path(self, tensor_cores=True):
         """tcgen05 tensor-core convolutions (True, the default) or the mma.sync path (False)."""

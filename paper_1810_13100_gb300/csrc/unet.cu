@@ -187,9 +187,9 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase)
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t phase, unsigned limit = TC_WAIT_LIMIT)
 {
-    for (unsigned it = 0; it < TC_WAIT_LIMIT; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
@@ -214,6 +214,8 @@ struct TcArgs {
     void* out;
     int ldo, offo, out_f32, relu;
     int* err;
+    unsigned wait_limit;  // mbarrier polls before a wait gives up
+    int no_mma;           // failure-path test: issue no MMAs or commits, so the waits run out
 };
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar)
@@ -275,7 +277,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
             // producer: TMA copies of stage `it` into ring slot it % TC_S
             for (int it = 0; it < stages; ++it) {
                 const int s = it % TC_S;
-                if (it >= TC_S && !tc_wait(smem_u32(&empty[s]), (uint32_t)((it / TC_S) - 1) & 1u)) {
+                if (it >= TC_S && !tc_wait(smem_u32(&empty[s]), (uint32_t)((it / TC_S) - 1) & 1u, a.wait_limit)) {
                     s_fail = 1;
                     break;
                 }
@@ -301,11 +303,12 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
             bool ok = true;
             for (int it = 0; it < stages; ++it) {
                 const int s = it % TC_S;
-                if (!tc_wait(smem_u32(&full[s]), (uint32_t)(it / TC_S) & 1u)) {
+                if (!tc_wait(smem_u32(&full[s]), (uint32_t)(it / TC_S) & 1u, a.wait_limit)) {
                     s_fail = 1;
                     ok = false;
                     break;
                 }
+                if (a.no_mma) continue;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int kk = it / nch, c0 = (it - kk * nch) * TC_KC;
                 const int nk = min(TC_KC, a.Cin - c0) / 16;
@@ -322,13 +325,13 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(smem_u32(&empty[s])) : "memory");
             }
-            if (ok)
+            if (ok && !a.no_mma)
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(smem_u32(&done)) : "memory");
         }
         __syncwarp();
     }
-    if (tid == 0 && !s_fail && !tc_wait(smem_u32(&done), 0u)) s_fail = 1;
+    if (tid == 0 && !s_fail && !tc_wait(smem_u32(&done), 0u, a.wait_limit)) s_fail = 1;
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {
@@ -720,6 +723,7 @@ struct ncs_unet {
     long long step = 0;
     int* d_err = nullptr;           // tensor-core wait gave up (checked after each call)
     int tc = 1;                     // convolutions on tcgen05 where the channel counts allow
+    int inject = 0;                 // failure-path test armed for the next call
     cudaStream_t st = nullptr;
 };
 
@@ -804,6 +808,8 @@ int launch_conv(ncs_unet* n, ConvArgs a)
             t.Rb = Rb; t.Wb = Wb;
             t.bias = a.bias; t.out = a.out; t.ldo = a.ldo; t.offo = a.offo; t.out_f32 = a.out_f32; t.relu = a.relu;
             t.err = a.err;
+            t.wait_limit = n->inject ? 4096u : TC_WAIT_LIMIT;
+            t.no_mma = n->inject;
             dim3 grid(tiles, a.Cout / BN);
             k_conv3x3_tc<<<grid, 128, TC_S * tc_stage_bytes(BN, std::min(TC_KC, a.Cin)), n->st>>>(tin, tw, t);
             UCK(cudaGetLastError());
@@ -1114,6 +1120,7 @@ int build_unet(ncs_unet* n, uint64_t seed)
 // NCS_ERR_TIMEOUT (and the flag cleared) if a tensor-core wait gave up since the last check.
 int check_err(ncs_unet* n)
 {
+    n->inject = 0;
     int h = 0;
     UCK(cudaMemcpyAsync(&h, n->d_err, sizeof(int), cudaMemcpyDeviceToHost, n->st));
     UCK(cudaStreamSynchronize(n->st));
@@ -1199,6 +1206,13 @@ int ncs_unet_train_step(ncs_unet* n, const float* x, const float* target, float 
     UCK(cudaGetLastError());
     UCKS(refresh_weights(n));
     return check_err(n);
+}
+
+int ncs_unet_inject_wait_timeout(ncs_unet* n)
+{
+    if (!n) return NCS_ERR_BADARG;
+    n->inject = 1;
+    return NCS_OK;
 }
 
 int ncs_unet_set_conv_path(ncs_unet* n, int tensor_cores)
