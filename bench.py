@@ -552,7 +552,16 @@ def run_batch(args, ws, rank, local):
         t_max = reduce_max(ms, ws)
         total = reduce_sum(args.steps * len(plans), ws)
         pix = reduce_sum(args.steps * sum(N * N for N in sides), ws)
+        # algorithmic HBM bytes of one iteration of every slice (FP32 state read + written
+        # once, b read, spectrum round trips: 4 (10 n + 3 m) per slice; BF16 storage halves
+        # the dual streams, which is not credited here)
+        it_bytes = sum(4.0 * (10 * Ns * Ns + 3 * int(round(1.4 * Ns)) * (Ns + 2)) for Ns in sides)
+        gbs = it_bytes / (t_max / args.steps / 1000.0) / 1e9
+        peaks, peak_kind = load_peaks()
         out[prec] = {"slice_iters_per_s": total / (t_max / 1000.0), "pixel_iters_per_s": pix / (t_max / 1000.0),
+                     "hbm": {"algorithmic_bytes_per_batch_iteration": it_bytes, "achieved_gbs": gbs,
+                             "peak_gbs": peaks.get("hbm_gbs", 6800.0), "frac": gbs / peaks.get("hbm_gbs", 6800.0),
+                             "peak_kind": peak_kind},
                      "ms_per_batch_iteration": t_max / args.steps, "clocks": clk.summary(), "lanes": lanes,
                      "gather_parts": [p.info()["gather_parts"] for p in plans[:4]]}
         batch.close()
