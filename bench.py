@@ -42,9 +42,9 @@ TTG_CAP = 2000
 METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
 # DRAM bytes (read + write) per launch of the current kernels, from one ncu capture
 # (profiles/ncu_k_gather_k_fwd_ct512.md); set to None when a kernel changes.
-NCU_TRAFFIC = {"joseph_gather": 4121088.0, "joseph_fwd": 8507392.0}
+NCU_TRAFFIC = {"joseph_gather": 4120832.0, "joseph_fwd": 8508672.0}
 # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
-NCU_WARP_INSTR = {"joseph_gather": 301096704.0, "joseph_fwd": 127679221.0}
+NCU_WARP_INSTR = {"joseph_gather": 301766912.0, "joseph_fwd": 128230021.0}
 
 
 def load_peaks():
