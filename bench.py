@@ -34,7 +34,7 @@ if ROOT not in sys.path:
 
 WORKLOAD = "ct512"
 # NCS / PDHG parameters for this workload, tuned on the {1,3} x 10^p grid (Sec. 5)
-NCS_PARAMS = dict(alpha=0.01, beta=0.01, gamma=0.0)
+NCS_PARAMS = dict(alpha=0.01, beta=0.01, gamma=0.0, h_probes=32)   # M's projector part by eq. (H-fan)
 PDHG_PARAMS = dict(alpha=0.001, beta=0.001)
 CHECK_EVERY = 10
 TTG_TOL = 1e-4
@@ -298,7 +298,7 @@ def run_ours(args, ws, rank, local):
     N, na, nd = W["N"], W["n_angles"], W["n_det"]
     n, m = N * N, na * nd
     plan = ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], gamma=NCS_PARAMS["gamma"],
-                    tv=W["tv"], check_every=CHECK_EVERY)
+                    tv=W["tv"], check_every=CHECK_EVERY, h_probes=NCS_PARAMS["h_probes"])
     W, pr = make_inputs(args.seed + rank, gpu_projector(plan, dev))
     b = torch.from_numpy(pr["b"].ravel()).to(dev)
     x = torch.zeros(n, device=dev)

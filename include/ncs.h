@@ -93,6 +93,11 @@ typedef struct {
                               creation and keep the fastest (default 0) */
     int warm_dual;         /* 1: the solves start the data dual at u^0 = K x^0 - b, consistent with the
                               given x^0 (L2 data term, FP32 storage); 0: zero duals (default) */
+    int h_probes;          /* 0 (default): the projector part of M from eq. (circ_R), C_R / |nu|;
+                              P > 0: from eq. (H-fan) in least-squares form over P probe images v
+                              (SplitMix64 seeds power_seed + 1 .. power_seed + P, uniform in
+                              [-1, 1)): sum_v Re((F K^T K v) conj(F v)) / sum_v |F v|^2, clamped at
+                              0; the DC entry stays h_dc either way */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */
@@ -109,7 +114,7 @@ typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and so
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
  * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
- * check_every 10, NULL stream, autotune 0, warm_dual 0. */
+ * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0. */
 void ncs_options_default(ncs_options* opt);
 
 /* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).

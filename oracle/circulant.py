@@ -94,6 +94,23 @@ def circulant_solve(r: np.ndarray, h: np.ndarray) -> np.ndarray:
     return np.real(np.fft.ifft2(np.fft.fft2(r) * hinv))
 
 
+def probe_ls(op, N: int, vs) -> np.ndarray:
+    """Eq. (H-fan) in least-squares form: sum over probe images v of
+    Re((F op(v)) conj(F v)) divided by sum of |F v|^2 (0 where every F v vanishes).
+    For one probe it equals the real part of probe_ratio; for a circulant op it is the
+    op's eigenvalues for any probes."""
+    num = np.zeros((N, N))
+    den = np.zeros((N, N))
+    for v in vs:
+        Fv = np.fft.fft2(v)
+        Fw = np.fft.fft2(op(v))
+        num += np.real(Fw * np.conj(Fv))
+        den += np.abs(Fv) ** 2
+    out = np.zeros((N, N))
+    np.divide(num, den, out=out, where=den > 0)
+    return out
+
+
 def probe_ratio(op, N: int, vs) -> np.ndarray:
     """Eq. (H-fan): the average over probe images v of (F op(v))_i / (F v)_i,
     an estimate of the circulant eigenvalues of a near-circulant op."""

@@ -517,6 +517,53 @@ void free_plan(ncs_plan* p)
 
 int autotune_plan(ncs_plan* p);
 
+// Eq. (H-fan) on the GPU, least-squares form: h = sum_v Re((F K^T K v) conj(F v)) /
+// sum_v |F v|^2 over P probe images v, into *h in the [k][p] half-spectrum layout of the
+// solve's tables (0 where every F v vanishes).
+int probe_h(ncs_plan* p, int P, std::vector<double>* h)
+{
+    const int N = p->N, H = N / 2;
+    const size_t n = NN(p), half = (size_t)(H + 1) * N;
+    float* v = p->d_tmp;
+    float* w = p->d_r;
+    float* y = nullptr;
+    float2* sv = nullptr;
+    double *num = nullptr, *den = nullptr;
+    int rc = dalloc(&y, MM(p));
+    if (rc == NCS_OK) rc = dalloc(&sv, half);
+    if (rc == NCS_OK) rc = dalloc(&num, half);
+    if (rc == NCS_OK) rc = dalloc(&den, half);
+    if (rc == NCS_OK && (cudaMemsetAsync(num, 0, half * sizeof(double), p->st) != cudaSuccess ||
+                         cudaMemsetAsync(den, 0, half * sizeof(double), p->st) != cudaSuccess))
+        rc = NCS_ERR_CUDA;
+    for (int q = 0; q < P && rc == NCS_OK; ++q) {
+        if (launch_splitmix(v, n, p->opt.power_seed + 1 + (uint64_t)q, p->st) != cudaSuccess) rc = NCS_ERR_CUDA;
+        if (rc == NCS_OK) rc = enq_pairs(p, v, p->d_tmp2, p->d_tmpT2);
+        if (rc == NCS_OK) rc = enq_K(p, p->d_tmp2, p->d_tmpT2, y);
+        if (rc == NCS_OK)
+            rc = enq_gather(p, GATHER_R, y, nullptr, 0.f, nullptr, 0.f, w, nullptr, nullptr, 0.f, p->na, false);
+        if (rc == NCS_OK && (launch_rows_fwd(w, p->d_spec, p->d_tw, p->rp, N, p->st) != cudaSuccess ||
+                             launch_rows_fwd(v, sv, p->d_tw, p->rp, N, p->st) != cudaSuccess ||
+                             launch_cols_ratio(p->d_spec, sv, num, den, p->d_tw, p->rp, N, p->st) != cudaSuccess))
+            rc = NCS_ERR_CUDA;
+    }
+    if (rc == NCS_OK) {
+        std::vector<double> d(half);
+        h->assign(half, 0.0);
+        if (cudaMemcpyAsync(h->data(), num, half * sizeof(double), cudaMemcpyDeviceToHost, p->st) != cudaSuccess ||
+            cudaMemcpyAsync(d.data(), den, half * sizeof(double), cudaMemcpyDeviceToHost, p->st) != cudaSuccess ||
+            cudaStreamSynchronize(p->st) != cudaSuccess)
+            rc = NCS_ERR_CUDA;
+        for (size_t i = 0; i < half; ++i) (*h)[i] = d[i] > 0.0 ? (*h)[i] / d[i] : 0.0;
+    }
+    cudaGetLastError();
+    cudaFree(y);
+    cudaFree(sv);
+    cudaFree(num);
+    cudaFree(den);
+    return rc;
+}
+
 int build_plan(ncs_plan* p, const ncs_geometry* geom)
 {
     const int N = p->N, na = p->na, nd = p->nd;
@@ -640,7 +687,10 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
         p->h_dc = p->h_pin[0] / (double)n;
     }
     if (std::isnan(p->c_r)) p->c_r = (double)na * N / M_PI;
-    // eigenvalues of M = gamma I + alpha C, C ~ A^T A (eqs. (circ_R), (circ_D))
+    // eq. (H-fan): the projector part estimated from probe images, in the [k][p] half layout
+    std::vector<double> hprobe;
+    if (p->opt.h_probes > 0) CKS(probe_h(p, p->opt.h_probes, &hprobe));
+    // eigenvalues of M = gamma I + alpha C, C ~ A^T A (eqs. (circ_R) or (H-fan), (circ_D))
     p->mu.assign(n, 0.0);
     const double b2a = p->beta * p->beta / p->alpha;
     const double kap = p->nonneg ? p->alpha * p->kappa * p->kappa : 0.0;
@@ -650,7 +700,13 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
         for (int q = 0; q < N; ++q) {
             const double kq = std::min(q, N - q);
             const double sq = std::sin(M_PI * q / N);
-            const double hr = (pp == 0 && q == 0) ? p->h_dc : p->c_r / std::sqrt(jp * jp + kq * kq);
+            double hr;
+            if (pp == 0 && q == 0) hr = p->h_dc;
+            else if (!hprobe.empty()) {
+                // a real operator's estimate is even: h(p, q) = h(-p, -q) for the half above N/2
+                const int qq = q <= N / 2 ? q : N - q, pr = q <= N / 2 ? pp : (N - pp) % N;
+                hr = std::max(0.0, hprobe[(size_t)qq * N + pr]);
+            } else hr = p->c_r / std::sqrt(jp * jp + kq * kq);
             const double hd = 4.0 * (sp * sp + sq * sq);
             p->mu[(size_t)pp * N + q] = p->gamma + p->alpha * hr + b2a * hd + kap;
         }
@@ -904,6 +960,7 @@ void ncs_options_default(ncs_options* o)
     o->cuda_stream = nullptr;
     o->autotune = 0;
     o->warm_dual = 0;
+    o->h_probes = 0;
 }
 
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,

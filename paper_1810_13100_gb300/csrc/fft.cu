@@ -184,6 +184,36 @@ __global__ void k_cols_solve(float2* __restrict__ S, const float* __restrict__ i
     for (int p = tid; p < N; p += nthr) col[p] = conj2(Z[p]);
 }
 
+// Eq. (H-fan), least-squares form: one probe's terms of the circulant-eigenvalue
+// estimate h_p = sum_v Re(W_p conj(V_p)) / sum_v |V_p|^2.  Column k of the
+// row-transformed probe v (Sv) and of w = E^T E v (Sw) are transformed along the
+// column and num[k][p] += Re(W_p conj(V_p)), den[k][p] += |V_p|^2.  The row pass is
+// k_rows_fwd; Sv is overwritten.
+__global__ void k_cols_ratio(const float2* __restrict__ Sw, float2* __restrict__ Sv, double* __restrict__ num,
+                             double* __restrict__ den, const float2* __restrict__ tw, RadixPlan rp, int N)
+{
+    extern __shared__ float2 sm[];
+    float2* a = sm;
+    float2* b = sm + N;
+    const int k = blockIdx.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    float2* colv = Sv + (size_t)k * N;
+    for (int q = tid; q < N; q += nthr) a[q] = colv[q];
+    __syncthreads();
+    float2* V = fft_smem(a, b, N, rp, tw, tid, nthr);
+    for (int q = tid; q < N; q += nthr) colv[q] = V[q];
+    __syncthreads();
+    const float2* colw = Sw + (size_t)k * N;
+    for (int q = tid; q < N; q += nthr) a[q] = colw[q];
+    __syncthreads();
+    float2* W = fft_smem(a, b, N, rp, tw, tid, nthr);
+    for (int q = tid; q < N; q += nthr) {
+        const float2 v = colv[q], w = W[q];
+        num[(size_t)k * N + q] += (double)w.x * v.x + (double)w.y * v.y;
+        den[(size_t)k * N + q] += (double)v.x * v.x + (double)v.y * v.y;
+    }
+}
+
 __global__ void k_rows_inv(const float2* __restrict__ S, const float2* __restrict__ tw, RadixPlan rp, int N,
                            int mode, float* __restrict__ x, float* __restrict__ xbar, float* __restrict__ out)
 {
@@ -249,6 +279,13 @@ cudaError_t launch_cols_solve(float2* S, const float* invmu, const float2* tw, c
                               cudaStream_t st)
 {
     k_cols_solve<<<N / 2 + 1, fft_threads(N), 2 * N * sizeof(float2), st>>>(S, invmu, tw, rp, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_ratio(const float2* Sw, float2* Sv, double* num, double* den, const float2* tw,
+                              const RadixPlan& rp, int N, cudaStream_t st)
+{
+    k_cols_ratio<<<N / 2 + 1, fft_threads(N), 2 * N * sizeof(float2), st>>>(Sw, Sv, num, den, tw, rp, N);
     return cudaGetLastError();
 }
 

@@ -191,6 +191,8 @@ int td_num_blocks(int N);
 
 cudaError_t launch_rows_fwd(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N,
                             cudaStream_t st);
+cudaError_t launch_cols_ratio(const float2* Sw, float2* Sv, double* num, double* den, const float2* tw,
+                              const RadixPlan& rp, int N, cudaStream_t st);   // eq. (H-fan) probe terms
 cudaError_t launch_cols_solve(float2* S, const float* invmu, const float2* tw, const RadixPlan& rp, int N,
                               cudaStream_t st);
 // mode 0: x <- x - delta, xbar <- x_old - 2 delta ; mode 1: out <- delta

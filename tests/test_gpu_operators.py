@@ -169,3 +169,22 @@ def test_objective_parity(kind):
     f = plan.objective(torch.from_numpy(x.ravel().astype(np.float32)).cuda(),
                        torch.from_numpy(pr["b"].ravel()).cuda(), bg)
     assert f == pytest.approx(osv.objective(P, x), rel=1e-6)
+
+
+@pytest.mark.parametrize("N,na,nd", [(64, 90, 92), (48, 60, 70)])
+def test_probe_estimated_circulant_matches_oracle(N, na, nd):
+    """Eq. (H-fan), least-squares form: M's projector part from SplitMix64 probe images on
+    the GPU against the oracle's probe_ls of K^T K over the same (float32) images; the A3
+    rescale is off (a3_margin < 0) so the raw eigenvalues are compared."""
+    P, lam, alpha, beta = 4, 0.01, 0.5, 1.5
+    plan = plan_for(N, na, nd, lam=lam, alpha=alpha, beta=beta, h_probes=P, a3_margin=-1.0, power_max_iter=2)
+    mu_gpu = plan.mu()
+    plan.close()
+    g = oop.Geometry(N, na, nd)
+    vs = [f32(osv.splitmix64_uniform(1 + q, N * N)).reshape(N, N) for q in range(P)]
+    h = np.maximum(oci.probe_ls(lambda v: oop.KT(oop.K(v, g), g), N, vs), 0.0)
+    h[0, 0] = oci.h_dc_default(g)
+    mu_ref = alpha * h + (beta * beta / alpha) * oci.H_D(N)
+    err = rel_l2(mu_gpu, mu_ref)
+    print("H-fan mu rel L2 %.2e" % err)
+    assert err <= 1e-4

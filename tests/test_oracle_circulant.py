@@ -100,3 +100,18 @@ def test_h_dc_default_is_rayleigh_quotient():
     one = np.ones((16, 16))
     KtK1 = op.KT(op.K(one, g), g)
     assert ci.h_dc_default(g) == pytest.approx(np.sum(one * KtK1) / 256.0, rel=1e-12)
+
+
+def test_probe_ls_recovers_circulant_eigenvalues_and_matches_one_probe_ratio():
+    """Eq. (H-fan), least-squares form: for a circulant operator it returns the exact
+    eigenvalues whatever the probes; with a single probe it is the real part of the
+    paper's ratio."""
+    N = 12
+    rng = np.random.default_rng(4)
+    h = rng.uniform(0.5, 3.0, (N, N))
+    h = 0.5 * (h + np.roll(np.flip(h), 1, axis=(0, 1)))      # h(-j, -k) = h(j, k): a real operator
+    op = lambda v: ci.circulant_apply(v, h)
+    vs = [rng.standard_normal((N, N)) for _ in range(3)]
+    assert np.max(np.abs(ci.probe_ls(op, N, vs) - h)) <= 1e-12 * h.max()
+    one = ci.probe_ls(op, N, vs[:1])
+    assert np.max(np.abs(one - np.real(ci.probe_ratio(op, N, vs[:1])))) <= 1e-12 * h.max()
