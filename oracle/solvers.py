@@ -246,6 +246,67 @@ def admm_textbook(P: Problem, n_iter: int, Ad: np.ndarray, x0=None, lam0=None, r
     return xs
 
 
+def admm_pcg(P: Problem, n_iter: int, n_cg: int, Minv, x0=None, record=None):
+    """ADMM in the textbook form of admm_textbook (Appendix, "Derivation from ADMM"),
+    CT only, with the x-update (A^T A) x = A^T (z+ + b + lambda) solved approximately
+    by n_cg steps of conjugate gradients preconditioned by the circulant M (Sec. 1.3,
+    the PCG inner loop of the ADMM comparator) and started from the current x.
+    Returns the list of x iterates x^1..x^n."""
+    assert P.kind == "ct"
+    N = P.g.N
+    f = P.beta / P.alpha
+    a = P.alpha
+    x = np.zeros((N, N)) if x0 is None else np.array(x0, dtype=np.float64).reshape(N, N)
+    lu = np.zeros_like(P.b)
+    lh = np.zeros((N, N - 1))
+    lv = np.zeros((N - 1, N))
+
+    def AtA(v):
+        dh, dv = D(v)
+        return KT(K(v, P.g), P.g) + f * f * DT(dh, dv)
+
+    Kx = K(x, P.g)
+    dh, dv = D(x)
+    xs = []
+    for k in range(n_iter):
+        # z+ = prox_{(1/alpha) g}(A x - b - lambda)
+        zu = (Kx - P.b - lu) / (1.0 + 1.0 / a)
+        t = P.lam / P.beta
+        wh, wv = f * dh - lh, f * dv - lv
+        if P.tv == "aniso":
+            zh, zv = prox.soft(wh, t), prox.soft(wv, t)
+        else:
+            ph, pv = prox.soft_iso(_pad_h(wh), _pad_v(wv), t)
+            zh, zv = ph[:, :-1], pv[:-1, :]
+        # x+ ~ (A^T A)^{-1} A^T (z+ + b + lambda) by PCG from x
+        rhs = KT(zu + P.b + lu, P.g) + f * DT(zh + lh, zv + lv)
+        r = rhs - AtA(x)
+        sv = Minv(r)
+        pv_ = sv.copy()
+        rs = float(np.sum(r * sv))
+        for _ in range(n_cg):
+            if rs <= 0.0:
+                break
+            q = AtA(pv_)
+            step = rs / float(np.sum(pv_ * q))
+            x = x + step * pv_
+            r = r - step * q
+            sv = Minv(r)
+            rs_new = float(np.sum(r * sv))
+            pv_ = sv + (rs_new / rs) * pv_
+            rs = rs_new
+        # lambda+ = lambda + z+ - A x+ + b
+        Kx = K(x, P.g)
+        dh, dv = D(x)
+        lu = lu + zu - Kx + P.b
+        lh = lh + zh - f * dh
+        lv = lv + zv - f * dv
+        xs.append(x.copy())
+        if record is not None:
+            record(k, x)
+    return xs
+
+
 def dense_Minv(Md: np.ndarray):
     """M^+ for a dense symmetric M (pseudo-inverse through its eigendecomposition)."""
     Mp = np.linalg.pinv(Md, hermitian=True)

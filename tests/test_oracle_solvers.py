@@ -160,3 +160,28 @@ def test_pet_kkt_at_ncs_limit():
     rng = np.random.default_rng(0)
     for _ in range(5):
         assert so.objective(P, np.maximum(st.x + 1e-3 * rng.standard_normal(st.x.shape), 0)) >= f - 1e-9 * abs(f)
+
+
+@pytest.mark.parametrize("tv", ["aniso", "iso"])
+def test_admm_pcg_with_long_inner_loop_is_textbook_admm(ct16, tv):
+    """The ADMM comparator with its PCG inner loop (circulant preconditioner) run to
+    convergence inside every outer step reproduces the dense-pseudo-inverse ADMM of the
+    Appendix; with a short inner loop it still descends to the same minimiser."""
+    g, b = ct16
+    P = so.Problem(g, b, lam=0.5, alpha=0.7, beta=1.3, tv=tv)
+    Ad = so.dense_A(P)
+    ref = so.admm_textbook(P, 8, Ad)
+    mus, _ = so.a3_scaled_mu(P, ci.mu_table(g, P.alpha, P.beta, 0.0))
+    xs = so.admm_pcg(P, 8, 120, so.circulant_Minv(mus))
+    for k in range(8):
+        assert np.linalg.norm(xs[k] - ref[k]) <= 1e-9 * np.linalg.norm(ref[k])
+
+
+def test_admm_pcg_with_short_inner_loop_reaches_the_ncs_minimiser(ct16, ct16_solution):
+    g, b = ct16
+    P, mus, st = ct16_solution
+    xs = so.admm_pcg(P, 1000, 3, so.circulant_Minv(mus))
+    f_admm = so.objective(P, xs[-1])
+    f_ncs = so.objective(P, st.x)
+    assert 0.0 <= (f_admm - f_ncs) / f_ncs <= 1e-6
+    assert np.linalg.norm(xs[-1] - st.x) <= 1e-5 * np.linalg.norm(st.x)
