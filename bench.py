@@ -36,6 +36,9 @@ WORKLOAD = "ct512"
 # NCS / PDHG parameters for this workload, tuned on the {1,3} x 10^p grid (Sec. 5)
 NCS_PARAMS = dict(alpha=0.01, beta=0.01, gamma=0.0, h_probes=32)   # M's projector part by eq. (H-fan)
 PDHG_PARAMS = dict(alpha=0.001, beta=0.001)
+# ADMM comparator (Sec. 1.3): penalty 1/alpha, n_cg preconditioned CG steps per outer step
+ADMM_PARAMS = dict(alpha=0.1, beta=0.1, n_cg=10)
+ADMM_CAP = 1000                     # outer steps
 CHECK_EVERY = 10
 TTG_TOL = 1e-4
 TTG_CAP = 2000
@@ -288,6 +291,26 @@ def cufft_reference(N, dev, iters=200):
                     "L2-warm, CUDA events; ours_ms = the three hand-written FFT kernels per iteration" % (N, N)}
 
 
+def admm_ttg(ncs, N, na, nd, W, b, f_star, dev, grid=False):
+    """Time to the gap of the ADMM comparator (PCG inner loop preconditioned by the same
+    eq. (H-fan) circulant as NCS) from zero; with grid, over alpha x n_cg as well."""
+    import torch
+    cfgs = [dict(ADMM_PARAMS)]
+    if grid:
+        cfgs += [dict(alpha=a, beta=a, n_cg=c) for a in (0.01, 0.03, 0.1, 0.3, 1.0) for c in (3, 10)
+                 if (a, c) != (ADMM_PARAMS["alpha"], ADMM_PARAMS["n_cg"])]
+    out = []
+    for c in cfgs:
+        aplan = ncs.Plan(N, na, nd, W["lam"], c["alpha"], beta=c["beta"], tv=W["tv"], check_every=CHECK_EVERY,
+                         h_probes=NCS_PARAMS["h_probes"])
+        x = torch.zeros(N * N, device=dev)
+        rep = aplan.admm_solve(b, x, tol=TTG_TOL, max_outer=ADMM_CAP, n_cg=c["n_cg"], f_star=f_star)
+        aplan.close()
+        out.append(dict(c, outer=rep["iters"], time_ms=rep["time_ms"], gap=rep["gap"], status=rep["status"],
+                        operator_passes=rep["iters"] * (c["n_cg"] + 2)))
+    return out if grid else out[0]
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1810_13100_gb300 as ncs
@@ -442,6 +465,7 @@ def run_ours(args, ws, rank, local):
                 xs.zero_()
                 rep = pplan.pdhg_solve(bs, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=f_star)
                 run["pdhg_extended"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+            run["admm"] = admm_ttg(ncs, N, na, nd, W, bs, f_star, dev, args.admm_grid and not runs)
             runs.append(run)
         if pplan is not None:
             pplan.close()
@@ -454,6 +478,11 @@ def run_ours(args, ws, rank, local):
                    "ncs_median_iters": statistics.median(r["iters"] for r in ok) if ok else None,
                    "pdhg_converged": sum(1 for r in runs if r["pdhg"]["status"] == 0),
                    "pdhg_median_gap_at_cap": statistics.median(r["pdhg"]["gap"] for r in runs)}
+            adm = [r["admm"] if isinstance(r["admm"], dict) else r["admm"][0] for r in runs]
+            adm_ok = [a for a in adm if a["status"] == 0]
+            ttg.update({"admm": ADMM_PARAMS, "admm_converged": len(adm_ok),
+                        "admm_median_ms": statistics.median(a["time_ms"] for a in adm_ok) if adm_ok else None,
+                        "admm_median_outer": statistics.median(a["outer"] for a in adm_ok) if adm_ok else None})
 
     # ---- cuFFT as a timing reference for the hand-written FFT solve (A2, A3)
     fft_ref = None
@@ -726,6 +755,8 @@ def main():
     ap.add_argument("--ttg-extended", type=int, default=8000)
     ap.add_argument("--pdhg-extended", type=int, default=20000,
                     help="PDHG iteration cap on the first seed when it misses the gap within the cap")
+    ap.add_argument("--admm-grid", action="store_true",
+                    help="time the ADMM comparator over a grid of alpha and n_cg on the first seed")
     ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256"])
     ap.add_argument("--slices", type=int, default=64)
     args = ap.parse_args()

@@ -164,6 +164,18 @@ int ncs_solve(ncs_plan* plan, const float* b, const float* bg, float* x,
 int pdhg_solve(ncs_plan* plan, const float* b, const float* bg, float* x,
                double tol, int max_iter, double f_star, ncs_report* report);
 
+/* The ADMM comparator (Ramani and Fessler's scheme, Sec. 1.3; the textbook ADMM of the
+ * Appendix with A = [K; (beta/alpha) D]): per outer step z+ = prox_{(1/alpha) g}(A x - b -
+ * lambda), then n_cg steps of conjugate gradients on A^T A x = A^T (z+ + b + lambda)
+ * preconditioned by the plan's circulant M and started from the current x, then
+ * lambda+ = lambda + z+ - A x+ + b.  L2 data, FP32 storage, no nonnegativity row (else
+ * NCS_ERR_UNSUPPORTED).  x (device, N*N) holds x^0 on entry and the result on exit; tol,
+ * f_star and the check every check_every outer steps as in ncs_solve; max_outer bounds the
+ * outer steps.  report->iters counts outer steps and report->rho holds n_cg.  Synchronises
+ * (each conjugate-gradient step reads two dot products on the host). */
+int admm_solve(ncs_plan* plan, const float* b, float* x, double tol, int max_outer, int n_cg, double f_star,
+               ncs_report* report);
+
 /* Host-side results of the setup power iterations: lambda_max(A^T A) (computed
  * now if not yet) and rho = lambda_max(M^{-1} alpha A^T A) before the rescale.
  * Synchronises. */

@@ -69,6 +69,7 @@ SIGNATURES = [
     ("pdhg_step", _I, [_P, _P, _P, _P, _P, _P, _P, _I]),
     ("ncs_solve", _I, [_P, _P, _P, _P, _D, _I, _D, ctypes.POINTER(Report)]),
     ("pdhg_solve", _I, [_P, _P, _P, _P, _D, _I, _D, ctypes.POINTER(Report)]),
+    ("admm_solve", _I, [_P, _P, _P, _D, _I, _I, _D, ctypes.POINTER(Report)]),
     ("ncs_power_bound", _I, [_P, _DP, _DP]),
     ("ncs_apply_K", _I, [_P, _P, _P]),
     ("ncs_apply_KT", _I, [_P, _P, _P]),
@@ -287,6 +288,13 @@ class Plan:
 
     def pdhg_solve(self, b, x, tol=1e-4, max_iter=2000, f_star=None, bg=None):
         return self._solve(self._L.pdhg_solve, "pdhg_solve", b, x, tol, max_iter, f_star, bg)
+
+    def admm_solve(self, b, x, tol=1e-4, max_outer=500, n_cg=10, f_star=None):
+        """The ADMM comparator with a PCG inner loop (admm_solve); x is x^0 in, result out."""
+        rep = Report()
+        self._call("admm_solve", self._L.admm_solve, self._h, _ptr(b, "b", self.m), _ptr(x, "x", self.n), float(tol),
+                   int(max_outer), int(n_cg), float("nan") if f_star is None else float(f_star), ctypes.byref(rep))
+        return rep.as_dict()
 
     def power_bound(self):
         lm, rho = ctypes.c_double(), ctypes.c_double()

@@ -57,6 +57,7 @@ struct ncs_plan {
     float2* d_spec = nullptr;
     double *d_part0 = nullptr, *d_part1 = nullptr, *d_scal = nullptr, *h_pin = nullptr;
     float* d_kx = nullptr;        // running K x of a solve (L2 data)
+    float* d_adm = nullptr;       // ADMM comparator workspace (allocated on first use)
     float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
     int gparts = 1;                  // angle slices of the gather
     float* d_gpart = nullptr;        // gather scratch: gparts * N * N partial sums
@@ -509,7 +510,7 @@ void free_plan(ncs_plan* p)
     cudaFree(p->d_xbar); cudaFree(p->d_r); cudaFree(p->d_tmp);
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
-    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s); cudaFree(p->d_kx);
+    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s); cudaFree(p->d_kx); cudaFree(p->d_adm);
     cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter); cudaFree(p->d_q);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
@@ -932,6 +933,127 @@ int solve_common(ncs_plan* p, int kind, const float* b, const float* bg, float* 
     return status;
 }
 
+// ADMM comparator (Appendix, "Derivation from ADMM"; Ramani and Fessler's scheme, Sec. 1.3)
+// for L2 data: z+ = prox_{(1/alpha) g}(A x - b - lambda), x+ from n_cg steps of conjugate
+// gradients on A^T A x = A^T (z+ + b + lambda) preconditioned by the plan's circulant M and
+// started from x, lambda+ = lambda + z+ - A x+ + b.  One outer step costs n_cg + 2 passes
+// of A^T A-like work; the objective is checked every check_every outer steps.
+int admm_common(ncs_plan* p, const float* b, float* x, double tol, int max_outer, int n_cg, double f_star,
+                ncs_report* rep)
+{
+    if (!b || !x || max_outer < 1 || n_cg < 1 || !(tol >= 0.0)) return NCS_ERR_BADARG;
+    if (p->kl || p->bf || p->bf_img || p->nonneg) return NCS_ERR_UNSUPPORTED;
+    CK(cudaSetDevice(p->dev));
+    const size_t n = NN(p), m = MM(p), nv = 2 * n;
+    // workspace: lu zu yu kx yk (m each) | lv zv yv fdx vb (2n each) | rhs r s q w pd sb (n each)
+    const size_t words = 5 * m + 5 * nv + 7 * n;
+    if (!p->d_adm) CKS(dalloc(&p->d_adm, words));
+    float* lu = p->d_adm;
+    float* zu = lu + m;
+    float* yu = zu + m;
+    float* kx = yu + m;
+    float* yk = kx + m;
+    float* lv = yk + m;
+    float* zv = lv + nv;
+    float* yv = zv + nv;
+    float* fdx = yv + nv;
+    float* vb = fdx + nv;
+    float* rhs = vb + nv;
+    float* r = rhs + n;
+    float* sv = r + n;
+    float* q = sv + n;
+    float* w = q + n;
+    float* pd = w + n;
+    float* sb = pd + n;
+    const float f = (float)(p->beta / p->alpha);
+    const float inv1pia = (float)(1.0 / (1.0 + 1.0 / p->alpha));
+    const float thr = (float)(p->lam / p->beta);
+    auto apply_A = [&](const float* xin) -> int {
+        // fdx = f D x (and the pair images), kx = K x
+        TdArgs a{};
+        a.x = xin;
+        a.x2 = p->d_tmp2;
+        a.xT2 = p->d_tmpT2;
+        a.v = fdx;
+        a.N = p->N;
+        a.beta = f;
+        CK(launch_td(TD_APPLY, a, p->st));
+        return enq_K(p, p->d_tmp2, p->d_tmpT2, kx);
+    };
+    CK(cudaMemsetAsync(lu, 0, m * sizeof(float), p->st));
+    CK(cudaMemsetAsync(lv, 0, nv * sizeof(float), p->st));
+    CKS(apply_A(x));
+    const int T = p->opt.check_every > 0 ? p->opt.check_every : 10;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, p->st));
+    int it = 0, status = NCS_NOT_CONVERGED, rc = NCS_OK;
+    double fval = std::numeric_limits<double>::quiet_NaN(), f_prev = fval, gap = fval;
+    while (it < max_outer && rc == NCS_OK) {
+        // z+ and the x-update's right-hand side A^T (z+ + b + lambda)
+        if (launch_admm_z(kx, b, lu, zu, yu, m, inv1pia, fdx, lv, zv, yv, p->N, thr, p->iso ? 1 : 0, p->st) !=
+            cudaSuccess) { rc = NCS_ERR_CUDA; break; }
+        if ((rc = enq_gather(p, GATHER_R, yu, yv, f, nullptr, 0.f, rhs, nullptr, nullptr, 0.f, p->na)) != NCS_OK) break;
+        // PCG from x
+        if ((rc = enq_AtA(p, x, yk, vb, sb, w)) != NCS_OK) break;
+        if (cudaMemcpyAsync(r, rhs, n * sizeof(float), cudaMemcpyDeviceToDevice, p->st) != cudaSuccess ||
+            launch_axpy(-1.0f, w, r, n, p->st) != cudaSuccess) { rc = NCS_ERR_CUDA; break; }
+        if ((rc = enq_solve(p, r, p->d_invmu, 1, nullptr, nullptr, sv)) != NCS_OK) break;
+        if (cudaMemcpyAsync(pd, sv, n * sizeof(float), cudaMemcpyDeviceToDevice, p->st) != cudaSuccess) {
+            rc = NCS_ERR_CUDA;
+            break;
+        }
+        if ((rc = enq_dot(p, r, sv, n, 0)) != NCS_OK || (rc = read_scalars(p, 1)) != NCS_OK) break;
+        double rs = p->h_pin[0];
+        for (int j = 0; j < n_cg && rs > 0.0 && rc == NCS_OK; ++j) {
+            if ((rc = enq_AtA(p, pd, yk, vb, sb, q)) != NCS_OK) break;
+            if ((rc = enq_dot(p, pd, q, n, 0)) != NCS_OK || (rc = read_scalars(p, 1)) != NCS_OK) break;
+            const double pq = p->h_pin[0];
+            if (!(pq > 0.0)) break;
+            const float step = (float)(rs / pq);
+            if (launch_axpy(step, pd, x, n, p->st) != cudaSuccess || launch_axpy(-step, q, r, n, p->st) != cudaSuccess) {
+                rc = NCS_ERR_CUDA;
+                break;
+            }
+            if ((rc = enq_solve(p, r, p->d_invmu, 1, nullptr, nullptr, sv)) != NCS_OK) break;
+            if ((rc = enq_dot(p, r, sv, n, 0)) != NCS_OK || (rc = read_scalars(p, 1)) != NCS_OK) break;
+            const double rs_new = p->h_pin[0];
+            if (launch_xpby(sv, (float)(rs_new / rs), pd, n, p->st) != cudaSuccess) { rc = NCS_ERR_CUDA; break; }
+            rs = rs_new;
+        }
+        if (rc != NCS_OK) break;
+        // A x+ and lambda+
+        if ((rc = apply_A(x)) != NCS_OK) break;
+        if (launch_admm_lambda(lu, zu, kx, b, m, lv, zv, fdx, nv, p->st) != cudaSuccess) { rc = NCS_ERR_CUDA; break; }
+        ++it;
+        if (it % T == 0 || it == max_outer) {
+            if ((rc = enq_objective(p, x, b, nullptr, 0)) != NCS_OK || (rc = read_scalars(p, 1)) != NCS_OK) break;
+            fval = p->h_pin[0];
+            if (!std::isfinite(fval)) { status = NCS_ERR_DIVERGED; break; }
+            gap = solve_gap(fval, f_prev, f_star);
+            if (std::isfinite(gap) && gap <= tol) { status = NCS_OK; break; }
+            f_prev = fval;
+        }
+    }
+    cudaEventRecord(e1, p->st);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != NCS_OK) return rc;
+    if (rep) {
+        rep->iters = it;
+        rep->status = status;
+        rep->time_ms = ms;
+        rep->f = fval;
+        rep->gap = gap;
+        rep->rho = (double)n_cg;
+    }
+    return status;
+}
+
 }  // namespace
 
 // ======================================================================= C ABI
@@ -1060,6 +1182,13 @@ int pdhg_solve(ncs_plan* p, const float* b, const float* bg, float* x, double to
 {
     CKS(check_plan(p));
     return solve_common(p, 1, b, bg, x, tol, max_iter, f_star, rep);
+}
+
+int admm_solve(ncs_plan* p, const float* b, float* x, double tol, int max_outer, int n_cg, double f_star,
+               ncs_report* rep)
+{
+    CKS(check_plan(p));
+    return admm_common(p, b, x, tol, max_outer, n_cg, f_star, rep);
 }
 
 int ncs_power_bound(ncs_plan* p, double* lambda_max_AtA, double* rho_M)

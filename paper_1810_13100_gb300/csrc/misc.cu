@@ -173,6 +173,63 @@ __global__ void k_scale(float* a, size_t n, float alpha)
         a[k] *= alpha;
 }
 
+// ADMM comparator (Appendix, "Derivation from ADMM", with A = [K; f D], f = beta/alpha):
+// z+ = prox_{(1/alpha) g}(A x - b - lambda) and the right-hand side y = z+ + b + lambda
+// of the x-update.  Data block: z = (K x - b - l) / (1 + 1/alpha); TV block (fdx = f D x in
+// the 2 N^2 layout): z = soft threshold of fdx - l at t = lambda / beta (the per-pixel
+// block soft threshold for isotropic TV).
+__global__ void k_admm_zu(const float* __restrict__ kx, const float* __restrict__ b, const float* __restrict__ lu,
+                          float* __restrict__ zu, float* __restrict__ yu, size_t m, float inv1pia)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (size_t)gridDim.x * blockDim.x) {
+        const float l = lu[i], bb = b[i];
+        const float z = (kx[i] - bb - l) * inv1pia;
+        zu[i] = z;
+        yu[i] = z + bb + l;
+    }
+}
+
+__global__ void k_admm_zv(const float* __restrict__ fdx, const float* __restrict__ lv, float* __restrict__ zv,
+                          float* __restrict__ yv, int N, float t, int iso)
+{
+    const size_t NN = (size_t)N * N;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < NN; i += (size_t)gridDim.x * blockDim.x) {
+        const float lh = lv[i], lvv = lv[NN + i];
+        const float wh = fdx[i] - lh, wv = fdx[NN + i] - lvv;
+        float zh, zvv;
+        if (iso) {
+            const float nrm = sqrtf(fmaf(wh, wh, wv * wv));
+            const float f = nrm > t ? 1.0f - t / nrm : 0.0f;
+            zh = wh * f;
+            zvv = wv * f;
+        } else {
+            zh = copysignf(fmaxf(fabsf(wh) - t, 0.0f), wh);
+            zvv = copysignf(fmaxf(fabsf(wv) - t, 0.0f), wv);
+        }
+        zv[i] = zh;
+        zv[NN + i] = zvv;
+        yv[i] = zh + lh;
+        yv[NN + i] = zvv + lvv;
+    }
+}
+
+// lambda+ = lambda + z+ - A x+ + b, both blocks (A x+ = (kx, fdx) of the new x).
+__global__ void k_admm_lambda(float* __restrict__ lu, const float* __restrict__ zu, const float* __restrict__ kx,
+                              const float* __restrict__ b, size_t m, float* __restrict__ lv,
+                              const float* __restrict__ zv, const float* __restrict__ fdx, size_t nv)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) lu[i] += zu[i] - kx[i] + b[i];
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) lv[i] += zv[i] - fdx[i];
+}
+
+// p = s + c p (conjugate-gradient direction update)
+__global__ void k_xpby(const float* __restrict__ s, float c, float* __restrict__ p, size_t n)
+{
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = fmaf(c, p[i], s[i]);
+}
+
 __global__ void k_axpy(float alpha, const float* __restrict__ x, float* __restrict__ y, size_t n)
 {
     for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
@@ -284,6 +341,28 @@ cudaError_t launch_scale_by_rsqrt(const float* x, float* y, size_t n, const doub
 cudaError_t launch_scale(float* a, size_t n, float alpha, cudaStream_t st)
 {
     k_scale<<<grid_for(n), 256, 0, st>>>(a, n, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_admm_z(const float* kx, const float* b, const float* lu, float* zu, float* yu, size_t m,
+                          float inv1pia, const float* fdx, const float* lv, float* zv, float* yv, int N, float t,
+                          int iso, cudaStream_t st)
+{
+    k_admm_zu<<<grid_for(m), 256, 0, st>>>(kx, b, lu, zu, yu, m, inv1pia);
+    k_admm_zv<<<grid_for((size_t)N * N), 256, 0, st>>>(fdx, lv, zv, yv, N, t, iso);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_admm_lambda(float* lu, const float* zu, const float* kx, const float* b, size_t m, float* lv,
+                               const float* zv, const float* fdx, size_t nv, cudaStream_t st)
+{
+    k_admm_lambda<<<grid_for(m > nv ? m : nv), 256, 0, st>>>(lu, zu, kx, b, m, lv, zv, fdx, nv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xpby(const float* s, float c, float* p, size_t n, cudaStream_t st)
+{
+    k_xpby<<<grid_for(n), 256, 0, st>>>(s, c, p, n);
     return cudaGetLastError();
 }
 

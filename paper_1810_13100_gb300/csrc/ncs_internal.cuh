@@ -216,5 +216,12 @@ cudaError_t launch_ramp(const float* b, float* q, int n_ang, int n_det, float ta
 cudaError_t launch_splitmix(float* x, size_t n, uint64_t seed, cudaStream_t st);
 // y = a*x + y ; y = x
 cudaError_t launch_axpy(float a, const float* x, float* y, size_t n, cudaStream_t st);
+// ADMM comparator: z-update with the x-update's right-hand side, lambda-update, p = s + c p
+cudaError_t launch_admm_z(const float* kx, const float* b, const float* lu, float* zu, float* yu, size_t m,
+                          float inv1pia, const float* fdx, const float* lv, float* zv, float* yv, int N, float t,
+                          int iso, cudaStream_t st);
+cudaError_t launch_admm_lambda(float* lu, const float* zu, const float* kx, const float* b, size_t m, float* lv,
+                               const float* zv, const float* fdx, size_t nv, cudaStream_t st);
+cudaError_t launch_xpby(const float* s, float c, float* p, size_t n, cudaStream_t st);
 
 }  // namespace ncs
