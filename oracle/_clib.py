@@ -43,5 +43,9 @@ def lib() -> ctypes.CDLL:
                 f.restype = None
                 f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ip,
                               ctypes.c_double, ctypes.c_double, dp, dp]
+            for name in ("oracle_joseph_forward_rays", "oracle_joseph_transpose_rays"):
+                f = getattr(L, name)
+                f.restype = None
+                f.argtypes = [ctypes.c_int, ctypes.c_long, dp, dp, dp, ip, dp, dp]
             _lib = L
     return _lib

@@ -1,5 +1,6 @@
 /*
- * FP64 oracle for the parallel-beam Joseph projector K and its transpose K^T.
+ * FP64 oracle for the Joseph projector K and its transpose K^T (parallel beam, and
+ * per ray for the fan beam).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
  * baseline of the benchmark may load this file.  It shares no code with the
@@ -137,6 +138,77 @@ void oracle_joseph_transpose(int N, int n_ang, int n_det,
                 add_pix(x, N, j0, i, (1.0 - w) * val);
                 add_pix(x, N, j0 + 1, i, w * val);
             }
+        }
+    }
+}
+
+/*
+ * Per-ray form of the same projector, for geometries whose rays do not come in
+ * parallel families (the fan beam of the Sec. 4 "fan beam and cone beam geometry"
+ * remark).  Ray r is the line u cos_r[r] + v sin_r[r] = s_r[r], stepped over rows
+ * when row_branch[r] is 1 and over columns otherwise, with exactly the crossing,
+ * interpolation and path-length weight of the functions above.
+ */
+void oracle_joseph_forward_rays(int N, long n_rays, const double* cos_r, const double* sin_r,
+                                const double* s_r, const int* row_branch, const double* x, double* y)
+{
+#pragma omp parallel for schedule(dynamic, 64) if ((long)N * n_rays > OMP_MIN_WORK)
+    for (long r = 0; r < n_rays; ++r) {
+        double c = cos_r[r], s = sin_r[r], st = s_r[r];
+        double acc = 0.0;
+        if (row_branch[r]) {
+            for (int j = 0; j < N; ++j) {
+                double fi = row_cross(N, c, s, st, j);
+                double f0 = floor(fi);
+                int i0 = (int)f0;
+                double w = fi - f0;
+                acc += (1.0 - w) * pix(x, N, j, i0) + w * pix(x, N, j, i0 + 1);
+            }
+            acc /= fabs(c);
+        } else {
+            for (int i = 0; i < N; ++i) {
+                double fj = col_cross(N, c, s, st, i);
+                double f0 = floor(fj);
+                int j0 = (int)f0;
+                double w = fj - f0;
+                acc += (1.0 - w) * pix(x, N, j0, i) + w * pix(x, N, j0 + 1, i);
+            }
+            acc /= fabs(s);
+        }
+        y[r] = acc;
+    }
+}
+
+void oracle_joseph_transpose_rays(int N, long n_rays, const double* cos_r, const double* sin_r,
+                                  const double* s_r, const int* row_branch, const double* y, double* x)
+{
+    memset(x, 0, sizeof(double) * (size_t)N * N);
+#pragma omp parallel for schedule(static) if ((long)N * n_rays > OMP_MIN_WORK)
+    for (int j = 0; j < N; ++j) {
+        for (long r = 0; r < n_rays; ++r) {
+            if (!row_branch[r]) continue;
+            double c = cos_r[r];
+            double val = y[r] / fabs(c);
+            double fi = row_cross(N, c, sin_r[r], s_r[r], j);
+            double f0 = floor(fi);
+            int i0 = (int)f0;
+            double w = fi - f0;
+            add_pix(x, N, j, i0, (1.0 - w) * val);
+            add_pix(x, N, j, i0 + 1, w * val);
+        }
+    }
+#pragma omp parallel for schedule(static) if ((long)N * n_rays > OMP_MIN_WORK)
+    for (int i = 0; i < N; ++i) {
+        for (long r = 0; r < n_rays; ++r) {
+            if (row_branch[r]) continue;
+            double s = sin_r[r];
+            double val = y[r] / fabs(s);
+            double fj = col_cross(N, cos_r[r], s, s_r[r], i);
+            double f0 = floor(fj);
+            int j0 = (int)f0;
+            double w = fj - f0;
+            add_pix(x, N, j0, i, (1.0 - w) * val);
+            add_pix(x, N, j0 + 1, i, w * val);
         }
     }
 }
