@@ -676,6 +676,122 @@ def run_pet(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+FAN_NCS = dict(alpha=0.01, beta=0.01, h_probes=32)   # as the 512x512 parallel-beam workload
+FAN_PDHG = dict(alpha=0.001, beta=0.001)
+
+
+def fan_plan(ncs, W, params, **kw):
+    import synth
+    return ncs.Plan(W["N"], W["n_angles"], W["n_det"], W["lam"], params["alpha"], beta=params["beta"], tv=W["tv"],
+                    src_dist=W["src_dist"], fan_pitch=synth.fan_pitch(W["N"], W["src_dist"], W["n_det"], W["cover"]),
+                    check_every=CHECK_EVERY, **kw)
+
+
+def run_fan(args, ws, rank, local):
+    """The 512x512 fan-beam TV-CT workload (Sec. 4, fan beam geometry; 720 source positions on
+    a full turn at 1024 pixels from the centre, 768 equiangular channels spanning the image's
+    circle, 20 ellipses, 0.5% noise, isotropic TV lambda 0.005): NCS iterations/s with M from
+    eq. (H-fan), L2 flushed before each step, the FP64 objective every 10 steps; per-kernel
+    shares; the roofline of the dominant kernel; NCS and PDHG from zero to the 1e-4 gap against
+    the oracle's f* when it is stored."""
+    import torch
+    import paper_1810_13100_gb300 as ncs
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = synth.WORKLOADS["fan512"]
+    N, na, nd = W["N"], W["n_angles"], W["n_det"]
+    n, m = N * N, na * nd
+    seed = args.seed + rank
+    plan = fan_plan(ncs, W, FAN_NCS, h_probes=FAN_NCS["h_probes"])
+    pr = synth.ct_problem(seed, N, na, nd, W["n_ellipses"], W["noise_frac"], gpu_projector(plan, dev))
+    b = torch.from_numpy(pr["b"].ravel()).to(dev)
+    x = torch.zeros(n, device=dev); u = torch.zeros(m, device=dev); v = torch.zeros(2 * n, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream, cur = plan.stream, torch.cuda.current_stream()
+
+    def one_step(k):
+        plan.step(x, u, v, None, b, n_iter=1)
+        if (k + 1) % CHECK_EVERY == 0:
+            plan.objective(x, b)
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.profile_mask(["joseph_gather"])
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            stream.wait_stream(cur)
+            starts[k].record(stream)
+            one_step(k)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    barrier(ws)
+    kern_timed = plan.profile_read()
+    t_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    t_max = reduce_max(t_ms, ws)
+    value = reduce_sum(args.steps, ws) / (t_max / 1000.0)
+    plan.profile(True)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        stream.wait_stream(cur)
+        one_step(k)
+    torch.cuda.synchronize()
+    kern = plan.profile_read()
+    plan.profile(False)
+    launches = sum(c for _, c in kern.values())
+    peaks, peak_kind = load_peaks()
+    dom_name = max(kern.items(), key=lambda kv: kv[1][0])[0]
+    dom_ms, dom_n = kern_timed[dom_name] if kern_timed.get(dom_name, (0, 0))[1] else kern[dom_name]
+    nnz = plan.nnz()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = 2.0 * nnz / (dom_ms / dom_n / 1000.0) / 1e12
+    roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": None,
+            "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
+            "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
+    tot_ms = sum(t for t, _ in kern.values())
+    kernels = {k: {"ms_per_launch": t / c if c else None, "launches": c, "share": t / tot_ms if tot_ms else None}
+               for k, (t, c) in kern.items()}
+    ttg = None
+    gold = load_golden("fan512", seed)
+    if gold and not args.skip_ttg:
+        fs = gold["f_star"]
+        bd = b.double()
+        ttg = {"tol": TTG_TOL, "f_star": fs, "oracle_iters": gold.get("iterations"),
+               "b_rel_diff": {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
+                              "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}}
+        xs = torch.zeros(n, device=dev)
+        rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=4000, f_star=fs)
+        ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        pplan = fan_plan(ncs, W, FAN_PDHG, h_probes=1, power_max_iter=2)
+        xs.zero_()
+        rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=fs)
+        ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        pplan.close()
+    plan.close()
+    if rank == 0:
+        line = {"metric": "fan-beam TV-CT NCS iterations/s (512x512, 720 views x 768 channels)", "value": value,
+                "unit": "it/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "512x512 fan-beam TV-CT, 720 views on [0, 2pi), 768 equiangular channels, "
+                                       "source at 1024 px, 20 ellipses, 0.5%% noise, iso TV lambda 0.005, seed %d"
+                                       % seed, "ncs": FAN_NCS, "pdhg": FAN_PDHG,
+                           "l2": "flushed before every step (256 MiB write, untimed)"},
+                "roofline": roof, "kernels": kernels, "gpu_launches": launches, "peaks": peak_kind,
+                "time_to_gap": ttg, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def unet_conv_flops(H, W, levels, base):
     """FLOPs of one forward pass of the U-Net's 3x3 convolutions (2 per multiply-add)."""
     c = [base << l for l in range(levels)]
@@ -757,7 +873,7 @@ def main():
                     help="PDHG iteration cap on the first seed when it misses the gap within the cap")
     ap.add_argument("--admm-grid", action="store_true",
                     help="time the ADMM comparator over a grid of alpha and n_cg on the first seed")
-    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256"])
+    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256", "fan512"])
     ap.add_argument("--slices", type=int, default=64)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -773,6 +889,8 @@ def main():
         run_unet(args, ws, rank, local)
     elif args.workload == "pet256":
         run_pet(args, ws, rank, local)
+    elif args.workload == "fan512":
+        run_fan(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

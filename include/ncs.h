@@ -10,7 +10,7 @@
  *
  * for the TV-CT problem of Sec. 4.1, A = [K; (beta/alpha) D], and the TV-PET
  * problem of Sec. 4.2, A = [K; (beta/alpha) D; kappa I] (the nonnegativity row of
- * its remark).  K is a parallel-beam Joseph projector, D the 2-D forward
+ * its remark).  K is a parallel-beam (or fan-beam) Joseph projector, D the 2-D forward
  * difference operator (Sec. 2), and M = gamma I + alpha C is the circulant
  * matrix whose eigenvalues come from eqs. (circ_R) and (circ_D), solved with a
  * real 2-D FFT.  PDHG (eq. (PDHG)) is provided on the same kernels.
@@ -130,6 +130,35 @@ void ncs_options_default(ncs_options* opt);
  * NCS_ERR_NOMEM, NCS_ERR_CUDA. */
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha,
                     const ncs_options* opt, ncs_plan** out);
+
+/* Fan-beam geometry with an equiangular (arc) detector (Sec. 4, "fan beam and cone beam
+ * geometry": X-rays leave a point source and are received over a fan of angles; source and
+ * detector circle the object).  Pixel coordinates as above.  View a puts the source at
+ * S_a = R (-sin beta_a, cos beta_a), R = src_dist.  Channel t receives the ray leaving S_a at
+ * the fan angle gamma_t = (t - (n_det-1)/2) * pitch + offset, counted counter-clockwise from
+ * the central ray (S_a towards the rotation centre); it is the line
+ * u cos(beta_a + gamma_t) + v sin(beta_a + gamma_t) = R sin(gamma_t) of eq. (radon-def).
+ * The sinogram is y[a*n_det + t]. */
+typedef struct {
+    int n_views;           /* source positions, >= 1 */
+    int n_det;             /* channels per view, >= 1 */
+    double src_dist;       /* R in pixel units, >= (N-1)/sqrt(2) + 3 (source outside the image's circle) */
+    double pitch;          /* fan angle between adjacent channels, radians, > 0 */
+    double offset;         /* fan angle of the detector centre, radians */
+    const double* views;   /* host array of n_views source angles beta_a (radians), or NULL for 2 pi a / n_views */
+} ncs_fan_geometry;
+
+/* Build a plan for the fan beam: the same solver, options and entry points as
+ * ncs_plan_create, with K the Joseph projector of the fan's rays (each ray stepped over the
+ * rows or the columns of the image by the parallel beam's rule, ties to rows) and K^T its
+ * exact transpose.  The projector part of M comes from eq. (H-fan) (least-squares form over
+ * ncs_options.h_probes probe images; 0 selects 16), since eq. (circ_R) is for the parallel
+ * beam; c_r is ignored.  ncs_fbp is not available for a fan plan (NCS_ERR_UNSUPPORTED).
+ * Errors as ncs_plan_create, and NCS_ERR_BADARG for a non-positive pitch, non-finite
+ * values or a source inside the image's circumscribed circle (plus a 3-pixel margin).
+ * Synchronises. */
+int ncs_plan_create_fan(const ncs_fan_geometry* geom, int nx, int ny, double lambda, double alpha,
+                        const ncs_options* opt, ncs_plan** out);
 
 /* Release the plan and everything it owns (NULL is a no-op). */
 void ncs_plan_destroy(ncs_plan* plan);

@@ -28,13 +28,39 @@ PARAMS = {
     "ct64": dict(alpha=0.01, beta=0.01, gamma=0.0),
     "ct512": dict(alpha=0.003, beta=0.003, gamma=0.0),
     "pet256": dict(alpha=1.0, beta=1.0, gamma=0.0),
+    "fan64": dict(alpha=0.01, beta=0.01, gamma=0.0),
+    "fan512": dict(alpha=0.01, beta=0.01, gamma=0.0),
 }
+
+# probe images of eq. (H-fan) for the fan-beam runs (SplitMix64 seeds 1..FAN_PROBES)
+FAN_PROBES = 32
+
+
+def geometry(workload: str):
+    """The oracle geometry of a named workload (parallel or fan beam)."""
+    import synth
+    W = synth.WORKLOADS[workload]
+    if W.get("geometry") == "fan":
+        return oop.FanGeometry(W["N"], W["n_angles"], W["n_det"], W["src_dist"],
+                               synth.fan_pitch(W["N"], W["src_dist"], W["n_det"], W["cover"]))
+    return oop.Geometry(W["N"], W["n_angles"], W["n_det"])
+
+
+def fan_mu(P, gamma: float, probes: int = FAN_PROBES):
+    """M's eigenvalues for a fan-beam problem before the (A3) rescale: eq. (H-fan) in
+    least-squares form over SplitMix64 probe images for K^T K (clamped at 0, DC entry
+    ||K 1||^2 / ||1||^2), eq. (circ_D) for D^T D."""
+    g, N = P.g, P.g.N
+    vs = [osv.splitmix64_uniform(1 + q, N * N).reshape(N, N) for q in range(probes)]
+    h = np.maximum(oci.probe_ls(lambda v: oop.KT(oop.K(v, g), g), N, vs), 0.0)
+    h[0, 0] = oci.h_dc_default(g)
+    return gamma + P.alpha * h + (P.beta * P.beta / P.alpha) * oci.H_D(N)
 
 
 def problem(workload: str, seed: int):
     import synth
     W = synth.WORKLOADS[workload]
-    g = oop.Geometry(W["N"], W["n_angles"], W["n_det"])
+    g = geometry(workload)
     p = PARAMS[workload]
     if W["kind"] == "ct":
         pr = synth.ct_problem(seed, W["N"], W["n_angles"], W["n_det"], W["n_ellipses"], W["noise_frac"],
@@ -55,7 +81,10 @@ def golden_path(workload: str, seed: int) -> str:
 
 def run(workload: str, seed: int, iters: int, checkpoint: str | None, every: int = 250):
     P, p = problem(workload, seed)
-    mu0 = oci.mu_table(P.g, P.alpha, P.beta, p["gamma"], kappa=P.kappa)
+    if isinstance(P.g, oop.FanGeometry):
+        mu0 = fan_mu(P, p["gamma"])
+    else:
+        mu0 = oci.mu_table(P.g, P.alpha, P.beta, p["gamma"], kappa=P.kappa)
     mus, rho = osv.a3_scaled_mu(P, mu0)
     Minv = osv.circulant_Minv(mus)
     st, k0, hist = osv.zero_state(P), 0, []

@@ -36,6 +36,12 @@ class Geometry(ctypes.Structure):
                 ("angles", ctypes.POINTER(ctypes.c_double))]
 
 
+class FanGeometry(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int), ("n_det", ctypes.c_int), ("src_dist", ctypes.c_double),
+                ("pitch", ctypes.c_double), ("offset", ctypes.c_double),
+                ("views", ctypes.POINTER(ctypes.c_double))]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("h_dc", ctypes.c_double),
                 ("c_r", ctypes.c_double), ("kappa", ctypes.c_double),
@@ -64,6 +70,8 @@ _IP = ctypes.POINTER(ctypes.c_int)
 SIGNATURES = [
     ("ncs_options_default", None, [ctypes.POINTER(Options)]),
     ("ncs_plan_create", _I, [ctypes.POINTER(Geometry), _I, _I, _D, _D, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    ("ncs_plan_create_fan", _I, [ctypes.POINTER(FanGeometry), _I, _I, _D, _D, ctypes.POINTER(Options),
+                                 ctypes.POINTER(_P)]),
     ("ncs_plan_destroy", None, [_P]),
     ("ncs_step", _I, [_P, _P, _P, _P, _P, _P, _P, _I]),
     ("pdhg_step", _I, [_P, _P, _P, _P, _P, _P, _P, _I]),
@@ -168,24 +176,41 @@ def default_options() -> Options:
 class Plan:
     """An NCS plan: geometry, image side N, TV weight lam, dual step alpha and the
     options of include/ncs.h.  Work runs on `stream` (a torch.cuda.Stream, a raw
-    cudaStream_t int, or None for a side stream ordered with torch's current stream)."""
+    cudaStream_t int, or None for a side stream ordered with torch's current stream).
+
+    Parallel beam by default (ncs_plan_create: n_angles angles, n_det bins, det_spacing,
+    det_offset, angles).  Giving src_dist selects the fan beam (ncs_plan_create_fan):
+    n_angles source positions (angles: their beta_a, default 2 pi a / n_angles), n_det
+    channels at fan pitch fan_pitch (radians) with centre offset fan_offset."""
 
     def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
                  power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
                  det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False, warm_dual=False,
-                 h_probes=0):
+                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0):
         import torch
         L = load_library()
         self._L = L
-        g = Geometry()
-        g.n_angles, g.n_det = int(n_angles), int(n_det)
-        g.det_spacing, g.det_offset = float(det_spacing), float(det_offset)
+        self.fan = src_dist is not None
         self._angles = None
+        arr = None
         if angles is not None:
             arr = (ctypes.c_double * len(angles))(*[float(a) for a in angles])
             self._angles = arr
-            g.angles = ctypes.cast(arr, _DP)
+        if self.fan:
+            if fan_pitch is None:
+                raise ValueError("a fan-beam plan needs fan_pitch")
+            g = FanGeometry()
+            g.n_views, g.n_det = int(n_angles), int(n_det)
+            g.src_dist, g.pitch, g.offset = float(src_dist), float(fan_pitch), float(fan_offset)
+            if arr is not None:
+                g.views = ctypes.cast(arr, _DP)
+        else:
+            g = Geometry()
+            g.n_angles, g.n_det = int(n_angles), int(n_det)
+            g.det_spacing, g.det_offset = float(det_spacing), float(det_offset)
+            if arr is not None:
+                g.angles = ctypes.cast(arr, _DP)
         o = default_options()
         nan = float("nan")
         o.beta = nan if beta is None else float(beta)
@@ -214,8 +239,12 @@ class Plan:
         o.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self.stream = stream
         h = ctypes.c_void_p()
-        _check(L.ncs_plan_create(ctypes.byref(g), int(N), int(N), float(lam), float(alpha), ctypes.byref(o),
-                                 ctypes.byref(h)), "ncs_plan_create")
+        if self.fan:
+            _check(L.ncs_plan_create_fan(ctypes.byref(g), int(N), int(N), float(lam), float(alpha), ctypes.byref(o),
+                                         ctypes.byref(h)), "ncs_plan_create_fan")
+        else:
+            _check(L.ncs_plan_create(ctypes.byref(g), int(N), int(N), float(lam), float(alpha), ctypes.byref(o),
+                                     ctypes.byref(h)), "ncs_plan_create")
         self._h = h
         self.N, self.n_angles, self.n_det = int(N), int(n_angles), int(n_det)
         self.lam, self.alpha = float(lam), float(alpha)

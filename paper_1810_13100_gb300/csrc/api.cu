@@ -46,6 +46,14 @@ struct ncs_plan {
     bool own_stream = false;
     std::vector<AngleParam> h_ap;
     AngleParam* d_ap = nullptr;
+    // fan beam (ncs_plan_create_fan): per-ray coefficients, signed path lengths, views
+    bool fan = false;
+    std::vector<FanRay> h_rays;
+    std::vector<float> h_rayw;
+    FanRay* d_rays = nullptr;
+    float* d_rayw = nullptr;
+    FanView* d_views = nullptr;
+    float inv_pitch = 0.f, t_off = 0.f;
     float2* d_tw = nullptr;
     RadixPlan rp{};
     std::vector<double> mu;          // eigenvalues of M, N x N, [p][q]
@@ -204,6 +212,8 @@ int enq_K(ncs_plan* p, const float2* x2, const float2* xT2, float* y)
     f.img2 = x2;
     f.imgT2 = xT2;
     f.ap = p->d_ap;
+    f.rays = p->d_rays;
+    f.rayw = p->d_rayw;
     f.N = p->N;
     f.n_ang = p->na;
     f.n_det = p->nd;
@@ -218,6 +228,11 @@ int enq_gather(ncs_plan* p, int mode, const void* u, const void* v, float dscale
     GatherArgs g{};
     g.u = u;
     g.ap = p->d_ap;
+    g.rays = p->d_rays;
+    g.rayw = p->d_rayw;
+    g.views = p->d_views;
+    g.inv_pitch = p->inv_pitch;
+    g.t_off = p->t_off;
     g.N = p->N;
     g.n_ang = n_ang;
     g.n_det = p->nd;
@@ -276,6 +291,8 @@ int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg, float* k
     f.img2 = p->d_xb2;
     f.imgT2 = p->d_xbT2;
     f.ap = p->d_ap;
+    f.rays = p->d_rays;
+    f.rayw = p->d_rayw;
     f.N = p->N;
     f.n_ang = p->na;
     f.n_det = p->nd;
@@ -339,6 +356,8 @@ int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, 
     f.img2 = p->d_tmp2;
     f.imgT2 = p->d_tmpT2;
     f.ap = p->d_ap;
+    f.rays = p->d_rays;
+    f.rayw = p->d_rayw;
     f.N = p->N;
     f.n_ang = p->na;
     f.n_det = p->nd;
@@ -506,7 +525,7 @@ void free_plan(ncs_plan* p)
     p->recs.clear();
     p->ev_pool.clear();
     if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
-    cudaFree(p->d_ap); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
+    cudaFree(p->d_ap); cudaFree(p->d_rays); cudaFree(p->d_rayw); cudaFree(p->d_views); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
     cudaFree(p->d_xbar); cudaFree(p->d_r); cudaFree(p->d_tmp);
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
@@ -565,9 +584,8 @@ int probe_h(ncs_plan* p, int P, std::vector<double>* h)
     return rc;
 }
 
-int build_plan(ncs_plan* p, const ncs_geometry* geom)
+int open_stream(ncs_plan* p)
 {
-    const int N = p->N, na = p->na, nd = p->nd;
     CK(cudaGetDevice(&p->dev));
     if (p->opt.cuda_stream) {
         p->st = (cudaStream_t)p->opt.cuda_stream;
@@ -575,6 +593,77 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
         CK(cudaStreamCreateWithFlags(&p->st, cudaStreamNonBlocking));
         p->own_stream = true;
     }
+    return NCS_OK;
+}
+
+// X = X_hi + X_lo with X_hi a multiple of 2^-10 (see AngleParam)
+double split_hi(double X) { return std::nearbyint(X * 1024.0) / 1024.0; }
+
+// Fan-beam rays (Sec. 4, fan beam geometry; equiangular detector): view a puts the source at
+// S_a = R (-sin beta_a, cos beta_a); channel t is the ray leaving S_a at the fan angle
+// gamma_t = (t - (n_det-1)/2) pitch + offset, counted counter-clockwise from the central ray
+// (S_a towards the centre).  It is the line u cos(theta) + v sin(theta) = s with theta =
+// beta_a + gamma_t and s = R sin(gamma_t) (every quantity in FP64, rounded once), stepped over
+// rows when |cos theta| >= |sin theta| with the parallel beam's crossing, interpolation and
+// path length.
+int build_fan_tables(ncs_plan* p, const ncs_fan_geometry* fg)
+{
+    const int N = p->N, na = p->na, nd = p->nd;
+    const double R = fg->src_dist, cN = 0.5 * (N - 1), cd = 0.5 * (nd - 1);
+    const double reach = cN * std::sqrt(2.0) + 2.0;   // farther from the centre a ray touches no pixel
+    const size_t m = (size_t)na * nd;
+    p->h_rays.resize(m);
+    p->h_rayw.resize(m);
+    std::vector<FanView> views(na);
+    for (int a = 0; a < na; ++a) {
+        const double be = fg->views ? fg->views[a] : 2.0 * M_PI * a / na;
+        const double sb = std::sin(be), cb = std::cos(be);
+        views[a] = make_float4((float)(-R * sb), (float)(R * cb), (float)sb, (float)(-cb));
+        for (int t = 0; t < nd; ++t) {
+            const double gam = (t - cd) * fg->pitch + fg->offset;
+            const double th = be + gam;
+            const double c = std::cos(th), sn = std::sin(th), s = R * std::sin(gam);
+            const int row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
+            double B, C, W;
+            if (std::fabs(s) > reach) {
+                B = 0.0;
+                C = -8.0;
+                W = 0.0;
+            } else if (row) {
+                B = sn / c;
+                C = (s - cN * sn) / c + cN;
+                W = 1.0 / std::fabs(c);
+            } else {
+                B = c / sn;
+                C = cN - (s + cN * c) / sn;
+                W = 1.0 / std::fabs(sn);
+            }
+            if (std::fabs(split_hi(B)) * (N - 1) + std::fabs(split_hi(C)) >= 16384.0) return NCS_ERR_UNSUPPORTED;
+            const size_t r = (size_t)a * nd + t;
+            p->h_rays[r] = make_float4((float)split_hi(B), (float)(B - split_hi(B)), (float)split_hi(C),
+                                       (float)(C - split_hi(C)));
+            p->h_rayw[r] = row ? (float)W : -(float)W;
+        }
+    }
+    p->fan = true;
+    p->inv_pitch = (float)(1.0 / fg->pitch);
+    p->t_off = (float)(cd - fg->offset / fg->pitch);
+    CKS(dalloc(&p->d_rays, m));
+    CKS(dalloc(&p->d_rayw, m));
+    CKS(dalloc(&p->d_views, (size_t)na));
+    CK(cudaMemcpyAsync(p->d_rays, p->h_rays.data(), m * sizeof(FanRay), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->d_rayw, p->h_rayw.data(), m * sizeof(float), cudaMemcpyHostToDevice, p->st));
+    CK(cudaMemcpyAsync(p->d_views, views.data(), na * sizeof(FanView), cudaMemcpyHostToDevice, p->st));
+    CK(cudaStreamSynchronize(p->st));
+    return NCS_OK;
+}
+
+int build_common(ncs_plan* p);
+
+int build_plan(ncs_plan* p, const ncs_geometry* geom)
+{
+    const int N = p->N, na = p->na, nd = p->nd;
+    CKS(open_stream(p));
     // per-angle Joseph coefficients in FP64, rounded once
     const double ds = (geom->det_spacing > 0.0) ? geom->det_spacing : 1.0;
     p->ds = ds;
@@ -612,8 +701,7 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
             invA = -sn / ds;
         }
         AngleParam& q = p->h_ap[a];
-        // X = X_hi + X_lo, X_hi a multiple of 2^-10 (see AngleParam)
-        auto hi = [](double X) { return std::nearbyint(X * 1024.0) / 1024.0; };
+        auto hi = [](double X) { return split_hi(X); };
         q.Ahi = (float)hi(A);
         q.Alo = (float)(A - hi(A));
         q.Bhi = (float)hi(B);
@@ -639,6 +727,14 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     }
     CKS(dalloc(&p->d_ap, na));
     CK(cudaMemcpyAsync(p->d_ap, p->h_ap.data(), na * sizeof(AngleParam), cudaMemcpyHostToDevice, p->st));
+    return build_common(p);
+}
+
+// Everything after the projector tables: FFT twiddles, workspace, the DC entry and the
+// eigenvalues of M, the (A3) power iteration and rescale, the optional autotuner.
+int build_common(ncs_plan* p)
+{
+    const int N = p->N, na = p->na, nd = p->nd;
     // twiddles exp(-2 pi i m / N) in FP64, rounded once
     std::vector<float2> tw(N);
     for (int m = 0; m < N; ++m) {
@@ -658,12 +754,13 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     CKS(alloc_pair(p, &p->d_tmp2));
     CKS(alloc_pair(p, &p->d_tmpT2));
     CKS(dalloc(&p->d_spec, (H + 1) * N));
-    p->gparts = gather_parts(N, na);
+    p->gparts = p->fan ? fan_gather_parts(N, na) : gather_parts(N, na);
+    const size_t counters = p->fan ? fan_gather_tiles(N) : gather_tiles(N);
     CKS(dalloc(&p->d_gpart, p->gparts > 1 ? (size_t)p->gparts * n : 1));
-    CKS(dalloc(&p->d_gcount, gather_tiles(N)));
+    CKS(dalloc(&p->d_gcount, counters));
     CKS(dalloc(&p->d_iter, 1));
     CK(cudaMemsetAsync(p->d_iter, 0, sizeof(unsigned long long), p->st));
-    CK(cudaMemsetAsync(p->d_gcount, 0, gather_tiles(N) * sizeof(int), p->st));
+    CK(cudaMemsetAsync(p->d_gcount, 0, counters * sizeof(int), p->st));
     CKS(dalloc(&p->d_part0, kMaxPartials));
     CKS(dalloc(&p->d_part1, (size_t)fwd_num_blocks(nd, na)));
     CKS(dalloc(&p->d_scal, 16));
@@ -756,6 +853,7 @@ int autotune_plan(ncs_plan* p)
 {
     const int base = p->gparts;
     int cand[3] = {std::max(1, base / 2), base, std::min(std::min(64, p->na), base * 2)};
+    if (p->fan) cand[0] = cand[2] = base;      // the fan gather's view slices are not tuned
     const int cmax = std::max(cand[2], base);
     if (cmax > 1) {
         float* bigger = nullptr;
@@ -1058,6 +1156,54 @@ int admm_common(ncs_plan* p, const float* b, float* x, double tol, int max_outer
 
 // ======================================================================= C ABI
 
+extern "C" void ncs_options_default(ncs_options* o);
+
+namespace {
+
+// Validate the sizes and options shared by every plan and fill a new plan's scalars.
+int new_plan(int nx, int ny, int n_angles, int n_det, double lambda, double alpha, const ncs_options* opt,
+             ncs_plan** out)
+{
+    if (nx != ny || nx < 8 || n_angles < 1 || n_det < 1) return NCS_ERR_BADARG;
+    if (!(lambda >= 0.0) || !(alpha > 0.0)) return NCS_ERR_BADARG;
+    ncs_options o;
+    if (opt) o = *opt;
+    else ncs_options_default(&o);
+    if (o.prec != NCS_FP32 && o.prec != NCS_BF16_STORE && o.prec != NCS_BF16_DUALS) return NCS_ERR_BADARG;
+    if (o.nonneg && o.data != NCS_DATA_KL) return NCS_ERR_BADARG;
+    if (o.warm_dual && o.prec != NCS_FP32) return NCS_ERR_BADARG;
+    if (o.power_max_iter < 1 || !(o.power_tol >= 0.0)) return NCS_ERR_BADARG;
+    RadixPlan rp;
+    if (nx % 2 != 0 || nx > 4096 || !factor_radices(nx, &rp)) return NCS_ERR_UNSUPPORTED;
+    ncs_plan* p = new (std::nothrow) ncs_plan();
+    if (!p) return NCS_ERR_NOMEM;
+    p->N = nx;
+    p->na = n_angles;
+    p->nd = n_det;
+    p->lam = lambda;
+    p->alpha = alpha;
+    p->beta = std::isnan(o.beta) ? alpha : o.beta;
+    p->gamma = o.gamma;
+    p->kappa = o.kappa;
+    p->c_r = o.c_r;
+    p->h_dc = o.h_dc;
+    p->kl = o.data == NCS_DATA_KL;
+    p->iso = o.tv == NCS_TV_ISO;
+    p->nonneg = o.nonneg != 0;
+    p->bf = o.prec != NCS_FP32;
+    p->bf_img = o.prec == NCS_BF16_STORE;
+    p->opt = o;
+    p->rp = rp;
+    if (!(p->beta > 0.0) || !(p->gamma >= 0.0) || (p->nonneg && !(p->kappa > 0.0))) {
+        delete p;
+        return NCS_ERR_BADARG;
+    }
+    *out = p;
+    return NCS_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void ncs_options_default(ncs_options* o)
@@ -1090,45 +1236,51 @@ int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, dou
 {
     if (!out) return NCS_ERR_BADARG;
     *out = nullptr;
-    if (!geom || nx != ny || nx < 8 || geom->n_angles < 1 || geom->n_det < 1) return NCS_ERR_BADARG;
-    if (!(lambda >= 0.0) || !(alpha > 0.0)) return NCS_ERR_BADARG;
-    if (geom->det_spacing != 0.0 && !(geom->det_spacing >= 1.0)) return NCS_ERR_UNSUPPORTED;
+    if (!geom) return NCS_ERR_BADARG;
+    ncs_plan* p = nullptr;
+    CKS(new_plan(nx, ny, geom->n_angles, geom->n_det, lambda, alpha, opt, &p));
+    int rc = NCS_OK;
+    if (geom->det_spacing != 0.0 && !(geom->det_spacing >= 1.0)) rc = NCS_ERR_UNSUPPORTED;
+    if (rc == NCS_OK && geom->angles)
+        for (int a = 0; a < geom->n_angles; ++a)
+            if (!std::isfinite(geom->angles[a])) rc = NCS_ERR_BADARG;
+    if (rc != NCS_OK) {
+        delete p;
+        return rc;
+    }
+    rc = build_plan(p, geom);
+    if (rc != NCS_OK) {
+        free_plan(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return NCS_OK;
+}
+
+int ncs_plan_create_fan(const ncs_fan_geometry* geom, int nx, int ny, double lambda, double alpha,
+                        const ncs_options* opt, ncs_plan** out)
+{
+    if (!out) return NCS_ERR_BADARG;
+    *out = nullptr;
+    if (!geom || !(geom->pitch > 0.0) || !std::isfinite(geom->pitch) || !std::isfinite(geom->offset) ||
+        !std::isfinite(geom->src_dist))
+        return NCS_ERR_BADARG;
+    // the source must lie outside the image's circumscribed circle with room to spare (the gather's
+    // channel window assumes every pixel centre is at least 2 pixels from the source)
+    if (nx >= 8 && !(geom->src_dist >= 0.5 * (nx - 1) * std::sqrt(2.0) + 3.0)) return NCS_ERR_BADARG;
+    if (geom->views)
+        for (int a = 0; a < geom->n_views; ++a)
+            if (!std::isfinite(geom->views[a])) return NCS_ERR_BADARG;
     ncs_options o;
     if (opt) o = *opt;
     else ncs_options_default(&o);
-    if (o.prec != NCS_FP32 && o.prec != NCS_BF16_STORE && o.prec != NCS_BF16_DUALS) return NCS_ERR_BADARG;
-    if (o.nonneg && o.data != NCS_DATA_KL) return NCS_ERR_BADARG;
-    if (o.warm_dual && o.prec != NCS_FP32) return NCS_ERR_BADARG;
-    if (o.power_max_iter < 1 || !(o.power_tol >= 0.0)) return NCS_ERR_BADARG;
-    RadixPlan rp;
-    if (nx % 2 != 0 || nx > 4096 || !factor_radices(nx, &rp)) return NCS_ERR_UNSUPPORTED;
-    if (geom->angles)
-        for (int a = 0; a < geom->n_angles; ++a)
-            if (!std::isfinite(geom->angles[a])) return NCS_ERR_BADARG;
-    ncs_plan* p = new (std::nothrow) ncs_plan();
-    if (!p) return NCS_ERR_NOMEM;
-    p->N = nx;
-    p->na = geom->n_angles;
-    p->nd = geom->n_det;
-    p->lam = lambda;
-    p->alpha = alpha;
-    p->beta = std::isnan(o.beta) ? alpha : o.beta;
-    p->gamma = o.gamma;
-    p->kappa = o.kappa;
-    p->c_r = o.c_r;
-    p->h_dc = o.h_dc;
-    p->kl = o.data == NCS_DATA_KL;
-    p->iso = o.tv == NCS_TV_ISO;
-    p->nonneg = o.nonneg != 0;
-    p->bf = o.prec != NCS_FP32;
-    p->bf_img = o.prec == NCS_BF16_STORE;
-    p->opt = o;
-    p->rp = rp;
-    if (!(p->beta > 0.0) || !(p->gamma >= 0.0) || (p->nonneg && !(p->kappa > 0.0))) {
-        delete p;
-        return NCS_ERR_BADARG;
-    }
-    int rc = build_plan(p, geom);
+    if (o.h_probes == 0) o.h_probes = 16;   // the fan beam has no closed-form H_R
+    ncs_plan* p = nullptr;
+    CKS(new_plan(nx, ny, geom->n_views, geom->n_det, lambda, alpha, &o, &p));
+    int rc = open_stream(p);
+    if (rc == NCS_OK) rc = build_fan_tables(p, geom);
+    if (rc == NCS_OK) rc = build_common(p);
     if (rc != NCS_OK) {
         free_plan(p);
         delete p;
@@ -1247,6 +1399,7 @@ int ncs_fbp(ncs_plan* p, const float* b, float* x)
 {
     CKS(check_plan(p));
     if (!b || !x) return NCS_ERR_BADARG;
+    if (p->fan) return NCS_ERR_UNSUPPORTED;
     CK(cudaSetDevice(p->dev));
     if (!p->d_q) CKS(dalloc(&p->d_q, MM(p)));
     CK(launch_ramp(b, p->d_q, p->na, p->nd, (float)p->ds, p->st));
@@ -1554,7 +1707,23 @@ int ncs_plan_nnz(ncs_plan* p, double* nnz)
         // count the nonzero weights of K exactly as the kernels evaluate them
         const int N = p->N;
         double cnt = 0.0;
-        for (int a = 0; a < p->na; ++a) {
+        for (size_t r = 0; r < p->h_rays.size(); ++r) {
+            const FanRay& q = p->h_rays[r];
+            for (int j = 0; j < N; ++j) {
+                const float jf = (float)j;
+                const float H = std::fma(q.x, jf, q.z);
+                const float L = std::fma(q.y, jf, q.w);
+                const float Hi = std::floor(H);
+                const float fr = (H - Hi) + L;
+                const float fl = std::floor(fr);
+                const float w = fr - fl;
+                const int i0 = (int)(Hi + fl);
+                if (p->h_rayw[r] == 0.0f) break;
+                if (i0 >= 0 && i0 < N && 1.0f - w != 0.0f) cnt += 1.0;
+                if (i0 + 1 >= 0 && i0 + 1 < N && w != 0.0f) cnt += 1.0;
+            }
+        }
+        for (int a = 0; a < (p->fan ? 0 : p->na); ++a) {
             const AngleParam& q = p->h_ap[a];
             for (int t = 0; t < p->nd; ++t) {
                 const float tf = (float)t;

@@ -18,6 +18,10 @@
 // block of a tile (an arrival counter) sums the slices in slice order.  The
 // epilogue adds (beta/alpha) D^T v and kappa s (A^T of Sec. 4) and, for PDHG
 // (eq. (PDHG)), applies the primal update.
+//
+// Fan beam (Sec. 4, fan beam geometry): the forward kernel reads per-ray
+// coefficients instead of per-angle ones (same stepping, taps and epilogues), and
+// K^T is a pixel-driven gather (k_gather_fan) that evaluates the same weights.
 #include "ncs_internal.cuh"
 
 namespace ncs {
@@ -49,28 +53,54 @@ __device__ __forceinline__ float kl_conj_prox(float z, float c)
     return d > 0.0f ? 1.0f - 2.0f * c / (d + root) : 1.0f + 0.5f * (d - root);
 }
 
-template <int MODE, bool PBF, bool SBF>
+// FAN: the ray's coefficients come from the per-ray table (fan beam) instead of the
+// block's angle; with no per-bin term the crossing is H = Bhi q + Chi, L = Blo q + Clo.
+template <int MODE, bool PBF, bool SBF, bool FAN>
 __global__ void __launch_bounds__(FWD_TB * FWD_SEG)
 k_fwd(FwdArgs g)
 {
     __shared__ float red[FWD_SEG][FWD_TB];
     __shared__ double dred[FWD_TB];
     const int a = blockIdx.y;
-    const AngleParam p = g.ap[a];
-    const void* im2 = p.row ? g.img2 : g.imgT2;
+    const int t = blockIdx.x * FWD_TB + threadIdx.x;
+    float Ahi, Alo, Bhi, Blo, Chi, Clo, Wr;
+    int row;
+    if (FAN) {
+        const size_t r = (size_t)a * g.n_det + min(t, g.n_det - 1);
+        const float4 q = __ldg(g.rays + r);
+        const float ws = __ldg(g.rayw + r);
+        Ahi = 0.0f;
+        Alo = 0.0f;
+        Bhi = q.x;
+        Blo = q.y;
+        Chi = q.z;
+        Clo = q.w;
+        Wr = fabsf(ws);
+        row = ws < 0.0f ? 0 : 1;
+    } else {
+        const AngleParam p = g.ap[a];
+        Ahi = p.Ahi;
+        Alo = p.Alo;
+        Bhi = p.Bhi;
+        Blo = p.Blo;
+        Chi = p.Chi;
+        Clo = p.Clo;
+        Wr = p.W;
+        row = p.row;
+    }
+    const void* im2 = row ? g.img2 : g.imgT2;
     const int pitch = pair_pitch(g.N);
     const int N = g.N;
-    const int t = blockIdx.x * FWD_TB + threadIdx.x;
     float acc = 0.0f;
     if (t < g.n_det) {
         const float ft = (float)t;
-        const float Hr = fmaf(p.Ahi, ft, p.Chi);    // exact
-        const float B = p.Bhi + p.Blo;
+        const float Hr = FAN ? Chi : fmaf(Ahi, ft, Chi);    // exact
+        const float B = Bhi + Blo;
         // Rows where the ray can touch the image: f in [-1, N).  Found in FP32
         // with a 2-row margin (|B| <= 1, so f stays in (-4, N + 3) on every
         // processed row and the pair image's zero border absorbs the steps
         // outside the image).
-        const float f0 = Hr + fmaf(p.Alo, ft, p.Clo);
+        const float f0 = Hr + (FAN ? Clo : fmaf(Alo, ft, Clo));
         int jlo = 0, jhi = N;
         if (fabsf(B) > 1e-6f) {
             float j1 = (-1.0f - f0) / B, j2 = ((float)N - f0) / B;
@@ -89,7 +119,8 @@ k_fwd(FwdArgs g)
         for (int j = js; j < je; ++j) {
             const float jf = (float)j;
             float k0f;
-            const float w = split_weight(fmaf(p.Bhi, jf, Hr), fmaf(p.Alo, ft, fmaf(p.Blo, jf, p.Clo)), k0f);
+            const float w = FAN ? split_weight(fmaf(Bhi, jf, Chi), fmaf(Blo, jf, Clo), k0f)
+                                : split_weight(fmaf(Bhi, jf, Hr), fmaf(Alo, ft, fmaf(Blo, jf, Clo)), k0f);
             const int i0 = (int)k0f;
             const float2 xv = St<PBF>::ld2(im2, (size_t)j * pitch + PAIR_PAD + i0);
             acc = fmaf(1.0f - w, xv.x, acc);
@@ -103,7 +134,7 @@ k_fwd(FwdArgs g)
         float tot = red[0][threadIdx.x];
 #pragma unroll
         for (int q = 1; q < FWD_SEG; ++q) tot += red[q][threadIdx.x];
-        const float y = p.W * tot;
+        const float y = Wr * tot;
         const size_t idx = (size_t)a * g.n_det + t;
         if (MODE == FWD_PLAIN) {
             St<false>::put(g.y, idx, y);
@@ -232,6 +263,33 @@ __device__ __forceinline__ void gather_angle(const AngleParam& p, const void* ua
     __syncwarp();
 }
 
+// Gather epilogue for pixel (j, i) with K^T u summed in r: adds dscale D^T v and kappa s
+// (A^T of Sec. 4), then stores r (GATHER_R) or applies the PDHG primal update.
+template <int MODE, bool IBF>
+__device__ __forceinline__ void gather_epilogue(const GatherArgs& g, int j, int i, float r)
+{
+    const int N = g.N;
+    const size_t pix = (size_t)j * N + i;
+    if (g.v) {
+        const size_t NN = (size_t)N * N;
+        float dt = 0.0f;
+        if (i < N - 1) dt += St<IBF>::get(g.v, pix);
+        if (i >= 1) dt -= St<IBF>::get(g.v, pix - 1);
+        if (j < N - 1) dt += St<IBF>::get(g.v, NN + pix);
+        if (j >= 1) dt -= St<IBF>::get(g.v, NN + pix - N);
+        r = fmaf(g.dscale, dt, r);
+    }
+    if (g.s) r = fmaf(g.kappa, St<IBF>::get(g.s, pix), r);
+    if (MODE == GATHER_R) {
+        g.r[pix] = r;
+    } else {
+        const float x = g.x[pix];
+        const float x1 = fmaf(-g.inv_gamma, r, x);
+        g.x[pix] = x1;
+        g.xbar[pix] = 2.0f * x1 - x;
+    }
+}
+
 template <int MODE, bool SBF, bool IBF>
 __global__ void __launch_bounds__(GT * GW)
 k_gather(GatherArgs g)
@@ -296,27 +354,89 @@ k_gather(GatherArgs g)
     for (int q = 0; q < GT / GW; ++q) {
         const int j = j0 + q * GW + wid, i = i0 + lane;
         if (j >= N || i >= N) continue;
-        const size_t pix = (size_t)j * N + i;
-        float r = tot[q];
-        if (g.v) {
-            const size_t NN = (size_t)N * N;
-            float dt = 0.0f;
-            if (i < N - 1) dt += St<IBF>::get(g.v, pix);
-            if (i >= 1) dt -= St<IBF>::get(g.v, pix - 1);
-            if (j < N - 1) dt += St<IBF>::get(g.v, NN + pix);
-            if (j >= 1) dt -= St<IBF>::get(g.v, NN + pix - N);
-            r = fmaf(g.dscale, dt, r);
-        }
-        if (g.s) r = fmaf(g.kappa, St<IBF>::get(g.s, pix), r);
-        if (MODE == GATHER_R) {
-            g.r[pix] = r;
-        } else {
-            const float x = g.x[pix];
-            const float x1 = fmaf(-g.inv_gamma, r, x);
-            g.x[pix] = x1;
-            g.xbar[pix] = 2.0f * x1 - x;
+        gather_epilogue<MODE, IBF>(g, j, i, tot[q]);
+    }
+}
+
+constexpr int FGX = 32;    // fan-beam gather block: 32 x 8 pixels, one per thread
+constexpr int FGY = 8;
+
+// K^T for the fan beam (pixel-driven, no atomics).  Rays of one view are not parallel,
+// and adjacent rays can cross a line less than a pixel apart, so the tile walk above does
+// not carry over.  Instead each thread owns one pixel P and, per view a, finds the channels
+// whose ray can reach it: a ray that puts a nonzero Joseph weight on P passes within one
+// pixel of P's centre (|f - k| < 1 along the interpolation axis, and the perpendicular
+// distance is that times |cos| or |sin| <= 1), so its fan angle differs from P's fan
+// angle gamma_P = atan2(cross, dot) of (P - S_a) against the central direction by less
+// than asin(1/|P - S_a|).  That window (widened for FP32 rounding) is scanned, and each
+// candidate's weight is evaluated with the forward kernel's split_weight on the ray's own
+// line (row j for a ray stepped over rows, column i otherwise): a pixel takes 1 - w when
+// the crossing's integer part is its own index and w when it is one less.  Views are summed
+// in order and channels in increasing order, so the result is deterministic.  With view
+// slices (gridDim.z > 1) the last block of a tile sums the slices in slice order.
+template <int MODE, bool SBF, bool IBF>
+__global__ void __launch_bounds__(FGX * FGY)
+k_gather_fan(GatherArgs g)
+{
+    __shared__ int s_last;
+    const int N = g.N, nd = g.n_det;
+    const int i = blockIdx.x * FGX + (threadIdx.x & 31);
+    const int j = blockIdx.y * FGY + (threadIdx.x >> 5);
+    const bool inside = i < N && j < N;
+    if (g.iter && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *g.iter += 1ull;
+    const int P = gridDim.z, part = blockIdx.z;
+    const int a_beg = (int)(((long long)g.n_ang * part) / P);
+    const int a_end = (int)(((long long)g.n_ang * (part + 1)) / P);
+    float acc = 0.0f;
+    if (inside) {
+        const float cN = 0.5f * (float)(N - 1);
+        const float pu = (float)i - cN, pv = cN - (float)j;     // exact
+        const float fi = (float)i, fj = (float)j;
+        for (int a = a_beg; a < a_end; ++a) {
+            const float4 sv = __ldg(g.views + a);
+            const float du = pu - sv.x, dv = pv - sv.y;
+            const float cr = fmaf(sv.z, dv, -sv.w * du);          // |P - S| sin(gamma_P)
+            const float dt = fmaf(sv.z, du, sv.w * dv);           // |P - S| cos(gamma_P)
+            const float tc = fmaf(atan2f(cr, dt), g.inv_pitch, g.t_off);
+            // x = 1/|P - S| with a relative margin; x + x^3 >= asin(x) for x <= 1/2
+            const float x = 1.002f * rsqrtf(fmaf(du, du, dv * dv));
+            const float half = fmaf(fmaf(x, x * x, x), g.inv_pitch, 0.02f);
+            const int t0 = max(0, (int)ceilf(tc - half));
+            const int t1 = min(nd - 1, (int)floorf(tc + half));
+            const size_t base = (size_t)a * nd;
+            const void* ua = static_cast<const char*>(g.u) + base * St<SBF>::bytes;
+            for (int t = t0; t <= t1; ++t) {
+                const float4 q = __ldg(g.rays + base + t);
+                const float ws = __ldg(g.rayw + base + t);
+                const bool row = !(ws < 0.0f);
+                const float lq = row ? fj : fi;
+                float k0f;
+                const float w = split_weight(fmaf(q.x, lq, q.z), fmaf(q.y, lq, q.w), k0f);
+                const int d = (row ? i : j) - (int)k0f;           // 0: weight 1 - w; 1: weight w
+                if (d == 0 || d == 1) {
+                    const float c = d == 0 ? 1.0f - w : w;
+                    acc = fmaf(c * fabsf(ws), St<SBF>::ld(ua, t), acc);
+                }
+            }
         }
     }
+    if (P > 1) {
+        const size_t NN = (size_t)N * N;
+        if (inside) g.part[(size_t)part * NN + (size_t)j * N + i] = acc;
+        __threadfence();
+        __syncthreads();
+        const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+        if (threadIdx.x == 0) s_last = (atomicAdd(&g.counters[tile], 1) == P - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        float sum = 0.0f;
+        if (inside)
+            for (int pp = 0; pp < P; ++pp) sum += __ldcg(g.part + (size_t)pp * NN + (size_t)j * N + i);
+        acc = sum;
+        if (threadIdx.x == 0) g.counters[tile] = 0;
+    }
+    if (inside) gather_epilogue<MODE, IBF>(g, j, i, acc);
 }
 
 }  // namespace
@@ -326,27 +446,35 @@ int fwd_num_blocks(int n_det, int n_ang)
     return ((n_det + FWD_TB - 1) / FWD_TB) * n_ang;
 }
 
-template <bool PBF, bool SBF>
+template <bool PBF, bool SBF, bool FAN>
 void fwd_dispatch(int mode, const FwdArgs& a, dim3 grid, dim3 block, cudaStream_t st)
 {
     switch (mode) {
-        case FWD_PLAIN: k_fwd<FWD_PLAIN, PBF, SBF><<<grid, block, 0, st>>>(a); break;
-        case FWD_PROX_L2: k_fwd<FWD_PROX_L2, PBF, SBF><<<grid, block, 0, st>>>(a); break;
-        case FWD_PROX_KL: k_fwd<FWD_PROX_KL, PBF, SBF><<<grid, block, 0, st>>>(a); break;
-        case FWD_RESID_L2: k_fwd<FWD_RESID_L2, PBF, SBF><<<grid, block, 0, st>>>(a); break;
-        default: k_fwd<FWD_RESID_KL, PBF, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_PLAIN: k_fwd<FWD_PLAIN, PBF, SBF, FAN><<<grid, block, 0, st>>>(a); break;
+        case FWD_PROX_L2: k_fwd<FWD_PROX_L2, PBF, SBF, FAN><<<grid, block, 0, st>>>(a); break;
+        case FWD_PROX_KL: k_fwd<FWD_PROX_KL, PBF, SBF, FAN><<<grid, block, 0, st>>>(a); break;
+        case FWD_RESID_L2: k_fwd<FWD_RESID_L2, PBF, SBF, FAN><<<grid, block, 0, st>>>(a); break;
+        default: k_fwd<FWD_RESID_KL, PBF, SBF, FAN><<<grid, block, 0, st>>>(a); break;
     }
+}
+
+template <bool FAN>
+void fwd_dispatch_prec(int mode, const FwdArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    if (a.pair_bf && a.sino_bf) fwd_dispatch<true, true, FAN>(mode, a, grid, block, st);
+    else if (a.pair_bf) fwd_dispatch<true, false, FAN>(mode, a, grid, block, st);
+    else if (a.sino_bf) fwd_dispatch<false, true, FAN>(mode, a, grid, block, st);
+    else fwd_dispatch<false, false, FAN>(mode, a, grid, block, st);
 }
 
 cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st)
 {
     if (mode < FWD_PLAIN || mode > FWD_RESID_KL) return cudaErrorInvalidValue;
     if (mode == FWD_PLAIN && a.sino_bf) return cudaErrorInvalidValue;    // y is float
+    if (a.rays && !a.rayw) return cudaErrorInvalidValue;
     dim3 grid((a.n_det + FWD_TB - 1) / FWD_TB, a.n_ang), block(FWD_TB, FWD_SEG);
-    if (a.pair_bf && a.sino_bf) fwd_dispatch<true, true>(mode, a, grid, block, st);
-    else if (a.pair_bf) fwd_dispatch<true, false>(mode, a, grid, block, st);
-    else if (a.sino_bf) fwd_dispatch<false, true>(mode, a, grid, block, st);
-    else fwd_dispatch<false, false>(mode, a, grid, block, st);
+    if (a.rays) fwd_dispatch_prec<true>(mode, a, grid, block, st);
+    else fwd_dispatch_prec<false>(mode, a, grid, block, st);
     return cudaGetLastError();
 }
 
@@ -376,15 +504,47 @@ void gather_dispatch(const GatherArgs& a, dim3 grid, dim3 block, cudaStream_t st
     else k_gather<MODE, false, false><<<grid, block, 0, st>>>(a);
 }
 
+template <int MODE>
+void gather_fan_dispatch(const GatherArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    if (a.sino_bf && a.img_bf) k_gather_fan<MODE, true, true><<<grid, block, 0, st>>>(a);
+    else if (a.sino_bf) k_gather_fan<MODE, true, false><<<grid, block, 0, st>>>(a);
+    else if (a.img_bf) k_gather_fan<MODE, false, true><<<grid, block, 0, st>>>(a);
+    else k_gather_fan<MODE, false, false><<<grid, block, 0, st>>>(a);
+}
+
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
 {
+    if (mode != GATHER_R && mode != GATHER_PDHG) return cudaErrorInvalidValue;
+    if (a.parts < 1 || (a.parts > 1 && (!a.part || !a.counters))) return cudaErrorInvalidValue;
+    if (a.rays) {
+        if (!a.rayw || !a.views || (a.n_ang > 0 && !a.u)) return cudaErrorInvalidValue;
+        dim3 grid((a.N + FGX - 1) / FGX, (a.N + FGY - 1) / FGY, a.parts), block(FGX * FGY);
+        if (mode == GATHER_R) gather_fan_dispatch<GATHER_R>(a, grid, block, st);
+        else gather_fan_dispatch<GATHER_PDHG>(a, grid, block, st);
+        return cudaGetLastError();
+    }
     const int b = (a.N + GT - 1) / GT;
     dim3 grid(b, b, a.parts), block(GT * GW);
-    if (a.parts < 1 || (a.parts > 1 && (!a.part || !a.counters))) return cudaErrorInvalidValue;
     if (mode == GATHER_R) gather_dispatch<GATHER_R>(a, grid, block, st);
-    else if (mode == GATHER_PDHG) gather_dispatch<GATHER_PDHG>(a, grid, block, st);
-    else return cudaErrorInvalidValue;
+    else gather_dispatch<GATHER_PDHG>(a, grid, block, st);
     return cudaGetLastError();
+}
+
+size_t fan_gather_tiles(int N)
+{
+    return (size_t)((N + FGX - 1) / FGX) * (size_t)((N + FGY - 1) / FGY);
+}
+
+int fan_gather_parts(int N, int n_views)
+{
+    // about 1024 blocks of 256 pixels; at most 64 slices
+    const long long tiles = (long long)fan_gather_tiles(N);
+    long long p = (1024 + tiles - 1) / tiles;
+    if (p > 64) p = 64;
+    if (p > n_views) p = n_views;
+    if (p < 1) p = 1;
+    return (int)p;
 }
 
 }  // namespace ncs

@@ -90,6 +90,19 @@ struct AngleParam {
     int pad0, pad1, pad2;
 };
 
+// Fan-beam rays (Sec. 4, fan beam geometry), one entry per ray r = a * n_det + t, FP64 on
+// the host and rounded once.  Ray r crosses stepping line q (a row of x, or a row of x^T)
+// at f = B q + C; as for AngleParam, B and C are split into a multiple of 2^-10 and a
+// remainder, so H = Bhi q + Chi is exact and L = Blo q + Clo small: the same split_weight
+// evaluation as the parallel beam with no per-bin term.  FanRay = (Bhi, Blo, Chi, Clo);
+// the path length W goes in a separate float array, +W for a ray stepped over rows of x,
+// -W for one stepped over rows of x^T.  A ray that passes no pixel has B = 0, C = -8, W = 0.
+// FanView = (Su, Sv, du, dv): the source position of the view and the unit direction of
+// its central ray (towards the rotation centre), used by the gather to find the channels
+// that reach a pixel.
+using FanRay = float4;
+using FanView = float4;
+
 // Images read by the forward projector are stored as "pair images": entry i of
 // row j holds (x[j][i], x[j][i+1]) as one float2, so one aligned 8-byte load
 // serves both interpolation taps, and each row carries PAIR_PAD zero entries on
@@ -122,6 +135,8 @@ struct FwdArgs {
     double* partials;    // RESID: one partial per block (gridDim.x * gridDim.y); PROX_L2 with kx:
                          // the same partials of the data term at the running K x+
     float* kx;           // PROX_L2 or nullptr: running K x, updated to (K xbar + K x) / 2 = K x+
+    const FanRay* rays;  // fan beam: per-ray table (ap unused), or nullptr for the parallel beam
+    const float* rayw;   // fan beam: signed path length per ray
 };
 
 // Gather epilogues.
@@ -147,6 +162,11 @@ struct GatherArgs {
     float* xbar;         // GATHER_PDHG: extrapolated primal
     float inv_gamma;
     unsigned long long* iter;  // if set, block (0,0,0) advances this device iteration counter
+    const FanRay* rays;  // fan beam: per-ray table (ap unused), or nullptr for the parallel beam
+    const float* rayw;   // fan beam: signed path length per ray
+    const FanView* views;// fan beam: per-view source and central direction
+    float inv_pitch;     // fan beam: 1 / (fan angle between adjacent channels)
+    float t_off;         // fan beam: channel coordinate of fan angle 0, (n_det-1)/2 - offset / pitch
 };
 
 // Transpose / finite-difference pass.
@@ -186,6 +206,8 @@ int fwd_num_blocks(int n_det, int n_ang);
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st);
 int gather_parts(int N, int n_ang);          // angle slices the gather uses for this size
 size_t gather_tiles(int N);                  // 32 x 32 tiles of an N x N image
+int fan_gather_parts(int N, int n_views);    // view slices of the fan-beam gather
+size_t fan_gather_tiles(int N);              // blocks (arrival counters) of the fan-beam gather
 cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st);
 int td_num_blocks(int N);
 

@@ -27,4 +27,5 @@ from .phantom import (  # noqa: F401
     pet_problem,
     WORKLOADS,
     batch_sides,
+    fan_pitch,
 )

@@ -178,4 +178,18 @@ WORKLOADS = {
     # 256x256 TV-PET, 1e6 counts, 10% background, lambda 0.02, nonnegativity.
     "pet256": dict(kind="pet", N=256, n_angles=180, n_det=257, n_ellipses=15,
                    lam=0.02, tv="aniso"),
+    # Fan-beam TV-CT (equiangular detector, full turn of source positions): the source at
+    # twice the image side from the centre, the fan just covering the image's circumscribed
+    # circle (fan_pitch with the given cover).  64x64: 120 views, 96 channels, the 64x64
+    # noise and lambda; 512x512: 720 views, 768 channels, the 512x512 noise and lambda.
+    "fan64": dict(kind="ct", geometry="fan", N=64, n_angles=120, n_det=96, src_dist=128.0, cover=1.05,
+                  n_ellipses=10, noise_frac=0.01, lam=0.01, tv="aniso"),
+    "fan512": dict(kind="ct", geometry="fan", N=512, n_angles=720, n_det=768, src_dist=1024.0, cover=1.02,
+                   n_ellipses=20, noise_frac=0.005, lam=0.005, tv="iso"),
 }
+
+
+def fan_pitch(N: int, src_dist: float, n_det: int, cover: float = 1.02) -> float:
+    """Fan angle between adjacent channels (radians) for n_det channels whose fan spans the
+    circle circumscribing the N x N image seen from distance src_dist, widened by `cover`."""
+    return 2.0 * math.asin(N / math.sqrt(2.0) / src_dist) * cover / n_det

@@ -86,3 +86,28 @@ def test_null_plan_calls_are_rejected(lib):
     assert lib.ncs_step(None, None, None, None, None, None, None, 1) == -1
     assert lib.ncs_apply_K(None, None, None) == -1
     lib.ncs_plan_destroy(None)
+
+
+def _create_fan(lib, N, nv=8, nd=10, R=None, pitch=0.01, offset=0.0, views=None):
+    from paper_1810_13100_gb300 import binding
+    g = binding.FanGeometry()
+    g.n_views, g.n_det = nv, nd
+    g.src_dist = 2.0 * N if R is None else R
+    g.pitch, g.offset = pitch, offset
+    if views is not None:
+        arr = (ctypes.c_double * len(views))(*views)
+        g.views = ctypes.cast(arr, ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    rc = lib.ncs_plan_create_fan(ctypes.byref(g), N, N, 0.1, 1.0, None, ctypes.byref(h))
+    return rc, h
+
+
+def test_fan_plan_create_rejects_bad_geometry_before_touching_cuda(lib):
+    assert _create_fan(lib, 64, pitch=0.0)[0] == -1
+    assert _create_fan(lib, 64, pitch=float("nan"))[0] == -1
+    # the source must stay outside the image's circumscribed circle plus 3 pixels
+    assert _create_fan(lib, 64, R=0.5 * 63 * math.sqrt(2.0) + 2.9)[0] == -1
+    assert _create_fan(lib, 64, nv=2, views=[0.0, float("inf")])[0] == -1
+    assert _create_fan(lib, 64, nv=0)[0] == -1
+    assert _create_fan(lib, 17)[0] == -2
+    assert lib.ncs_plan_create_fan(None, 64, 64, 0.1, 1.0, None, None) == -1
