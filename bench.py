@@ -45,7 +45,7 @@ TTG_CAP = 2000
 METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
 # DRAM bytes (read + write) per launch of the current kernels, from one ncu capture
 # (profiles/ncu_k_gather_k_fwd_ct512.md); set to None when a kernel changes.
-NCU_TRAFFIC = {"joseph_gather": 4120832.0, "joseph_fwd": 8508672.0}
+NCU_TRAFFIC = {"joseph_gather": None, "joseph_fwd": 8508672.0}
 # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
 NCU_WARP_INSTR = {"joseph_gather": 301766912.0, "joseph_fwd": 128230021.0}
 
@@ -678,6 +678,10 @@ def run_pet(args, ws, rank, local):
 
 FAN_NCS = dict(alpha=0.01, beta=0.01, h_probes=32)   # as the 512x512 parallel-beam workload
 FAN_PDHG = dict(alpha=0.001, beta=0.001)
+# per launch of the fan-beam kernels, from one ncu capture (profiles/ncu_k_gather_fan_k_fwd_fan512.md);
+# None when a kernel changes
+FAN_NCU_TRAFFIC = {"joseph_gather": 14062848.0, "joseph_fwd": 19752192.0}
+FAN_NCU_WARP_INSTR = {"joseph_gather": 644243860.0, "joseph_fwd": 126397358.0}
 
 
 def fan_plan(ncs, W, params, **kw):
@@ -755,9 +759,17 @@ def run_fan(args, ws, rank, local):
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = 2.0 * nnz / (dom_ms / dom_n / 1000.0) / 1e12
     roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": None,
+            "frac": achieved / fp32_peak, "traffic": FAN_NCU_TRAFFIC.get(dom_name),
             "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
             "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
+    wi = FAN_NCU_WARP_INSTR.get(dom_name)
+    if wi:
+        issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
+        issue = wi / (dom_ms / dom_n / 1000.0) / 1e12
+        roof["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "Twarp-inst/s", "frac": issue / issue_peak,
+                         "warp_instructions_per_launch": wi,
+                         "peak_kind": "152 SMs x 4 schedulers x 1 warp-instruction/cycle x %.0f MHz (derived)"
+                                      % sm_mhz}
     tot_ms = sum(t for t, _ in kern.values())
     kernels = {k: {"ms_per_launch": t / c if c else None, "launches": c, "share": t / tot_ms if tot_ms else None}
                for k, (t, c) in kern.items()}

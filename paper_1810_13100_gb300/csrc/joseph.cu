@@ -358,48 +358,58 @@ k_gather(GatherArgs g)
     }
 }
 
-constexpr int FGX = 32;    // fan-beam gather block: 32 x 8 pixels, one per thread
-constexpr int FGY = 8;
+constexpr int FQX = 16;    // fan-beam gather block: 16 x 8 threads, each owning a 2 x 2 pixel quad,
+constexpr int FQY = 8;     // so a block covers 32 columns x 16 rows
 
-// K^T for the fan beam (pixel-driven, no atomics).  Rays of one view are not parallel,
-// and adjacent rays can cross a line less than a pixel apart, so the tile walk above does
-// not carry over.  Instead each thread owns one pixel P and, per view a, finds the channels
-// whose ray can reach it: a ray that puts a nonzero Joseph weight on P passes within one
-// pixel of P's centre (|f - k| < 1 along the interpolation axis, and the perpendicular
-// distance is that times |cos| or |sin| <= 1), so its fan angle differs from P's fan
-// angle gamma_P = atan2(cross, dot) of (P - S_a) against the central direction by less
-// than asin(1/|P - S_a|).  That window (widened for FP32 rounding) is scanned, and each
-// candidate's weight is evaluated with the forward kernel's split_weight on the ray's own
-// line (row j for a ray stepped over rows, column i otherwise): a pixel takes 1 - w when
-// the crossing's integer part is its own index and w when it is one less.  Views are summed
-// in order and channels in increasing order, so the result is deterministic.  With view
-// slices (gridDim.z > 1) the last block of a tile sums the slices in slice order.
+// Weights that one crossing (integer part k0, fraction w) of a line puts on the two
+// positions p and p + 1 of that line: 1 - w where k0 is the position, w where k0 is one less.
+__device__ __forceinline__ void quad_weights(int p, float k0f, float w, float& c0, float& c1)
+{
+    const int d = p - (int)k0f;
+    c0 = d == 0 ? 1.0f - w : (d == 1 ? w : 0.0f);
+    c1 = d == -1 ? 1.0f - w : (d == 0 ? w : 0.0f);
+}
+
+// K^T for the fan beam (pixel-driven, no atomics).  Rays of one view are not parallel, and
+// adjacent rays can cross a line less than a pixel apart, so the tile walk above does not
+// carry over.  Instead each thread owns a 2 x 2 pixel quad (N is even, so a quad is inside
+// the image or outside it) and, per view a, finds the channels whose ray can reach it: a ray
+// that puts a nonzero Joseph weight on a pixel passes within one pixel of its centre (|f - k|
+// < 1 along the interpolation axis, and the perpendicular distance is that times |cos| or
+// |sin| <= 1), hence within 1 + sqrt(2)/2 of the quad's centre Q, so its fan angle differs
+// from Q's fan angle, atan2(cross, dot) of (Q - S_a) against the central direction, by less
+// than asin((1 + sqrt(2)/2) / |Q - S_a|) <= x + x^3.  That window, widened for FP32 rounding,
+// is scanned; each candidate ray's weights on the quad's two lines (rows j, j + 1 for a ray
+// stepped over rows, columns i, i + 1 otherwise) come from the forward kernel's split_weight
+// on the ray's own coefficients, so the pair holds the same FP32 matrix.  Each pixel sums
+// its views in order and their channels in increasing order (deterministic).  With view slices
+// (gridDim.z > 1) the last block of a tile sums the slices in slice order.
 template <int MODE, bool SBF, bool IBF>
-__global__ void __launch_bounds__(FGX * FGY)
+__global__ void __launch_bounds__(FQX * FQY)
 k_gather_fan(GatherArgs g)
 {
     __shared__ int s_last;
     const int N = g.N, nd = g.n_det;
-    const int i = blockIdx.x * FGX + (threadIdx.x & 31);
-    const int j = blockIdx.y * FGY + (threadIdx.x >> 5);
+    const int i = blockIdx.x * (2 * FQX) + 2 * (int)(threadIdx.x % FQX);
+    const int j = blockIdx.y * (2 * FQY) + 2 * (int)(threadIdx.x / FQX);
     const bool inside = i < N && j < N;
     if (g.iter && threadIdx.x == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *g.iter += 1ull;
     const int P = gridDim.z, part = blockIdx.z;
     const int a_beg = (int)(((long long)g.n_ang * part) / P);
     const int a_end = (int)(((long long)g.n_ang * (part + 1)) / P);
-    float acc = 0.0f;
+    float a00 = 0.0f, a01 = 0.0f, a10 = 0.0f, a11 = 0.0f;     // pixel (j + r, i + c) in a{r}{c}
     if (inside) {
         const float cN = 0.5f * (float)(N - 1);
-        const float pu = (float)i - cN, pv = cN - (float)j;     // exact
+        const float qu = ((float)i + 0.5f) - cN, qv = cN - ((float)j + 0.5f);   // quad centre (exact)
         const float fi = (float)i, fj = (float)j;
         for (int a = a_beg; a < a_end; ++a) {
             const float4 sv = __ldg(g.views + a);
-            const float du = pu - sv.x, dv = pv - sv.y;
-            const float cr = fmaf(sv.z, dv, -sv.w * du);          // |P - S| sin(gamma_P)
-            const float dt = fmaf(sv.z, du, sv.w * dv);           // |P - S| cos(gamma_P)
+            const float du = qu - sv.x, dv = qv - sv.y;
+            const float cr = fmaf(sv.z, dv, -sv.w * du);          // |Q - S| sin(gamma_Q)
+            const float dt = fmaf(sv.z, du, sv.w * dv);           // |Q - S| cos(gamma_Q)
             const float tc = fmaf(atan2f(cr, dt), g.inv_pitch, g.t_off);
-            // x = 1/|P - S| with a relative margin; x + x^3 >= asin(x) for x <= 1/2
-            const float x = 1.002f * rsqrtf(fmaf(du, du, dv * dv));
+            // x = (1 + sqrt(2)/2) / |Q - S| with a relative margin of 2e-3
+            const float x = fminf(1.0f, 1.7092f * rsqrtf(fmaf(du, du, dv * dv)));
             const float half = fmaf(fmaf(x, x * x, x), g.inv_pitch, 0.02f);
             const int t0 = max(0, (int)ceilf(tc - half));
             const int t1 = min(nd - 1, (int)floorf(tc + half));
@@ -409,20 +419,32 @@ k_gather_fan(GatherArgs g)
                 const float4 q = __ldg(g.rays + base + t);
                 const float ws = __ldg(g.rayw + base + t);
                 const bool row = !(ws < 0.0f);
-                const float lq = row ? fj : fi;
-                float k0f;
-                const float w = split_weight(fmaf(q.x, lq, q.z), fmaf(q.y, lq, q.w), k0f);
-                const int d = (row ? i : j) - (int)k0f;           // 0: weight 1 - w; 1: weight w
-                if (d == 0 || d == 1) {
-                    const float c = d == 0 ? 1.0f - w : w;
-                    acc = fmaf(c * fabsf(ws), St<SBF>::ld(ua, t), acc);
-                }
+                const float Wu = fabsf(ws) * St<SBF>::ld(ua, t);
+                const float l0 = row ? fj : fi;             // the quad's first line for this ray
+                const float l1 = l0 + 1.0f;
+                const int p0 = row ? i : j;                 // its first position along the line
+                float kA, kB, cA0, cA1, cB0, cB1;
+                const float wA = split_weight(fmaf(q.x, l0, q.z), fmaf(q.y, l0, q.w), kA);
+                const float wB = split_weight(fmaf(q.x, l1, q.z), fmaf(q.y, l1, q.w), kB);
+                quad_weights(p0, kA, wA, cA0, cA1);
+                quad_weights(p0, kB, wB, cB0, cB1);
+                // row branch: line A is row j, line B row j + 1; column branch: A is column i, B column i + 1
+                const float c01 = row ? cA1 : cB0;
+                const float c10 = row ? cB0 : cA1;
+                a00 = cA0 != 0.0f ? fmaf(cA0, Wu, a00) : a00;
+                a01 = c01 != 0.0f ? fmaf(c01, Wu, a01) : a01;
+                a10 = c10 != 0.0f ? fmaf(c10, Wu, a10) : a10;
+                a11 = cB1 != 0.0f ? fmaf(cB1, Wu, a11) : a11;
             }
         }
     }
     if (P > 1) {
         const size_t NN = (size_t)N * N;
-        if (inside) g.part[(size_t)part * NN + (size_t)j * N + i] = acc;
+        float* pp0 = g.part + (size_t)part * NN + (size_t)j * N + i;
+        if (inside) {
+            *reinterpret_cast<float2*>(pp0) = make_float2(a00, a01);
+            *reinterpret_cast<float2*>(pp0 + N) = make_float2(a10, a11);
+        }
         __threadfence();
         __syncthreads();
         const int tile = blockIdx.y * gridDim.x + blockIdx.x;
@@ -430,13 +452,25 @@ k_gather_fan(GatherArgs g)
         __syncthreads();
         if (!s_last) return;
         __threadfence();
-        float sum = 0.0f;
+        a00 = a01 = a10 = a11 = 0.0f;
         if (inside)
-            for (int pp = 0; pp < P; ++pp) sum += __ldcg(g.part + (size_t)pp * NN + (size_t)j * N + i);
-        acc = sum;
+            for (int k = 0; k < P; ++k) {
+                const float* src = g.part + (size_t)k * NN + (size_t)j * N + i;
+                const float2 r0 = __ldcg(reinterpret_cast<const float2*>(src));
+                const float2 r1 = __ldcg(reinterpret_cast<const float2*>(src + N));
+                a00 += r0.x;
+                a01 += r0.y;
+                a10 += r1.x;
+                a11 += r1.y;
+            }
         if (threadIdx.x == 0) g.counters[tile] = 0;
     }
-    if (inside) gather_epilogue<MODE, IBF>(g, j, i, acc);
+    if (inside) {
+        gather_epilogue<MODE, IBF>(g, j, i, a00);
+        gather_epilogue<MODE, IBF>(g, j, i + 1, a01);
+        gather_epilogue<MODE, IBF>(g, j + 1, i, a10);
+        gather_epilogue<MODE, IBF>(g, j + 1, i + 1, a11);
+    }
 }
 
 }  // namespace
@@ -519,7 +553,8 @@ cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
     if (a.parts < 1 || (a.parts > 1 && (!a.part || !a.counters))) return cudaErrorInvalidValue;
     if (a.rays) {
         if (!a.rayw || !a.views || (a.n_ang > 0 && !a.u)) return cudaErrorInvalidValue;
-        dim3 grid((a.N + FGX - 1) / FGX, (a.N + FGY - 1) / FGY, a.parts), block(FGX * FGY);
+        if (a.N % 2 != 0) return cudaErrorInvalidValue;
+        dim3 grid((a.N + 2 * FQX - 1) / (2 * FQX), (a.N + 2 * FQY - 1) / (2 * FQY), a.parts), block(FQX * FQY);
         if (mode == GATHER_R) gather_fan_dispatch<GATHER_R>(a, grid, block, st);
         else gather_fan_dispatch<GATHER_PDHG>(a, grid, block, st);
         return cudaGetLastError();
@@ -533,14 +568,14 @@ cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
 
 size_t fan_gather_tiles(int N)
 {
-    return (size_t)((N + FGX - 1) / FGX) * (size_t)((N + FGY - 1) / FGY);
+    return (size_t)((N + 2 * FQX - 1) / (2 * FQX)) * (size_t)((N + 2 * FQY - 1) / (2 * FQY));
 }
 
 int fan_gather_parts(int N, int n_views)
 {
-    // about 1024 blocks of 256 pixels; at most 64 slices
+    // about 152 x 8 blocks of 128 threads (2048 pixels each); at most 64 slices
     const long long tiles = (long long)fan_gather_tiles(N);
-    long long p = (1024 + tiles - 1) / tiles;
+    long long p = (1216 + tiles - 1) / tiles;
     if (p > 64) p = 64;
     if (p > n_views) p = n_views;
     if (p < 1) p = 1;
