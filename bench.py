@@ -676,12 +676,14 @@ def run_pet(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
-FAN_NCS = dict(alpha=0.01, beta=0.01, h_probes=32)   # as the 512x512 parallel-beam workload
+FAN_NCS = dict(alpha=0.01, beta=0.01, h_probes=128)   # {1,3} x 10^p grid on this workload (seed 0)
 FAN_PDHG = dict(alpha=0.001, beta=0.001)
 # per launch of the fan-beam kernels, from one ncu capture (profiles/ncu_k_gather_fan_k_fwd_fan512.md);
 # None when a kernel changes
-FAN_NCU_TRAFFIC = {"joseph_gather": 14062848.0, "joseph_fwd": 19752192.0}
-FAN_NCU_WARP_INSTR = {"joseph_gather": 644243860.0, "joseph_fwd": 126397358.0}
+FAN_NCU_TRAFFIC = {"joseph_gather": 14109952.0, "joseph_fwd": 19752192.0}
+FAN_NCU_WARP_INSTR = {"joseph_gather": 355371778.0, "joseph_fwd": 126397358.0}
+# the same for the pixel-quad K^T kernel (--fan-gather quads)
+FAN_NCU_QUADS = {"traffic": 14062848.0, "warp_instr": 644243860.0}
 
 
 def fan_plan(ncs, W, params, **kw):
@@ -707,7 +709,7 @@ def run_fan(args, ws, rank, local):
     N, na, nd = W["N"], W["n_angles"], W["n_det"]
     n, m = N * N, na * nd
     seed = args.seed + rank
-    plan = fan_plan(ncs, W, FAN_NCS, h_probes=FAN_NCS["h_probes"])
+    plan = fan_plan(ncs, W, FAN_NCS, h_probes=FAN_NCS["h_probes"], fan_gather=args.fan_gather)
     pr = synth.ct_problem(seed, N, na, nd, W["n_ellipses"], W["noise_frac"], gpu_projector(plan, dev))
     b = torch.from_numpy(pr["b"].ravel()).to(dev)
     x = torch.zeros(n, device=dev); u = torch.zeros(m, device=dev); v = torch.zeros(2 * n, device=dev)
@@ -757,12 +759,14 @@ def run_fan(args, ws, rank, local):
     nnz = plan.nnz()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    quads = dom_name == "joseph_gather" and args.fan_gather == "quads"
     achieved = 2.0 * nnz / (dom_ms / dom_n / 1000.0) / 1e12
     roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak, "traffic": FAN_NCU_TRAFFIC.get(dom_name),
+            "frac": achieved / fp32_peak,
+            "traffic": FAN_NCU_QUADS["traffic"] if quads else FAN_NCU_TRAFFIC.get(dom_name),
             "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
             "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
-    wi = FAN_NCU_WARP_INSTR.get(dom_name)
+    wi = FAN_NCU_QUADS["warp_instr"] if quads else FAN_NCU_WARP_INSTR.get(dom_name)
     if wi:
         issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
         issue = wi / (dom_ms / dom_n / 1000.0) / 1e12
@@ -784,7 +788,7 @@ def run_fan(args, ws, rank, local):
         xs = torch.zeros(n, device=dev)
         rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=4000, f_star=fs)
         ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-        pplan = fan_plan(ncs, W, FAN_PDHG, h_probes=1, power_max_iter=2)
+        pplan = fan_plan(ncs, W, FAN_PDHG, h_probes=1, power_max_iter=2, fan_gather=args.fan_gather)
         xs.zero_()
         rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=fs)
         ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
@@ -797,7 +801,7 @@ def run_fan(args, ws, rank, local):
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "512x512 fan-beam TV-CT, 720 views on [0, 2pi), 768 equiangular channels, "
                                        "source at 1024 px, 20 ellipses, 0.5%% noise, iso TV lambda 0.005, seed %d"
-                                       % seed, "ncs": FAN_NCS, "pdhg": FAN_PDHG,
+                                       % seed, "ncs": FAN_NCS, "pdhg": FAN_PDHG, "fan_gather": args.fan_gather,
                            "l2": "flushed before every step (256 MiB write, untimed)"},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "peaks": peak_kind,
                 "time_to_gap": ttg, "clocks": clk.summary()}
@@ -887,6 +891,8 @@ def main():
                     help="time the ADMM comparator over a grid of alpha and n_cg on the first seed")
     ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256", "fan512"])
     ap.add_argument("--slices", type=int, default=64)
+    ap.add_argument("--fan-gather", default="auto", choices=["auto", "lines", "quads"],
+                    help="fan-beam K^T kernel (fan512 workload)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -98,6 +98,9 @@ typedef struct {
                               (SplitMix64 seeds power_seed + 1 .. power_seed + P, uniform in
                               [-1, 1)): sum_v Re((F K^T K v) conj(F v)) / sum_v |F v|^2, clamped at
                               0; the DC entry stays h_dc either way */
+    int fan_gather;        /* fan-beam plans only, the K^T kernel: 0 (default) or 2: ray-driven 32 x 32 tiles,
+                              1: pixel-driven 2 x 2 quads (both exact transposes); with autotune = 1 the plan
+                              times both and keeps the faster */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */
@@ -114,7 +117,7 @@ typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and so
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
  * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
- * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0. */
+ * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0, fan_gather 0. */
 void ncs_options_default(ncs_options* opt);
 
 /* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).
@@ -152,7 +155,7 @@ typedef struct {
  * ncs_plan_create, with K the Joseph projector of the fan's rays (each ray stepped over the
  * rows or the columns of the image by the parallel beam's rule, ties to rows) and K^T its
  * exact transpose.  The projector part of M comes from eq. (H-fan) (least-squares form over
- * ncs_options.h_probes probe images; 0 selects 16), since eq. (circ_R) is for the parallel
+ * ncs_options.h_probes probe images; 0 selects 128), since eq. (circ_R) is for the parallel
  * beam; c_r is ignored.  ncs_fbp is not available for a fan plan (NCS_ERR_UNSUPPORTED).
  * Errors as ncs_plan_create, and NCS_ERR_BADARG for a non-positive pitch, non-finite
  * values or a source inside the image's circumscribed circle (plus a 3-pixel margin).

@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("data", ctypes.c_int), ("tv", ctypes.c_int), ("nonneg", ctypes.c_int), ("prec", ctypes.c_int),
                 ("a3_margin", ctypes.c_double), ("power_max_iter", ctypes.c_int), ("power_tol", ctypes.c_double),
                 ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
-                ("autotune", ctypes.c_int), ("warm_dual", ctypes.c_int), ("h_probes", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("warm_dual", ctypes.c_int), ("h_probes", ctypes.c_int),
+                ("fan_gather", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -181,13 +182,14 @@ class Plan:
     Parallel beam by default (ncs_plan_create: n_angles angles, n_det bins, det_spacing,
     det_offset, angles).  Giving src_dist selects the fan beam (ncs_plan_create_fan):
     n_angles source positions (angles: their beta_a, default 2 pi a / n_angles), n_det
-    channels at fan pitch fan_pitch (radians) with centre offset fan_offset."""
+    channels at fan pitch fan_pitch (radians) with centre offset fan_offset; fan_gather picks
+    its K^T kernel ("auto" / "lines": ray-driven tiles, "quads": pixel-driven 2 x 2 quads)."""
 
     def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
                  power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
                  det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False, warm_dual=False,
-                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0):
+                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0, fan_gather="auto"):
         import torch
         L = load_library()
         self._L = L
@@ -230,6 +232,7 @@ class Plan:
         o.autotune = 1 if autotune else 0
         o.warm_dual = 1 if warm_dual else 0
         o.h_probes = int(h_probes)
+        o.fan_gather = {"auto": 0, "quads": 1, "lines": 2}[fan_gather]
         # With no stream given, the plan runs on a side stream that is ordered
         # after torch's current stream on entry to every call and before it on
         # exit, so results are visible to torch without extra synchronisation.

@@ -54,6 +54,7 @@ struct ncs_plan {
     float* d_rayw = nullptr;
     FanView* d_views = nullptr;
     float inv_pitch = 0.f, t_off = 0.f;
+    bool fan_lines = true;           // fan-beam K^T: ray-driven tiles (true) or pixel quads (false)
     float2* d_tw = nullptr;
     RadixPlan rp{};
     std::vector<double> mu;          // eigenvalues of M, N x N, [p][q]
@@ -233,6 +234,7 @@ int enq_gather(ncs_plan* p, int mode, const void* u, const void* v, float dscale
     g.views = p->d_views;
     g.inv_pitch = p->inv_pitch;
     g.t_off = p->t_off;
+    g.fan_lines = p->fan_lines ? 1 : 0;
     g.N = p->N;
     g.n_ang = n_ang;
     g.n_det = p->nd;
@@ -754,9 +756,10 @@ int build_common(ncs_plan* p)
     CKS(alloc_pair(p, &p->d_tmp2));
     CKS(alloc_pair(p, &p->d_tmpT2));
     CKS(dalloc(&p->d_spec, (H + 1) * N));
-    p->gparts = p->fan ? fan_gather_parts(N, na) : gather_parts(N, na);
-    const size_t counters = p->fan ? fan_gather_tiles(N) : gather_tiles(N);
-    CKS(dalloc(&p->d_gpart, p->gparts > 1 ? (size_t)p->gparts * n : 1));
+    p->gparts = !p->fan ? gather_parts(N, na) : p->fan_lines ? fan_lines_parts(N, na) : fan_gather_parts(N, na);
+    const size_t counters = p->fan ? fan_gather_tiles(N) : gather_tiles(N);   // fan: enough for either kernel
+    const size_t slices = p->fan ? (size_t)std::max(fan_lines_parts(N, na), fan_gather_parts(N, na)) : p->gparts;
+    CKS(dalloc(&p->d_gpart, slices > 1 ? slices * n : 1));
     CKS(dalloc(&p->d_gcount, counters));
     CKS(dalloc(&p->d_iter, 1));
     CK(cudaMemsetAsync(p->d_iter, 0, sizeof(unsigned long long), p->st));
@@ -846,14 +849,39 @@ int time_launches(ncs_plan* p, int reps, F fn, float* ms)
     return rc;
 }
 
+// Fan beam: time the two K^T kernels (pixel quads, ray-driven tiles), each with its default
+// view slices, on the plan's sizes, and keep the faster.
+int autotune_fan_gather(ncs_plan* p)
+{
+    float* y = nullptr;
+    float* xo = nullptr;
+    CKS(dalloc(&y, MM(p)));
+    int rc = dalloc(&xo, NN(p));
+    if (rc == NCS_OK && cudaMemsetAsync(y, 0, MM(p) * sizeof(float), p->st) != cudaSuccess) rc = NCS_ERR_CUDA;
+    float ms[2] = {1e30f, 1e30f};
+    for (int k = 0; k < 2 && rc == NCS_OK; ++k) {
+        p->fan_lines = k == 1;
+        p->gparts = p->fan_lines ? fan_lines_parts(p->N, p->na) : fan_gather_parts(p->N, p->na);
+        rc = time_launches(p, 5, [&]() {
+            return enq_gather(p, GATHER_R, y, nullptr, 0.f, nullptr, 0.f, xo, nullptr, nullptr, 0.f, p->na);
+        }, &ms[k]);
+    }
+    p->fan_lines = ms[1] <= ms[0];
+    p->gparts = p->fan_lines ? fan_lines_parts(p->N, p->na) : fan_gather_parts(p->N, p->na);
+    cudaFree(y);
+    cudaFree(xo);
+    return rc;
+}
+
 // Autotuner: the gather's number of angle slices (half, same, double the default)
 // and the order of the FFT radices (distinct permutations), each timed on the plan's
 // own sizes with CUDA events; the fastest is kept.
 int autotune_plan(ncs_plan* p)
 {
+    if (p->fan) CKS(autotune_fan_gather(p));
     const int base = p->gparts;
     int cand[3] = {std::max(1, base / 2), base, std::min(std::min(64, p->na), base * 2)};
-    if (p->fan) cand[0] = cand[2] = base;      // the fan gather's view slices are not tuned
+    if (p->fan) cand[0] = cand[2] = base;      // the fan gather's view slices are set with its kernel
     const int cmax = std::max(cand[2], base);
     if (cmax > 1) {
         float* bigger = nullptr;
@@ -1229,6 +1257,7 @@ void ncs_options_default(ncs_options* o)
     o->autotune = 0;
     o->warm_dual = 0;
     o->h_probes = 0;
+    o->fan_gather = 0;
 }
 
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,
@@ -1275,9 +1304,13 @@ int ncs_plan_create_fan(const ncs_fan_geometry* geom, int nx, int ny, double lam
     ncs_options o;
     if (opt) o = *opt;
     else ncs_options_default(&o);
-    if (o.h_probes == 0) o.h_probes = 16;   // the fan beam has no closed-form H_R
+    // the fan beam has no closed-form H_R; with fewer probes the estimate's noise leaves some
+    // frequencies far too low (512x512 fan: rho(M^{-1} alpha A^T A) 47 with 32 probes, 8.7 with 128)
+    if (o.h_probes == 0) o.h_probes = 128;
+    if (o.fan_gather < 0 || o.fan_gather > 2) return NCS_ERR_BADARG;
     ncs_plan* p = nullptr;
     CKS(new_plan(nx, ny, geom->n_views, geom->n_det, lambda, alpha, &o, &p));
+    p->fan_lines = o.fan_gather != 1;
     int rc = open_stream(p);
     if (rc == NCS_OK) rc = build_fan_tables(p, geom);
     if (rc == NCS_OK) rc = build_common(p);

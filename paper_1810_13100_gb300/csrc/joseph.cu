@@ -473,6 +473,162 @@ k_gather_fan(GatherArgs g)
     }
 }
 
+constexpr int LT = 32;     // line-walk fan gather: 32 x 32 pixel tile per block
+constexpr int LW = 4;      // warps per block, each with a private shared tile
+constexpr int LCAP = 64;   // rays staged per warp at a time
+
+// K^T for the fan beam, ray-driven (no atomics).  A block owns a 32 x 32 tile and a slice of
+// the views; warps take whole views round robin.  Lane l owns line l of the tile: row j0 + l
+// for rays stepped over rows, column i0 + l for rays stepped over columns, so whatever ray a
+// lane works on it writes only its own row (or column) of the warp's tile, and rays closer
+// than a pixel (adjacent fan rays can be) never collide.  The rays that can put a weight on
+// the tile cross the tile widened by one pixel, so their channels lie between the fan angles
+// of its four corners (atan2 of each corner seen from the source, widened for FP32
+// rounding).  They are staged, up to 64 at a time, in the warp's shared arrays by coalesced
+// loads (coefficients and W u), rays stepped over rows from the front in channel order and
+// rays stepped over columns from the back; each lane then walks the row list and, after a
+// warp barrier, the column list, starting at a lane-dependent offset (11 l mod n) so that
+// simultaneous shared-memory writes spread over the banks.  The crossing and weight come
+// from the forward's split_weight on the ray's coefficients and the lane's line.  Per pixel
+// the order of the sums is fixed (views by warp and slice, rays by lane), so the result is
+// deterministic.  Warp tiles are summed in a fixed order and view slices by the last block
+// of a tile, as in k_gather.
+template <int MODE, bool SBF, bool IBF>
+__global__ void __launch_bounds__(LT * LW)
+k_gather_fan_lines(GatherArgs g)
+{
+    __shared__ float acc[LW][LT][LT + 1];
+    __shared__ float stage[LW][5][LCAP];      // Bhi, Blo, Chi, Clo, |W| u of the staged rays
+    __shared__ int s_last;
+    const int N = g.N, nd = g.n_det;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int i0 = blockIdx.x * LT, j0 = blockIdx.y * LT;
+    float (*A)[LT + 1] = acc[wid];
+    float (*S)[LCAP] = stage[wid];
+    if (g.iter && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *g.iter += 1ull;
+    for (int rr = 0; rr < LT; ++rr) A[rr][lane] = 0.0f;
+    __syncwarp();
+    const int P = gridDim.z, part = blockIdx.z;
+    const int a_beg = (int)(((long long)g.n_ang * part) / P);
+    const int a_end = (int)(((long long)g.n_ang * (part + 1)) / P);
+    const float cN = 0.5f * (float)(N - 1);
+    // corner (lane & 3) of the tile widened by one pixel: columns i0 - 1 / i0 + 32, rows j0 - 1 / j0 + 32
+    const float cu = ((lane & 1) ? (float)(i0 + LT) : (float)(i0 - 1)) - cN;
+    const float cv = cN - ((lane & 2) ? (float)(j0 + LT) : (float)(j0 - 1));
+    const float lrow = (float)(j0 + lane), lcol = (float)(i0 + lane);
+    const unsigned below = (1u << lane) - 1u;
+    for (int a = a_beg + wid; a < a_end; a += LW) {
+        const float4 sv = __ldg(g.views + a);
+        const float du = cu - sv.x, dv = cv - sv.y;
+        const float tcor = fmaf(atan2f(fmaf(sv.z, dv, -sv.w * du), fmaf(sv.z, du, sv.w * dv)), g.inv_pitch, g.t_off);
+        float tmin = fminf(tcor, __shfl_xor_sync(0xffffffffu, tcor, 1));
+        float tmax = fmaxf(tcor, __shfl_xor_sync(0xffffffffu, tcor, 1));
+        tmin = fminf(tmin, __shfl_xor_sync(0xffffffffu, tmin, 2));
+        tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, 2));
+        const int t0 = max(0, (int)ceilf(tmin - 0.02f));
+        const int t1 = min(nd - 1, (int)floorf(tmax + 0.02f));
+        const size_t base = (size_t)a * nd;
+        const void* ua = static_cast<const char*>(g.u) + base * St<SBF>::bytes;
+        for (int c0 = t0; c0 <= t1; c0 += LCAP) {                  // warp-uniform
+            const int c1 = min(t1, c0 + LCAP - 1);
+            int nR = 0, nC = 0;
+            for (int tb = c0; tb <= c1; tb += 32) {
+                const int t = tb + lane;
+                const bool valid = t <= c1;
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                float ws = 0.0f, uu = 0.0f;
+                if (valid) {
+                    q = __ldg(g.rays + base + t);
+                    ws = __ldg(g.rayw + base + t);
+                    uu = St<SBF>::ld(ua, t);
+                }
+                const bool isrow = valid && !(ws < 0.0f);
+                const bool iscol = valid && ws < 0.0f;
+                const unsigned mr = __ballot_sync(0xffffffffu, isrow);
+                const unsigned mc = __ballot_sync(0xffffffffu, iscol);
+                if (valid) {
+                    const int slot = isrow ? nR + __popc(mr & below) : LCAP - 1 - (nC + __popc(mc & below));
+                    S[0][slot] = q.x;
+                    S[1][slot] = q.y;
+                    S[2][slot] = q.z;
+                    S[3][slot] = q.w;
+                    S[4][slot] = fabsf(ws) * uu;
+                }
+                nR += __popc(mr);
+                nC += __popc(mc);
+            }
+            __syncwarp();
+            for (int pass = 0; pass < 2; ++pass) {
+                const int n = pass == 0 ? nR : nC;
+                if (pass == 1) __syncwarp();
+                if (n == 0) continue;                                // warp-uniform
+                const bool rowpass = pass == 0;
+                const int s0 = rowpass ? 0 : LCAP - nC;
+                const float lf = rowpass ? lrow : lcol;
+                const int o0 = rowpass ? i0 : j0;
+                int sidx = (lane * 11) % n;
+                for (int k = 0; k < n; ++k) {
+                    const int e = s0 + sidx;
+                    float k0f;
+                    const float w = split_weight(fmaf(S[0][e], lf, S[2][e]), fmaf(S[1][e], lf, S[3][e]), k0f);
+                    const float Wu = S[4][e];
+                    const int kk = (int)k0f - o0;
+                    if ((unsigned)kk < (unsigned)LT) {
+                        float& d = rowpass ? A[lane][kk] : A[kk][lane];
+                        d = fmaf(1.0f - w, Wu, d);
+                    }
+                    if ((unsigned)(kk + 1) < (unsigned)LT) {
+                        float& d = rowpass ? A[lane][kk + 1] : A[kk + 1][lane];
+                        d = fmaf(w, Wu, d);
+                    }
+                    sidx = sidx + 1 == n ? 0 : sidx + 1;
+                }
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // sum the warp tiles in a fixed order; thread -> pixels (q*LW + wid, lane)
+    float tot[LT / LW];
+#pragma unroll
+    for (int q = 0; q < LT / LW; ++q) {
+        const int rr = q * LW + wid;
+        float sum = 0.0f;
+#pragma unroll
+        for (int w = 0; w < LW; ++w) sum += acc[w][rr][lane];
+        tot[q] = sum;
+    }
+    if (P > 1) {
+        const size_t NN = (size_t)N * N;
+#pragma unroll
+        for (int q = 0; q < LT / LW; ++q) {
+            const int j = j0 + q * LW + wid, i = i0 + lane;
+            if (j < N && i < N) g.part[(size_t)part * NN + (size_t)j * N + i] = tot[q];
+        }
+        __threadfence();
+        __syncthreads();
+        const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+        if (tid == 0) s_last = (atomicAdd(&g.counters[tile], 1) == P - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+#pragma unroll
+        for (int q = 0; q < LT / LW; ++q) {
+            const int j = j0 + q * LW + wid, i = i0 + lane;
+            float sum = 0.0f;
+            if (j < N && i < N)
+                for (int pp = 0; pp < P; ++pp) sum += __ldcg(g.part + (size_t)pp * NN + (size_t)j * N + i);
+            tot[q] = sum;
+        }
+        if (tid == 0) g.counters[tile] = 0;
+    }
+#pragma unroll
+    for (int q = 0; q < LT / LW; ++q) {
+        const int j = j0 + q * LW + wid, i = i0 + lane;
+        if (j < N && i < N) gather_epilogue<MODE, IBF>(g, j, i, tot[q]);
+    }
+}
+
 }  // namespace
 
 int fwd_num_blocks(int n_det, int n_ang)
@@ -547,10 +703,27 @@ void gather_fan_dispatch(const GatherArgs& a, dim3 grid, dim3 block, cudaStream_
     else k_gather_fan<MODE, false, false><<<grid, block, 0, st>>>(a);
 }
 
+template <int MODE>
+void gather_fan_lines_dispatch(const GatherArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    if (a.sino_bf && a.img_bf) k_gather_fan_lines<MODE, true, true><<<grid, block, 0, st>>>(a);
+    else if (a.sino_bf) k_gather_fan_lines<MODE, true, false><<<grid, block, 0, st>>>(a);
+    else if (a.img_bf) k_gather_fan_lines<MODE, false, true><<<grid, block, 0, st>>>(a);
+    else k_gather_fan_lines<MODE, false, false><<<grid, block, 0, st>>>(a);
+}
+
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
 {
     if (mode != GATHER_R && mode != GATHER_PDHG) return cudaErrorInvalidValue;
     if (a.parts < 1 || (a.parts > 1 && (!a.part || !a.counters))) return cudaErrorInvalidValue;
+    if (a.rays && a.fan_lines) {
+        if (!a.rayw || !a.views || (a.n_ang > 0 && !a.u)) return cudaErrorInvalidValue;
+        const int b = (a.N + LT - 1) / LT;
+        dim3 grid(b, b, a.parts), block(LT * LW);
+        if (mode == GATHER_R) gather_fan_lines_dispatch<GATHER_R>(a, grid, block, st);
+        else gather_fan_lines_dispatch<GATHER_PDHG>(a, grid, block, st);
+        return cudaGetLastError();
+    }
     if (a.rays) {
         if (!a.rayw || !a.views || (a.n_ang > 0 && !a.u)) return cudaErrorInvalidValue;
         if (a.N % 2 != 0) return cudaErrorInvalidValue;
@@ -569,6 +742,17 @@ cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
 size_t fan_gather_tiles(int N)
 {
     return (size_t)((N + 2 * FQX - 1) / (2 * FQX)) * (size_t)((N + 2 * FQY - 1) / (2 * FQY));
+}
+
+int fan_lines_parts(int N, int n_views)
+{
+    // about 2048 blocks of 4 warps; at most 64 slices
+    const long long tiles = (long long)gather_tiles(N);
+    long long p = (2048 + tiles - 1) / tiles;
+    if (p > 64) p = 64;
+    if (p > n_views) p = n_views;
+    if (p < 1) p = 1;
+    return (int)p;
 }
 
 int fan_gather_parts(int N, int n_views)

@@ -167,6 +167,7 @@ struct GatherArgs {
     const FanView* views;// fan beam: per-view source and central direction
     float inv_pitch;     // fan beam: 1 / (fan angle between adjacent channels)
     float t_off;         // fan beam: channel coordinate of fan angle 0, (n_det-1)/2 - offset / pitch
+    int fan_lines;       // fan beam: 1 = ray-driven tile walk (k_gather_fan_lines), 0 = pixel quads (k_gather_fan)
 };
 
 // Transpose / finite-difference pass.
@@ -206,7 +207,8 @@ int fwd_num_blocks(int n_det, int n_ang);
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st);
 int gather_parts(int N, int n_ang);          // angle slices the gather uses for this size
 size_t gather_tiles(int N);                  // 32 x 32 tiles of an N x N image
-int fan_gather_parts(int N, int n_views);    // view slices of the fan-beam gather
+int fan_gather_parts(int N, int n_views);    // view slices of the fan-beam gather (pixel quads)
+int fan_lines_parts(int N, int n_views);     // view slices of the fan-beam gather (ray-driven tiles)
 size_t fan_gather_tiles(int N);              // blocks (arrival counters) of the fan-beam gather
 cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st);
 int td_num_blocks(int N);

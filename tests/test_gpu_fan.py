@@ -64,20 +64,23 @@ def test_fan_forward_parity(N, na, nd, R, pitch, off, views):
     assert rel_l2(to_np(y), ref) <= TOL
 
 
+@pytest.mark.parametrize("kernel", ["lines", "quads"])
 @pytest.mark.parametrize("N,na,nd,R,pitch,off,views", FAN_GEOMS)
-def test_fan_gather_transpose_parity(N, na, nd, R, pitch, off, views):
+def test_fan_gather_transpose_parity(N, na, nd, R, pitch, off, views, kernel):
+    """Both K^T kernels: the ray-driven tile walk (default) and the pixel-driven quads."""
     yv = f32(np.random.default_rng(7 * N + na).uniform(-1, 1, (na, nd)))
     ref = oop.KT(yv, ogeom(N, na, nd, R, pitch, off, views))
-    plan = fan_plan(N, na, nd, R, pitch, off, views, power_max_iter=2, h_probes=1)
+    plan = fan_plan(N, na, nd, R, pitch, off, views, power_max_iter=2, h_probes=1, fan_gather=kernel)
     x = plan.apply_KT(torch.from_numpy(yv.ravel().astype(np.float32)).cuda())
     plan.close()
     assert rel_l2(to_np(x), ref) <= TOL
 
 
+@pytest.mark.parametrize("kernel", ["lines", "quads"])
 @pytest.mark.parametrize("N,na,nd,R,pitch,off,views", FAN_GEOMS[:5])
-def test_fan_gpu_pair_is_exact_transpose(N, na, nd, R, pitch, off, views):
+def test_fan_gpu_pair_is_exact_transpose(N, na, nd, R, pitch, off, views, kernel):
     """<K x, y> = <x, K^T y> for the GPU pair (FP64 dot products of the FP32 results)."""
-    plan = fan_plan(N, na, nd, R, pitch, off, views, power_max_iter=2, h_probes=1)
+    plan = fan_plan(N, na, nd, R, pitch, off, views, power_max_iter=2, h_probes=1, fan_gather=kernel)
     gen = torch.Generator(device="cuda").manual_seed(5)
     for _ in range(3):
         x = torch.rand(N * N, device="cuda", generator=gen) * 2 - 1
@@ -111,12 +114,13 @@ def test_fan_probe_mu_matches_oracle():
     assert rel_l2(mu_gpu, mu_ref) <= 1e-4
 
 
-def run_fan_pair(N, na, nd, R, pitch, tv, lam, alpha, beta, iters, solver="ncs", probes=8):
+def run_fan_pair(N, na, nd, R, pitch, tv, lam, alpha, beta, iters, solver="ncs", probes=8, kernel="auto"):
     import paper_1810_13100_gb300 as ncs
     g = ogeom(N, na, nd, R, pitch, 0.0, None)
     pr = synth.ct_problem(1, N, na, nd, 8, 0.01, lambda x: oop.K(x, g))
     P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv=tv)
-    plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, src_dist=R, fan_pitch=pitch, h_probes=probes)
+    plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, src_dist=R, fan_pitch=pitch, h_probes=probes,
+                    fan_gather=kernel)
     b = torch.from_numpy(pr["b"].ravel()).cuda()
     x = torch.zeros(N * N, device="cuda")
     u = torch.zeros(na * nd, device="cuda")
@@ -150,11 +154,13 @@ def run_fan_pair(N, na, nd, R, pitch, tv, lam, alpha, beta, iters, solver="ncs",
     return out
 
 
-@pytest.mark.parametrize("solver,tv", [("ncs", "aniso"), ("ncs", "iso"), ("pdhg", "iso")])
-def test_fan_iterations(solver, tv):
+@pytest.mark.parametrize("solver,tv,kernel", [("ncs", "aniso", "lines"), ("ncs", "iso", "lines"),
+                                              ("pdhg", "iso", "lines"), ("ncs", "iso", "quads"),
+                                              ("pdhg", "aniso", "quads")])
+def test_fan_iterations(solver, tv, kernel):
     N, na, nd, R = 48, 60, 70, 60.0
     pitch = synth.fan_pitch(N, R, nd, 1.05)
-    for k, errs in run_fan_pair(N, na, nd, R, pitch, tv, 0.3, 1.0, 3.0, [1, 5, 20], solver=solver):
+    for k, errs in run_fan_pair(N, na, nd, R, pitch, tv, 0.3, 1.0, 3.0, [1, 5, 20], solver=solver, kernel=kernel):
         for name, e in errs.items():
             assert e <= (2e-5 if k == 1 else 2e-4), (k, name, e)
 
@@ -182,6 +188,22 @@ def test_fan_solve_reaches_gap_checked_by_oracle():
     assert f_oracle <= fs * (1 + 1e-4 + 1e-6)
     assert f_oracle >= fs * (1 - 1e-6)
     assert rep["f"] == pytest.approx(f_oracle, rel=1e-6)
+
+
+def test_fan_kernels_agree_and_autotune_keeps_one():
+    """The two K^T kernels give the same image up to FP32 summation order, and a plan with the
+    autotuner (which times both) still matches them."""
+    N, na, nd, R = 96, 90, 130, 100.0
+    pitch = synth.fan_pitch(N, R, nd, 1.05)
+    yv = torch.from_numpy(f32(np.random.default_rng(2).uniform(-1, 1, (na, nd))).ravel().astype(np.float32)).cuda()
+    outs = []
+    for kernel, tune in (("lines", False), ("quads", False), ("auto", True)):
+        plan = fan_plan(N, na, nd, R, pitch, 0.0, None, power_max_iter=2, h_probes=1, fan_gather=kernel,
+                        autotune=tune)
+        outs.append(to_np(plan.apply_KT(yv)))
+        plan.close()
+    assert rel_l2(outs[0], outs[1]) <= 2e-6
+    assert min(rel_l2(outs[2], outs[0]), rel_l2(outs[2], outs[1])) <= 2e-6
 
 
 def test_fan_fbp_is_unsupported():
