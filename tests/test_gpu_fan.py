@@ -213,3 +213,34 @@ def test_fan_fbp_is_unsupported():
     with pytest.raises(ncs.NCSError):
         plan.fbp(torch.zeros(na * nd, device="cuda"))
     plan.close()
+
+
+def test_fan_and_parallel_plans_in_one_batch_equal_single_solves():
+    """Fan-beam plans (both K^T kernels) and a parallel-beam plan solved together by
+    ncs_batch_solve give, bit for bit, the iterates of each plan solved alone."""
+    import paper_1810_13100_gb300 as ncs
+    specs = [(48, 60, 70, 60.0, "lines"), (64, 120, 96, 128.0, "quads"), (96, 90, 130, 100.0, "lines")]
+    plans, bs = [], []
+    for k, (N, na, nd, R, kern) in enumerate(specs):
+        pitch = synth.fan_pitch(N, R, nd, 1.05)
+        g = oop.FanGeometry(N, na, nd, R, pitch)
+        pr = synth.ct_problem(10 + k, N, na, nd, 8, 0.01, lambda x, g=g: oop.K(x, g))
+        plans.append(ncs.Plan(N, na, nd, 0.05, 0.01, tv="iso", src_dist=R, fan_pitch=pitch, h_probes=8,
+                              fan_gather=kern))
+        bs.append(torch.from_numpy(pr["b"].ravel()).cuda())
+    pr = synth.ct_problem(13, 64, 90, 92, 8, 0.01, lambda x: oop.K(x, oop.Geometry(64, 90, 92)))
+    plans.append(ncs.Plan(64, 90, 92, 0.05, 0.01, tv="aniso"))
+    bs.append(torch.from_numpy(pr["b"].ravel()).cuda())
+    xs = [torch.zeros(p.n, device="cuda") for p in plans]
+    batch = ncs.Batch(plans)
+    code, reps = batch.solve(bs, xs, tol=0.0, max_iter=25, f_stars=[-1e300] * len(plans))
+    assert code == 1 and all(r["iters"] == 25 for r in reps)
+    for p, b, xb in zip(plans, bs, xs):
+        x1 = torch.zeros(p.n, device="cuda")
+        rep = p.solve(b, x1, tol=0.0, max_iter=25, f_star=-1e300)
+        torch.cuda.synchronize()
+        assert rep["iters"] == 25
+        assert torch.equal(x1, xb)
+    batch.close()
+    for p in plans:
+        p.close()
