@@ -244,3 +244,35 @@ def test_fan_and_parallel_plans_in_one_batch_equal_single_solves():
     batch.close()
     for p in plans:
         p.close()
+
+
+@pytest.mark.parametrize("kernel", ["lines", "quads"])
+def test_fan_bf16_iterations_against_oracle(kernel):
+    """BF16 storage of the duals and the projector's images on a fan plan (both K^T kernels):
+    x against the oracle within the bfloat16 bounds of tests/test_gpu_bf16.py (4e-3 after one
+    iteration, 2e-2 after 20)."""
+    import paper_1810_13100_gb300 as ncs
+    N, na, nd, R = 48, 60, 70, 60.0
+    pitch = synth.fan_pitch(N, R, nd, 1.05)
+    lam, alpha, beta, probes = 0.3, 1.0, 3.0, 8
+    g = ogeom(N, na, nd, R, pitch, 0.0, None)
+    pr = synth.ct_problem(2, N, na, nd, 8, 0.01, lambda x: oop.K(x, g))
+    P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv="iso")
+    plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv="iso", src_dist=R, fan_pitch=pitch, h_probes=probes,
+                    precision="bf16", fan_gather=kernel)
+    mus, _ = osv.a3_scaled_mu(P, oracle_fan_mu(g, alpha, beta, probes))
+    Minv = osv.circulant_Minv(mus)
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(N * N, device="cuda")
+    u = torch.zeros(na * nd, device="cuda", dtype=torch.bfloat16)
+    v = torch.zeros(2 * N * N, device="cuda", dtype=torch.bfloat16)
+    st, done = osv.zero_state(P), 0
+    for k, tol in ((1, 4e-3), (20, 2e-2)):
+        plan.step(x, u, v, None, b, None, n_iter=k - done)
+        for _ in range(k - done):
+            st = osv.ncs_step(P, st, Minv)
+        done = k
+        torch.cuda.synchronize()
+        assert rel_l2(to_np(x), st.x) <= tol, (k, "x")
+        assert rel_l2(to_np(u.float()), st.u) <= tol, (k, "u")
+    plan.close()
