@@ -47,7 +47,7 @@ METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % 
 # (profiles/ncu_k_gather_k_fwd_ct512.md); set to None when a kernel changes.
 NCU_TRAFFIC = {"joseph_gather": None, "joseph_fwd": 8508672.0}
 # warp instructions executed per launch (smsp__inst_executed.sum, same capture)
-NCU_WARP_INSTR = {"joseph_gather": 301766912.0, "joseph_fwd": 128230021.0}
+NCU_WARP_INSTR = {"joseph_gather": None, "joseph_fwd": 128230021.0}
 
 
 def load_peaks():
@@ -678,6 +678,7 @@ def run_pet(args, ws, rank, local):
 
 FAN_NCS = dict(alpha=0.01, beta=0.01, h_probes=128)   # {1,3} x 10^p grid on this workload (seed 0)
 FAN_PDHG = dict(alpha=0.001, beta=0.001)
+FAN_ADMM = dict(alpha=0.1, beta=0.1, n_cg=10)          # the 512x512 parallel beam's ADMM point
 # per launch of the fan-beam kernels, from one ncu capture (profiles/ncu_k_gather_fan_k_fwd_fan512.md);
 # None when a kernel changes
 FAN_NCU_TRAFFIC = {"joseph_gather": 14109952.0, "joseph_fwd": 19752192.0}
@@ -793,6 +794,12 @@ def run_fan(args, ws, rank, local):
         rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=fs)
         ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
         pplan.close()
+        aplan = fan_plan(ncs, W, FAN_ADMM, h_probes=FAN_NCS["h_probes"], fan_gather=args.fan_gather)
+        xs.zero_()
+        rep = aplan.admm_solve(b, xs, tol=TTG_TOL, max_outer=ADMM_CAP, n_cg=FAN_ADMM["n_cg"], f_star=fs)
+        ttg["admm"] = dict(FAN_ADMM, outer=rep["iters"], time_ms=rep["time_ms"], gap=rep["gap"],
+                           status=rep["status"])
+        aplan.close()
     plan.close()
     if rank == 0:
         line = {"metric": "fan-beam TV-CT NCS iterations/s (512x512, 720 views x 768 channels)", "value": value,
@@ -801,7 +808,8 @@ def run_fan(args, ws, rank, local):
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "512x512 fan-beam TV-CT, 720 views on [0, 2pi), 768 equiangular channels, "
                                        "source at 1024 px, 20 ellipses, 0.5%% noise, iso TV lambda 0.005, seed %d"
-                                       % seed, "ncs": FAN_NCS, "pdhg": FAN_PDHG, "fan_gather": args.fan_gather,
+                                       % seed, "ncs": FAN_NCS, "pdhg": FAN_PDHG, "admm": FAN_ADMM,
+                           "fan_gather": args.fan_gather,
                            "l2": "flushed before every step (256 MiB write, untimed)"},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches, "peaks": peak_kind,
                 "time_to_gap": ttg, "clocks": clk.summary()}

@@ -1742,6 +1742,7 @@ int ncs_plan_nnz(ncs_plan* p, double* nnz)
         double cnt = 0.0;
         for (size_t r = 0; r < p->h_rays.size(); ++r) {
             const FanRay& q = p->h_rays[r];
+            if (p->h_rayw[r] == 0.0f) continue;          // a ray that passes no pixel
             for (int j = 0; j < N; ++j) {
                 const float jf = (float)j;
                 const float H = std::fma(q.x, jf, q.z);
@@ -1751,7 +1752,6 @@ int ncs_plan_nnz(ncs_plan* p, double* nnz)
                 const float fl = std::floor(fr);
                 const float w = fr - fl;
                 const int i0 = (int)(Hi + fl);
-                if (p->h_rayw[r] == 0.0f) break;
                 if (i0 >= 0 && i0 < N && 1.0f - w != 0.0f) cnt += 1.0;
                 if (i0 + 1 >= 0 && i0 + 1 < N && w != 0.0f) cnt += 1.0;
             }

@@ -179,54 +179,77 @@ k_fwd(FwdArgs g)
 constexpr int GT = 32;     // gather tile side (pixels)
 constexpr int GW = 8;      // warps per gather block
 
-// Per-line quantities of one angle for a warp: first ray tl, the exact
-// B_hi q + C_hi, the remainder B_lo q + C_lo and the line index q.
-struct LineEntry {
-    int tl;
-    float Hq, Lq;
-    int line;
+// Per line pair (2p, 2p + 1) of a tile for one angle: the exact B_hi q + C_hi and the
+// remainder B_lo q + C_lo of both lines, the first ray that can reach either line, and
+// the first line's index.
+struct PairEntry {
+    float4 h;      // Hq, Lq of line 2p; Hq, Lq of line 2p + 1
+    int tl, line, pad0, pad1;
 };
 
 // All (ray, line) pairs of one angle that reach a 32 x 32 tile, accumulated by
 // one warp into its private shared-memory tile A.  ROW: the angle steps over
 // image rows (line = row, window along columns); otherwise over columns.  o0 is
-// the tile's first index along the interpolation axis, l0 its first line.
-// Lanes take consecutive rays of a line, so the loads of u coalesce; a pixel
-// receives at most one "right" weight (1 - w) and one "left" weight w per
-// angle, so the two phases never write one address twice.  CHECK: test the
-// line and ray ranges per pair (edge tiles and rays beyond the detector).
+// the tile's first index along the interpolation axis.  Each lane takes one ray
+// on two adjacent lines (one load of u and W u serve both weights); lanes take
+// consecutive rays of a line pair, so the loads of u coalesce.  A pixel receives at
+// most one "right" weight (1 - w) and one "left" weight w per angle (rays of one
+// angle cross a line at least a pixel apart), and the two lines of a pair are
+// different rows of A, so the two phases never write one address twice.  CHECK:
+// test the line and ray ranges (edge tiles and rays beyond the detector).
 template <bool ROW, bool CHECK, bool SBF>
 __device__ __forceinline__ void gather_pairs(const AngleParam& p, const void* ua, int n_det, int N,
-                                             int o0, int RPL, int lane, const LineEntry* tab, float (*A)[GT + 1])
+                                             int o0, int RPP, int lane, const PairEntry* tab, float (*A)[GT + 1])
 {
-    int lo = lane / RPL, r = lane - lo * RPL;
-    for (int it = 0; it < RPL; ++it) {
-        const LineEntry e = tab[lo];
-        const int t = e.tl + r;
-        float vR = 0.0f, vL = 0.0f;
-        int kk = -2;
-        if (!CHECK || (e.line < N && (unsigned)t < (unsigned)n_det)) {
-            const float tf = (float)t;
-            float k0f;
-            const float w = split_weight(fmaf(p.Ahi, tf, e.Hq), fmaf(p.Alo, tf, e.Lq), k0f);
-            kk = (int)k0f - o0;
-            const float Wu = p.W * St<SBF>::ld(ua, t);
-            vR = fmaf(-w, Wu, Wu);
-            vL = w * Wu;
+    constexpr int NP = GT / 2;
+    int lo = lane / RPP, r = lane - lo * RPP;
+    const int steps = (NP * RPP + 31) / 32;
+    for (int it = 0; it < steps; ++it) {
+        float vR0 = 0.0f, vL0 = 0.0f, vR1 = 0.0f, vL1 = 0.0f;
+        int k0 = -2, k1 = -2;
+        if (lo < NP) {
+            const PairEntry e = tab[lo];
+            const int t = e.tl + r;
+            if (!CHECK || (unsigned)t < (unsigned)n_det) {
+                const float tf = (float)t;
+                const float Wu = p.W * St<SBF>::ld(ua, t);
+                float kf;
+                if (!CHECK || e.line < N) {
+                    const float w = split_weight(fmaf(p.Ahi, tf, e.h.x), fmaf(p.Alo, tf, e.h.y), kf);
+                    k0 = (int)kf - o0;
+                    vR0 = fmaf(-w, Wu, Wu);
+                    vL0 = w * Wu;
+                }
+                if (!CHECK || e.line + 1 < N) {
+                    const float w = split_weight(fmaf(p.Ahi, tf, e.h.z), fmaf(p.Alo, tf, e.h.w), kf);
+                    k1 = (int)kf - o0;
+                    vR1 = fmaf(-w, Wu, Wu);
+                    vL1 = w * Wu;
+                }
+            }
         }
-        if ((unsigned)kk < (unsigned)GT) {
-            if (ROW) A[lo][kk] += vR;
-            else A[kk][lo] += vR;
+        const int q0 = 2 * lo, q1 = q0 + 1;
+        if ((unsigned)k0 < (unsigned)GT) {
+            if (ROW) A[q0][k0] += vR0;
+            else A[k0][q0] += vR0;
+        }
+        if ((unsigned)k1 < (unsigned)GT) {
+            if (ROW) A[q1][k1] += vR1;
+            else A[k1][q1] += vR1;
         }
         __syncwarp();
-        if ((unsigned)(kk + 1) < (unsigned)GT) {
-            if (ROW) A[lo][kk + 1] += vL;
-            else A[kk + 1][lo] += vL;
+        if ((unsigned)(k0 + 1) < (unsigned)GT) {
+            if (ROW) A[q0][k0 + 1] += vL0;
+            else A[k0 + 1][q0] += vL0;
+        }
+        if ((unsigned)(k1 + 1) < (unsigned)GT) {
+            if (ROW) A[q1][k1 + 1] += vL1;
+            else A[k1 + 1][q1] += vL1;
         }
         __syncwarp();
         r += 32;
-        while (r >= RPL) {
-            r -= RPL;
+        while (r >= RPP) {
+            r -= RPP;
             ++lo;
         }
     }
@@ -234,32 +257,37 @@ __device__ __forceinline__ void gather_pairs(const AngleParam& p, const void* ua
 
 template <bool ROW, bool SBF>
 __device__ __forceinline__ void gather_angle(const AngleParam& p, const void* ua, int n_det, int N,
-                                             int o0, int l0, int lane, LineEntry* tab, float (*A)[GT + 1])
+                                             int o0, int l0, int lane, PairEntry* tab, float (*A)[GT + 1])
 {
+    constexpr int NP = GT / 2;
     const float lf0 = (float)l0;
     const float base0 = fmaf(p.Bhi, lf0, p.Chi) + fmaf(p.Blo, lf0, p.Clo);      // ~ B l0 + C
     const float ta = ((float)o0 - 1.0f - base0) * p.invA;
     const float tb = ((float)o0 + (float)GT - base0) * p.invA;
     const float T0 = fminf(ta, tb) - 1e-3f;                                      // first ray of line l0
-    const float dT = -(p.Bhi + p.Blo) * p.invA;                                  // shift per line
+    const float dT = -(p.Bhi + p.Blo) * p.invA;                                  // shift per line, |dT| <= 1
     const int RPL = (int)ceilf((float)(GT + 1) * fabsf(p.invA) + 2e-3f) + 1;     // rays per line
-    {
-        const int line = l0 + lane;
-        const float lf = (float)line;
-        LineEntry e;
-        e.tl = (int)floorf(fmaf((float)lane, dT, T0));
-        e.Hq = fmaf(p.Bhi, lf, p.Chi);                                           // exact
-        e.Lq = fmaf(p.Blo, lf, p.Clo);
-        e.line = line;
+    const int RPP = RPL + 1;              // rays per line pair: the lines' first rays differ by <= 1
+    if (lane < NP) {
+        const int la = 2 * lane;
+        const int tla = (int)floorf(fmaf((float)la, dT, T0));
+        const int tlb = (int)floorf(fmaf((float)(la + 1), dT, T0));
+        const float lfa = (float)(l0 + la), lfb = lfa + 1.0f;
+        PairEntry e;
+        e.h = make_float4(fmaf(p.Bhi, lfa, p.Chi), fmaf(p.Blo, lfa, p.Clo),       // Hq exact
+                          fmaf(p.Bhi, lfb, p.Chi), fmaf(p.Blo, lfb, p.Clo));
+        e.tl = min(tla, tlb);
+        e.line = l0 + la;
+        e.pad0 = e.pad1 = 0;
         tab[lane] = e;
     }
     __syncwarp();
     // interior: every line inside the image and every ray on the detector
-    const int t_first = min(tab[0].tl, tab[GT - 1].tl);
-    const int t_last = max(tab[0].tl, tab[GT - 1].tl) + RPL - 1;
+    const int t_first = min(tab[0].tl, tab[NP - 1].tl);
+    const int t_last = max(tab[0].tl, tab[NP - 1].tl) + RPP - 1;
     const bool inside = (l0 + GT <= N) && t_first >= 0 && t_last < n_det;
-    if (inside) gather_pairs<ROW, false, SBF>(p, ua, n_det, N, o0, RPL, lane, tab, A);
-    else gather_pairs<ROW, true, SBF>(p, ua, n_det, N, o0, RPL, lane, tab, A);
+    if (inside) gather_pairs<ROW, false, SBF>(p, ua, n_det, N, o0, RPP, lane, tab, A);
+    else gather_pairs<ROW, true, SBF>(p, ua, n_det, N, o0, RPP, lane, tab, A);
     __syncwarp();
 }
 
@@ -295,7 +323,7 @@ __global__ void __launch_bounds__(GT * GW)
 k_gather(GatherArgs g)
 {
     __shared__ float acc[GW][GT][GT + 1];
-    __shared__ LineEntry lines[GW][GT];
+    __shared__ PairEntry lines[GW][GT / 2];
     __shared__ int s_last;
     const int N = g.N;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;

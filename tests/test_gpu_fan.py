@@ -276,3 +276,27 @@ def test_fan_bf16_iterations_against_oracle(kernel):
         assert rel_l2(to_np(x), st.x) <= tol, (k, "x")
         assert rel_l2(to_np(u.float()), st.u) <= tol, (k, "u")
     plan.close()
+
+
+def test_fan_admm_iterates_match_oracle():
+    """The ADMM comparator (admm_solve) on a fan plan against the oracle's admm_pcg with the
+    same probe-estimated M (tolerances of tests/test_gpu_admm.py: 2e-4 after one outer step,
+    2e-3 after five)."""
+    import paper_1810_13100_gb300 as ncs
+    N, na, nd, R = 48, 60, 70, 60.0
+    pitch = synth.fan_pitch(N, R, nd, 1.05)
+    lam, a, n_cg, probes = 0.01, 0.1, 3, 8
+    g = ogeom(N, na, nd, R, pitch, 0.0, None)
+    pr = synth.ct_problem(0, N, na, nd, 8, 0.01, lambda x: oop.K(x, g))
+    P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=a, beta=a, tv="iso")
+    mus, _ = osv.a3_scaled_mu(P, oracle_fan_mu(g, a, a, probes))
+    xs = osv.admm_pcg(P, 5, n_cg, osv.circulant_Minv(mus))
+    plan = ncs.Plan(N, na, nd, lam, a, beta=a, tv="iso", src_dist=R, fan_pitch=pitch, h_probes=probes)
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(N * N, device="cuda")
+    for k, tol in ((1, 2e-4), (5, 2e-3)):
+        x.zero_()
+        rep = plan.admm_solve(b, x, tol=0.0, max_outer=k, n_cg=n_cg)
+        assert rep["iters"] == k
+        assert rel_l2(to_np(x), xs[k - 1]) <= tol, k
+    plan.close()
