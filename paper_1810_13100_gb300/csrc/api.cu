@@ -737,6 +737,7 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
 int build_common(ncs_plan* p)
 {
     const int N = p->N, na = p->na, nd = p->nd;
+    CK(fft_prepare(N));
     // twiddles exp(-2 pi i m / N) in FP64, rounded once
     std::vector<float2> tw(N);
     for (int m = 0; m < N; ++m) {

@@ -268,6 +268,19 @@ int fft_threads(int N)
 
 }  // namespace
 
+cudaError_t fft_prepare(int N)
+{
+    // each FFT block stages two length-N complex sequences: above 48 KB (N > 3072) the
+    // kernels must opt in to the larger dynamic shared memory of the current device
+    const int smem = 2 * N * (int)sizeof(float2);
+    if (smem <= 48 * 1024) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_ratio, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
+}
+
 cudaError_t launch_rows_fwd(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N,
                             cudaStream_t st)
 {

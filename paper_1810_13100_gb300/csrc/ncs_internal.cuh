@@ -213,6 +213,9 @@ size_t fan_gather_tiles(int N);              // blocks (arrival counters) of the
 cudaError_t launch_td(int mode, const TdArgs& a, cudaStream_t st);
 int td_num_blocks(int N);
 
+// once per plan (per device), before any launch below or graph capture: opt the FFT kernels in
+// to more than 48 KB of dynamic shared memory when N needs it
+cudaError_t fft_prepare(int N);
 cudaError_t launch_rows_fwd(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N,
                             cudaStream_t st);
 cudaError_t launch_cols_ratio(const float2* Sw, float2* Sv, double* num, double* den, const float2* tw,

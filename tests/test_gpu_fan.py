@@ -92,6 +92,24 @@ def test_fan_gpu_pair_is_exact_transpose(N, na, nd, R, pitch, off, views, kernel
     plan.close()
 
 
+@pytest.mark.parametrize("kernel", ["lines", "quads"])
+@pytest.mark.parametrize("N,na,nd,R,pitch", [(4096, 6, 4100, 8192.0, synth.fan_pitch(4096, 8192.0, 4100, 1.02)),
+                                             (16, 1, 1, 20.0, 0.05), (12, 3, 2, 15.0, 0.3)])
+def test_fan_extreme_sizes_parity(N, na, nd, R, pitch, kernel):
+    """The largest image side, a single ray, and a fan of two channels wider than the image."""
+    rng = np.random.default_rng(N + 5 * na)
+    x = f32(rng.uniform(-1, 1, (N, N)))
+    yv = f32(rng.uniform(-1, 1, (na, nd)))
+    g = ogeom(N, na, nd, R, pitch, 0.0, None)
+    plan = fan_plan(N, na, nd, R, pitch, 0.0, None, power_max_iter=2, h_probes=1, fan_gather=kernel)
+    y = plan.apply_K(torch.from_numpy(x.ravel().astype(np.float32)).cuda())
+    ref = oop.K(x, g)
+    assert rel_l2(to_np(y), ref) <= TOL
+    xt = plan.apply_KT(torch.from_numpy(yv.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(xt), oop.KT(yv, g)) <= TOL
+    plan.close()
+
+
 def oracle_fan_mu(g, alpha, beta, probes, gamma=0.0):
     """The oracle's eigenvalues of M for a fan plan before the (A3) rescale: eq. (H-fan) in
     least-squares form over the plan's float32 SplitMix64 probes, DC ||K 1||^2 / ||1||^2."""

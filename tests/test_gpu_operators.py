@@ -83,6 +83,26 @@ def test_gpu_pair_is_exact_transpose(N, na, nd, sp, off):
         assert abs(lhs - rhs) <= 2e-6 * scale
 
 
+@pytest.mark.parametrize("N,na,nd", [(4096, 6, 4100), (16, 1, 1), (12, 3, 2)])
+def test_extreme_sizes_parity(N, na, nd):
+    """The largest image side a plan accepts (4096: 128 x 128 gather tiles, a 4096-point FFT
+    in the plan's setup), a single ray, and fewer bins than the image is wide."""
+    rng = np.random.default_rng(N + 3 * na)
+    x = f32(rng.uniform(-1, 1, (N, N)))
+    yv = f32(rng.uniform(-1, 1, (na, nd)))
+    g = oop.Geometry(N, na, nd)
+    plan = plan_for(N, na, nd, power_max_iter=2)
+    y = plan.apply_K(torch.from_numpy(x.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(y), oop.K(x, g)) <= TOL
+    xt = plan.apply_KT(torch.from_numpy(yv.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(xt), oop.KT(yv, g)) <= TOL
+    # the FFT solve at this side against the oracle's, with the plan's own eigenvalues
+    r = f32(rng.standard_normal((N, N)))
+    out = plan.apply_Minv(torch.from_numpy(r.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(out), oci.circulant_solve(r, plan.mu().reshape(N, N))) <= TOL
+    plan.close()
+
+
 def test_user_angles_with_exact_ties():
     th = [0.0, 0.3, math.pi / 4, 1.1, math.pi / 2, 2.0, 3 * math.pi / 4, 3.0, math.pi - 1e-3]
     N, nd = 48, 61
