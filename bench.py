@@ -193,9 +193,10 @@ def gpu_projector(plan, dev):
 
 # ------------------------------------------------------------------ CPU oracle leg
 
-def oracle_rate(seed, budget_s=15.0, min_iters=2):
+def oracle_rate(seed, budget_s=15.0, min_iters=2, warmup=1, max_iters=1000):
     """FP64 oracle NCS iterations per second on the host cores for a bounded
-    sample of the workload (iterations from the zero state)."""
+    sample of the workload (iterations from the zero state, after `warmup` untimed ones;
+    at least min_iters and at most max_iters timed, stopping once the budget is spent)."""
     import numpy as np
     from oracle import circulant as oci, operators as oop, solvers as osv
     import synth
@@ -208,7 +209,8 @@ def oracle_rate(seed, budget_s=15.0, min_iters=2):
     mu, _ = osv.a3_scaled_mu(P, oci.mu_table(g, P.alpha, P.beta, NCS_PARAMS["gamma"]), max_iter=3)
     Minv = osv.circulant_Minv(mu)
     st = osv.zero_state(P)
-    st = osv.ncs_step(P, st, Minv)          # warm-up (library loading, page faults)
+    for _ in range(max(1, warmup)):
+        st = osv.ncs_step(P, st, Minv)      # warm-up (library loading, page faults)
     times = []
     t_start = time.perf_counter()
     while len(times) < min_iters or time.perf_counter() - t_start < budget_s:
@@ -217,7 +219,7 @@ def oracle_rate(seed, budget_s=15.0, min_iters=2):
         if (len(times) + 1) % CHECK_EVERY == 0:
             osv.objective(P, st.x)
         times.append(time.perf_counter() - t0)
-        if len(times) >= 1000:
+        if len(times) >= max_iters:
             break
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return dict(rate=len(times) / sum(times), iters=len(times), seconds=sum(times), cores=cores,
@@ -243,14 +245,17 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return
     per_iter_budget = max(5.0, min(150.0, 0.8 * args.steps))
-    # warm-up steps (untimed), then timed steps bounded to a few minutes
-    r = oracle_rate(args.seed, budget_s=per_iter_budget, min_iters=min(args.steps, 3))
+    # warm-up steps (untimed, at most 5: the oracle has nothing to warm beyond the first), then
+    # the K timed steps, cut short only if they would run past a few minutes
+    warm = max(1, min(args.warmup, 5))
+    r = oracle_rate(args.seed, budget_s=per_iter_budget, min_iters=min(args.steps, 3), warmup=warm,
+                    max_iters=args.steps)
     times = r["per_iter"][: args.steps]
     total = sum(times)
     value = len(times) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": args.gpus,
-        "steps": len(times), "warmup": 1, "ms_per_step": 1000.0 * total / len(times),
+        "steps": len(times), "warmup": warm, "ms_per_step": 1000.0 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "512x512 TV-CT, 720 angles x 730 bins, iso TV lambda 0.005, seed %d" % args.seed,
                    "l2": "n/a (host)"},
