@@ -794,7 +794,8 @@ def run_fan(args, ws, rank, local):
         xs = torch.zeros(n, device=dev)
         rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=4000, f_star=fs)
         ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-        pplan = fan_plan(ncs, W, FAN_PDHG, h_probes=1, power_max_iter=2, fan_gather=args.fan_gather)
+        # PDHG's step comes from lambda_max(A^T A) by the plan's full power iteration
+        pplan = fan_plan(ncs, W, FAN_PDHG, h_probes=1, fan_gather=args.fan_gather)
         xs.zero_()
         rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=fs)
         ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
