@@ -100,3 +100,27 @@ def test_transpose_is_adjoint():
     x, y = rng.random((N, N)), rng.random((na, nd))
     lhs, rhs = np.sum(oop.K(x, g) * y), np.sum(x * oop.KT(y, g))
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_fan_ncs_fixed_point_is_dense_admm_minimiser():
+    """NCS (eq. (NCS)) with the fan-beam K and M from eq. (H-fan) (least-squares form over
+    probe images, rescaled for (A3)) converges to the minimiser that the textbook ADMM of the
+    Appendix reaches with a dense (A^T A)^+; at the limit u* = K x* - b and A^T u* = 0."""
+    from oracle import circulant as ci
+    from oracle import solvers as so
+    import synth
+    N, na, nd, R = 16, 24, 28, 20.0
+    g = oop.FanGeometry(N, na, nd, R, cover_pitch(N, R, nd))
+    b = synth.ct_problem(0, N, na, nd, 4, 0.01, lambda x: oop.K(x, g))["b"].astype(np.float64)
+    P = so.Problem(g, b, lam=0.5, alpha=1.0, beta=3.0, tv="aniso")
+    vs = [so.splitmix64_uniform(1 + q, N * N).reshape(N, N) for q in range(8)]
+    h = np.maximum(ci.probe_ls(lambda v: oop.KT(oop.K(v, g), g), N, vs), 0.0)
+    h[0, 0] = ci.h_dc_default(g)
+    mus, rho = so.a3_scaled_mu(P, P.alpha * h + (P.beta ** 2 / P.alpha) * ci.H_D(N))
+    st = so.run(P, so.zero_state(P), 4000, so.circulant_Minv(mus))
+    Pa = so.Problem(g, b, lam=0.5, alpha=10.0, beta=10.0, tv="aniso")
+    xstar = so.admm_textbook(Pa, 2500, so.dense_A(Pa))[-1]
+    assert np.linalg.norm(st.x - xstar) <= 1e-8 * np.linalg.norm(xstar)
+    assert np.linalg.norm(st.u - (oop.K(st.x, g) - b)) <= 1e-8 * np.linalg.norm(st.u)
+    r = so.AT_apply(P, st.u, st.vh, st.vv)
+    assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(oop.KT(st.u, g))
