@@ -283,8 +283,9 @@ int ncs_objective(ncs_plan* plan, const float* x, const float* b, const float* b
  * host array mu_host.  Synchronises. */
 int ncs_get_mu(ncs_plan* plan, double* mu_host);
 
-/* Tuning of the plan: the gather's angle slices per 32 x 32 tile and the FFT radix
- * order (fft_radices: host array of at least 12 ints; any pointer may be NULL). */
+/* Tuning of the plan: the gather's angle slices per tile (32 x 32 pixels; for a fan plan the
+ * view slices of its K^T kernel, whose tiles are 32 x 32 or, with pixel quads, 32 x 16) and
+ * the FFT radix order (fft_radices: host array of at least 12 ints; any pointer may be NULL). */
 int ncs_plan_info(const ncs_plan* plan, int* gather_parts, int* fft_radices, int* n_radices);
 
 /* Plan sizes: N, n_angles, n_det. */
