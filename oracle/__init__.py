@@ -16,7 +16,9 @@ Parts (each function cites the passage it follows):
   prox       - proximal maps of the conjugates (Sec. 2, Sec. 4)
   solvers    - NCS, PDHG, textbook dense ADMM, objective, seminorm D, power
                iterations for (A3)
+  cone       - 3-D cone beam on a circular orbit: geometry, Joseph K / K^T (in the C
+               file), 3-D D, circulant M and NCS, dense ADMM (Sec. 4)
 """
-from . import circulant, operators, prox, solvers  # noqa: F401
+from . import circulant, cone, operators, prox, solvers  # noqa: F401
 from .operators import Geometry, K, KT, D, DT  # noqa: F401
 from .solvers import Problem, State  # noqa: F401

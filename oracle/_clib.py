@@ -1,4 +1,5 @@
-"""Loader for the oracle's C part (joseph_fp64.c), compiled with gcc on demand.
+"""Loader for the oracle's C part (joseph_fp64.c: the parallel-, fan- and cone-beam Joseph
+projectors), compiled with gcc on demand.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 """
@@ -47,5 +48,9 @@ def lib() -> ctypes.CDLL:
                 f = getattr(L, name)
                 f.restype = None
                 f.argtypes = [ctypes.c_int, ctypes.c_long, dp, dp, dp, ip, dp, dp]
+            for name in ("oracle_cone_forward", "oracle_cone_transpose"):
+                f = getattr(L, name)
+                f.restype = None
+                f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, dp, dp, dp, dp, dp, dp, ip, dp, dp]
             _lib = L
     return _lib

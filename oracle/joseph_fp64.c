@@ -212,3 +212,111 @@ void oracle_joseph_transpose_rays(int N, long n_rays, const double* cos_r, const
         }
     }
 }
+
+/*
+ * Cone beam on a circular orbit (Sec. 4, "fan beam and cone beam geometry": the 3-D
+ * divergent-beam transform).  Volume x[k][j][i], Nz slices of N x N, voxel centre
+ * (u, v, w) = (i - cN, cN - j, k - cZ).  Ray r is given by its in-plane line
+ * u cos_r + v sin_r = s_r (a fan-beam ray), its source (su_r, sv_r) in the plane w = 0, and
+ * its slope sig_r: along the in-plane direction d = (sin_r, -cos_r), which points from the
+ * source into the volume, the ray rises by sig_r per unit of in-plane distance.  It is stepped
+ * over the in-plane lines like the in-plane ray (rows when row_branch, else columns).  On each
+ * line the in-plane crossing gives the fractional index along the other in-plane axis, and the
+ * in-plane distance h = (P - S) . d of the crossing point P gives the fractional slice index
+ * sig_r h + cZ; the volume is interpolated bilinearly in those two indices and the sum is
+ * scaled by the path length per step, sqrt(1 + sig_r^2) / |cos| (or / |sin|).  Voxels outside
+ * the volume are zero.  The transpose is the literal scatter, threads owning one row (row
+ * branch) or one column (column branch) of every slice.
+ */
+static double vox(const double* x, int N, int Nz, int k, int j, int i)
+{
+    if (k < 0 || k >= Nz || j < 0 || j >= N || i < 0 || i >= N) return 0.0;
+    return x[((long)k * N + j) * N + i];
+}
+
+static void add_vox(double* x, int N, int Nz, int k, int j, int i, double val)
+{
+    if (k < 0 || k >= Nz || j < 0 || j >= N || i < 0 || i >= N) return;
+    x[((long)k * N + j) * N + i] += val;
+}
+
+/* Crossing of cone ray r with in-plane line q: index f along the interpolation axis, slice
+ * index g. */
+static void cone_cross(int N, int Nz, int row, double c, double s, double st, double su, double sv,
+                       double sg, int q, double* f, double* g)
+{
+    double cN = 0.5 * (N - 1), cZ = 0.5 * (Nz - 1), u, v;
+    if (row) {
+        v = cN - q;
+        u = (st - v * s) / c;
+        *f = u + cN;
+    } else {
+        u = q - cN;
+        v = (st - u * c) / s;
+        *f = cN - v;
+    }
+    *g = sg * ((u - su) * s - (v - sv) * c) + cZ;
+}
+
+void oracle_cone_forward(int N, int Nz, long n_rays, const double* cos_r, const double* sin_r, const double* s_r,
+                         const double* su_r, const double* sv_r, const double* sig_r, const int* row_branch,
+                         const double* x, double* y)
+{
+#pragma omp parallel for schedule(dynamic, 64) if ((long)N * n_rays > OMP_MIN_WORK)
+    for (long r = 0; r < n_rays; ++r) {
+        double c = cos_r[r], s = sin_r[r], acc = 0.0;
+        int row = row_branch[r];
+        for (int q = 0; q < N; ++q) {
+            double f, g;
+            cone_cross(N, Nz, row, c, s, s_r[r], su_r[r], sv_r[r], sig_r[r], q, &f, &g);
+            double f0 = floor(f), g0 = floor(g);
+            int p0 = (int)f0, k0 = (int)g0;
+            double w = f - f0, wz = g - g0;
+            double a0, a1;
+            if (row) {
+                a0 = (1.0 - w) * vox(x, N, Nz, k0, q, p0) + w * vox(x, N, Nz, k0, q, p0 + 1);
+                a1 = (1.0 - w) * vox(x, N, Nz, k0 + 1, q, p0) + w * vox(x, N, Nz, k0 + 1, q, p0 + 1);
+            } else {
+                a0 = (1.0 - w) * vox(x, N, Nz, k0, p0, q) + w * vox(x, N, Nz, k0, p0 + 1, q);
+                a1 = (1.0 - w) * vox(x, N, Nz, k0 + 1, p0, q) + w * vox(x, N, Nz, k0 + 1, p0 + 1, q);
+            }
+            acc += (1.0 - wz) * a0 + wz * a1;
+        }
+        y[r] = acc * sqrt(1.0 + sig_r[r] * sig_r[r]) / fabs(row ? c : s);
+    }
+}
+
+void oracle_cone_transpose(int N, int Nz, long n_rays, const double* cos_r, const double* sin_r, const double* s_r,
+                           const double* su_r, const double* sv_r, const double* sig_r, const int* row_branch,
+                           const double* y, double* x)
+{
+    memset(x, 0, sizeof(double) * (size_t)N * N * Nz);
+    for (int pass = 1; pass >= 0; --pass) {        /* rays stepped over rows, then over columns */
+#pragma omp parallel for schedule(static) if ((long)N * n_rays > OMP_MIN_WORK)
+        for (int q = 0; q < N; ++q) {
+            for (long r = 0; r < n_rays; ++r) {
+                if (row_branch[r] != pass) continue;
+                double c = cos_r[r], s = sin_r[r];
+                double val = y[r] * sqrt(1.0 + sig_r[r] * sig_r[r]) / fabs(pass ? c : s);
+                double f, g;
+                cone_cross(N, Nz, pass, c, s, s_r[r], su_r[r], sv_r[r], sig_r[r], q, &f, &g);
+                double f0 = floor(f), g0 = floor(g);
+                int p0 = (int)f0, k0 = (int)g0;
+                double w = f - f0, wz = g - g0;
+                double v00 = (1.0 - wz) * (1.0 - w) * val, v01 = (1.0 - wz) * w * val;
+                double v10 = wz * (1.0 - w) * val, v11 = wz * w * val;
+                if (pass) {
+                    add_vox(x, N, Nz, k0, q, p0, v00);
+                    add_vox(x, N, Nz, k0, q, p0 + 1, v01);
+                    add_vox(x, N, Nz, k0 + 1, q, p0, v10);
+                    add_vox(x, N, Nz, k0 + 1, q, p0 + 1, v11);
+                } else {
+                    add_vox(x, N, Nz, k0, p0, q, v00);
+                    add_vox(x, N, Nz, k0, p0 + 1, q, v01);
+                    add_vox(x, N, Nz, k0 + 1, p0, q, v10);
+                    add_vox(x, N, Nz, k0 + 1, p0 + 1, q, v11);
+                }
+            }
+        }
+    }
+}
