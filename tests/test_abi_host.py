@@ -111,3 +111,15 @@ def test_fan_plan_create_rejects_bad_geometry_before_touching_cuda(lib):
     assert _create_fan(lib, 64, nv=0)[0] == -1
     assert _create_fan(lib, 17)[0] == -2
     assert lib.ncs_plan_create_fan(None, 64, 64, 0.1, 1.0, None, None) == -1
+
+
+def test_fan_plan_rejects_unknown_gather_kernel(lib):
+    from paper_1810_13100_gb300 import binding
+    g = binding.FanGeometry()
+    g.n_views, g.n_det, g.src_dist, g.pitch, g.offset = 8, 10, 128.0, 0.01, 0.0
+    for bad in (-1, 3):
+        o = binding.default_options()
+        o.fan_gather = bad
+        h = ctypes.c_void_p()
+        assert lib.ncs_plan_create_fan(ctypes.byref(g), 64, 64, 0.1, 1.0, ctypes.byref(o), ctypes.byref(h)) == -1
+        assert not h.value
