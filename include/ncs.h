@@ -213,6 +213,47 @@ int admm_solve(ncs_plan* plan, const float* b, float* x, double tol, int max_out
  * Synchronises. */
 int ncs_power_bound(ncs_plan* plan, double* lambda_max_AtA, double* rho_M);
 
+/* ---- Cone beam (3-D) operators ---- */
+
+/* Cone beam on a circular orbit (Sec. 4, "fan beam and cone beam geometry": the 3-D
+ * divergent-beam transform).  Volume x[k*N*N + j*N + i]: Nz slices of N x N, voxel centre
+ * (i - (N-1)/2, (N-1)/2 - j, k - (Nz-1)/2).  Sinogram y[(a*n_rows + r)*n_det + t].  The source
+ * of view a is that of the fan beam (ncs_fan_geometry) in the plane w = 0; channel t has the fan
+ * beam's fan angle, and detector row r (a cylindrical detector) holds the rays whose slope
+ * sigma_r = (r - (n_rows-1)/2) * row_pitch + row_offset is the rise in w per unit of in-plane
+ * distance from the source.  K is Joseph's method along the ray's in-plane trace (rows or
+ * columns, the fan beam's rule), bilinear in (in-plane position, slice), weighted by the path
+ * length per step sqrt(1 + sigma^2)/|cos| (or /|sin|); voxels outside the volume are zero. */
+typedef struct {
+    int n_views;           /* source positions, >= 1 */
+    int n_rows;            /* detector rows, >= 1 */
+    int n_det;             /* channels per row, >= 1 */
+    double src_dist;       /* R in voxel units, >= (N-1)/sqrt(2) + 3 */
+    double pitch;          /* fan angle between adjacent channels, radians, > 0 */
+    double offset;         /* fan angle of the channel centre, radians */
+    double row_pitch;      /* slope step between adjacent rows, > 0 */
+    double row_offset;     /* slope of the row centre; every |sigma_r| < 1/sqrt(2) */
+    const double* views;   /* host array of n_views source angles, or NULL for 2 pi a / n_views */
+} ncs_cone_geometry;
+
+typedef struct ncs_cone ncs_cone;   /* opaque; owns the projector's device tables */
+
+/* Build the cone-beam operator pair for an N x N x Nz volume (N even, 8 <= N <= 4096,
+ * 1 <= Nz <= 4096) whose calls run on cuda_stream (NULL: the default stream).  Synchronises.
+ * Errors: NCS_ERR_BADARG (sizes, non-positive pitches, a slope of magnitude >= 1/sqrt(2), a
+ * source inside the image's circle plus 3 pixels, non-finite values), NCS_ERR_UNSUPPORTED, NCS_ERR_NOMEM,
+ * NCS_ERR_CUDA. */
+int ncs_cone_create(const ncs_cone_geometry* geom, int N, int Nz, void* cuda_stream, ncs_cone** out);
+
+/* Release it (NULL is a no-op); waits for its stream. */
+void ncs_cone_destroy(ncs_cone* cone);
+
+/* y = K x (device pointers, float32; x: N*N*Nz, y: n_views*n_rows*n_det).  Asynchronous. */
+int ncs_cone_apply_K(ncs_cone* cone, const float* x, float* y);
+
+/* x = K^T y, the exact transpose (gather, no atomics; deterministic).  Asynchronous. */
+int ncs_cone_apply_KT(ncs_cone* cone, const float* y, float* x);
+
 /* ---- Batches of independent slices ---- */
 
 typedef struct ncs_batch ncs_batch;   /* opaque; a set of plans solved together */

@@ -8,6 +8,7 @@ binding.  PyTorch supplies device memory and streams only.
 from .binding import (  # noqa: F401
     Plan,
     Batch,
+    Cone,
     UNet,
     NCSError,
     load_library,

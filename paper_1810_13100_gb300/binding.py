@@ -42,6 +42,13 @@ class FanGeometry(ctypes.Structure):
                 ("views", ctypes.POINTER(ctypes.c_double))]
 
 
+class ConeGeometry(ctypes.Structure):
+    _fields_ = [("n_views", ctypes.c_int), ("n_rows", ctypes.c_int), ("n_det", ctypes.c_int),
+                ("src_dist", ctypes.c_double), ("pitch", ctypes.c_double), ("offset", ctypes.c_double),
+                ("row_pitch", ctypes.c_double), ("row_offset", ctypes.c_double),
+                ("views", ctypes.POINTER(ctypes.c_double))]
+
+
 class Options(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("gamma", ctypes.c_double), ("h_dc", ctypes.c_double),
                 ("c_r", ctypes.c_double), ("kappa", ctypes.c_double),
@@ -106,6 +113,10 @@ SIGNATURES = [
     ("ncs_unet_train_step", _I, [_P, _P, _P, ctypes.c_float, _DP]),
     ("ncs_unet_set_conv_path", _I, [_P, _I]),
     ("ncs_unet_inject_wait_timeout", _I, [_P]),
+    ("ncs_cone_create", _I, [ctypes.POINTER(ConeGeometry), _I, _I, _P, ctypes.POINTER(_P)]),
+    ("ncs_cone_destroy", None, [_P]),
+    ("ncs_cone_apply_K", _I, [_P, _P, _P]),
+    ("ncs_cone_apply_KT", _I, [_P, _P, _P]),
     ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     ("ncs_batch_destroy", None, [_P]),
     ("ncs_batch_set_lanes", _I, [_P, _I]),
@@ -414,6 +425,71 @@ class Plan:
         out = np.empty(self.n, dtype=np.float64)
         _check(self._L.ncs_get_mu(self._h, out.ctypes.data_as(_DP)), "ncs_get_mu")
         return out.reshape(self.N, self.N)
+
+
+class Cone:
+    """Cone-beam operator pair (ncs_cone_create): K and its exact transpose for an N x N x Nz
+    volume.  Work runs on `stream` (torch.cuda.Stream / raw cudaStream_t int / None: a side
+    stream ordered with torch's current stream)."""
+
+    def __init__(self, N, Nz, n_views, n_rows, n_det, src_dist, pitch, row_pitch, offset=0.0, row_offset=0.0,
+                 views=None, stream=None):
+        import torch
+        L = load_library()
+        self._L = L
+        g = ConeGeometry()
+        g.n_views, g.n_rows, g.n_det = int(n_views), int(n_rows), int(n_det)
+        g.src_dist, g.pitch, g.offset = float(src_dist), float(pitch), float(offset)
+        g.row_pitch, g.row_offset = float(row_pitch), float(row_offset)
+        self._views = None
+        if views is not None:
+            self._views = (ctypes.c_double * len(views))(*[float(v) for v in views])
+            g.views = ctypes.cast(self._views, _DP)
+        self._auto = stream is None
+        if stream is None:
+            stream = torch.cuda.Stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        _check(L.ncs_cone_create(ctypes.byref(g), int(N), int(Nz),
+                                 ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)),
+                                 ctypes.byref(h)), "ncs_cone_create")
+        self._h = h
+        self.N, self.Nz = int(N), int(Nz)
+        self.n = self.N * self.N * self.Nz
+        self.m = int(n_views) * int(n_rows) * int(n_det)
+
+    def _call(self, what, fn, *args):
+        import torch
+        if self._auto:
+            self.stream.wait_stream(torch.cuda.current_stream())
+        try:
+            return _check(fn(*args), what)
+        finally:
+            if self._auto:
+                torch.cuda.current_stream().wait_stream(self.stream)
+
+    def apply_K(self, x, y=None):
+        import torch
+        y = torch.empty(self.m, device=x.device) if y is None else y
+        self._call("ncs_cone_apply_K", self._L.ncs_cone_apply_K, self._h, _ptr(x, "x", self.n), _ptr(y, "y", self.m))
+        return y
+
+    def apply_KT(self, y, x=None):
+        import torch
+        x = torch.empty(self.n, device=y.device) if x is None else x
+        self._call("ncs_cone_apply_KT", self._L.ncs_cone_apply_KT, self._h, _ptr(y, "y", self.m), _ptr(x, "x", self.n))
+        return x
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ncs_cone_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

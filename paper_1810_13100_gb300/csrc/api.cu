@@ -31,6 +31,67 @@ struct GraphCache {
 
 }  // namespace
 
+namespace ncs {
+
+// Fan-beam rays (Sec. 4, fan beam geometry; equiangular detector): view a puts the source at
+// S_a = R (-sin beta_a, cos beta_a); channel t is the ray leaving S_a at the fan angle
+// gamma_t = (t - (n_det-1)/2) pitch + offset, counted counter-clockwise from the central ray
+// (S_a towards the centre).  It is the line u cos(theta) + v sin(theta) = s with theta =
+// beta_a + gamma_t and s = R sin(gamma_t) (every quantity in FP64, rounded once), stepped over
+// rows when |cos theta| >= |sin theta| with the parallel beam's crossing, interpolation and
+// path length.
+bool fan_ray_tables(int N, int na, int nd, double R, double pitch, double offset, const double* views_in,
+                    std::vector<FanRay>& rays, std::vector<float>& rayw, std::vector<FanView>& views,
+                    std::vector<double>* geo)
+{
+    const double cN = 0.5 * (N - 1), cd = 0.5 * (nd - 1);
+    const double reach = cN * std::sqrt(2.0) + 2.0;   // farther from the centre a ray touches no pixel
+    const size_t m = (size_t)na * nd;
+    auto split_hi = [](double X) { return std::nearbyint(X * 1024.0) / 1024.0; };
+    rays.resize(m);
+    rayw.resize(m);
+    views.resize(na);
+    if (geo) geo->resize(3 * m);
+    for (int a = 0; a < na; ++a) {
+        const double be = views_in ? views_in[a] : 2.0 * M_PI * a / na;
+        const double sb = std::sin(be), cb = std::cos(be);
+        views[a] = make_float4((float)(-R * sb), (float)(R * cb), (float)sb, (float)(-cb));
+        for (int t = 0; t < nd; ++t) {
+            const double gam = (t - cd) * pitch + offset;
+            const double th = be + gam;
+            const double c = std::cos(th), sn = std::sin(th), s = R * std::sin(gam);
+            const int row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
+            double B, C, W;
+            if (std::fabs(s) > reach) {
+                B = 0.0;
+                C = -8.0;
+                W = 0.0;
+            } else if (row) {
+                B = sn / c;
+                C = (s - cN * sn) / c + cN;
+                W = 1.0 / std::fabs(c);
+            } else {
+                B = c / sn;
+                C = cN - (s + cN * c) / sn;
+                W = 1.0 / std::fabs(sn);
+            }
+            if (std::fabs(split_hi(B)) * (N - 1) + std::fabs(split_hi(C)) >= 16384.0) return false;
+            const size_t r = (size_t)a * nd + t;
+            rays[r] = make_float4((float)split_hi(B), (float)(B - split_hi(B)), (float)split_hi(C),
+                                  (float)(C - split_hi(C)));
+            rayw[r] = row ? (float)W : -(float)W;
+            if (geo) {
+                (*geo)[3 * r] = c;
+                (*geo)[3 * r + 1] = sn;
+                (*geo)[3 * r + 2] = s;
+            }
+        }
+    }
+    return true;
+}
+
+}  // namespace ncs
+
 struct ncs_plan {
     int dev = 0;
     int N = 0, na = 0, nd = 0;
@@ -611,42 +672,12 @@ double split_hi(double X) { return std::nearbyint(X * 1024.0) / 1024.0; }
 int build_fan_tables(ncs_plan* p, const ncs_fan_geometry* fg)
 {
     const int N = p->N, na = p->na, nd = p->nd;
-    const double R = fg->src_dist, cN = 0.5 * (N - 1), cd = 0.5 * (nd - 1);
-    const double reach = cN * std::sqrt(2.0) + 2.0;   // farther from the centre a ray touches no pixel
+    const double cd = 0.5 * (nd - 1);
     const size_t m = (size_t)na * nd;
-    p->h_rays.resize(m);
-    p->h_rayw.resize(m);
-    std::vector<FanView> views(na);
-    for (int a = 0; a < na; ++a) {
-        const double be = fg->views ? fg->views[a] : 2.0 * M_PI * a / na;
-        const double sb = std::sin(be), cb = std::cos(be);
-        views[a] = make_float4((float)(-R * sb), (float)(R * cb), (float)sb, (float)(-cb));
-        for (int t = 0; t < nd; ++t) {
-            const double gam = (t - cd) * fg->pitch + fg->offset;
-            const double th = be + gam;
-            const double c = std::cos(th), sn = std::sin(th), s = R * std::sin(gam);
-            const int row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
-            double B, C, W;
-            if (std::fabs(s) > reach) {
-                B = 0.0;
-                C = -8.0;
-                W = 0.0;
-            } else if (row) {
-                B = sn / c;
-                C = (s - cN * sn) / c + cN;
-                W = 1.0 / std::fabs(c);
-            } else {
-                B = c / sn;
-                C = cN - (s + cN * c) / sn;
-                W = 1.0 / std::fabs(sn);
-            }
-            if (std::fabs(split_hi(B)) * (N - 1) + std::fabs(split_hi(C)) >= 16384.0) return NCS_ERR_UNSUPPORTED;
-            const size_t r = (size_t)a * nd + t;
-            p->h_rays[r] = make_float4((float)split_hi(B), (float)(B - split_hi(B)), (float)split_hi(C),
-                                       (float)(C - split_hi(C)));
-            p->h_rayw[r] = row ? (float)W : -(float)W;
-        }
-    }
+    std::vector<FanView> views;
+    if (!fan_ray_tables(N, na, nd, fg->src_dist, fg->pitch, fg->offset, fg->views, p->h_rays, p->h_rayw, views,
+                        nullptr))
+        return NCS_ERR_UNSUPPORTED;
     p->fan = true;
     p->inv_pitch = (float)(1.0 / fg->pitch);
     p->t_off = (float)(cd - fg->offset / fg->pitch);

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace ncs {
 
 // Storage precision of the iteration state (FP32 arithmetic either way):
@@ -200,6 +202,13 @@ struct RadixPlan {
     int n;               // number of stages
     int r[12];           // radices (2, 3, 4 or 8)
 };
+
+// Host: the fan-beam ray tables of N x N images for n_views x n_det rays (see FanRay): FP64,
+// rounded once.  geo (optional) receives (cos, sin, s) of every ray in FP64.  Returns false
+// when a ray's coefficients leave the range in which H = Bhi q + Chi is exact.
+bool fan_ray_tables(int N, int na, int nd, double R, double pitch, double offset, const double* views,
+                    std::vector<FanRay>& rays, std::vector<float>& rayw, std::vector<FanView>& vws,
+                    std::vector<double>* geo);
 
 // ---- launchers (all asynchronous on `st`) ----
 cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st);

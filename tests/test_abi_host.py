@@ -123,3 +123,22 @@ def test_fan_plan_rejects_unknown_gather_kernel(lib):
         h = ctypes.c_void_p()
         assert lib.ncs_plan_create_fan(ctypes.byref(g), 64, 64, 0.1, 1.0, ctypes.byref(o), ctypes.byref(h)) == -1
         assert not h.value
+
+
+def test_cone_create_rejects_bad_geometry_before_touching_cuda(lib):
+    from paper_1810_13100_gb300 import binding
+
+    def create(N=16, Nz=4, nv=4, nr=5, nd=8, R=20.0, pitch=0.05, rp=0.1, roff=0.0):
+        g = binding.ConeGeometry()
+        g.n_views, g.n_rows, g.n_det = nv, nr, nd
+        g.src_dist, g.pitch, g.offset, g.row_pitch, g.row_offset = R, pitch, 0.0, rp, roff
+        h = ctypes.c_void_p()
+        rc = lib.ncs_cone_create(ctypes.byref(g), N, Nz, None, ctypes.byref(h))
+        assert not h.value
+        return rc
+    assert create(rp=0.4) == -1            # outer slopes +-0.8 >= 1/sqrt(2)
+    assert create(roff=0.7) == -1
+    assert create(R=12.0) == -1            # source inside the image's circle plus 3 pixels
+    assert create(pitch=0.0) == -1 and create(rp=-0.1) == -1
+    assert create(N=15) == -1 and create(Nz=0) == -1 and create(nr=0) == -1
+    assert lib.ncs_cone_create(None, 16, 4, None, None) == -1
