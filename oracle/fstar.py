@@ -30,6 +30,7 @@ PARAMS = {
     "pet256": dict(alpha=1.0, beta=1.0, gamma=0.0),
     "fan64": dict(alpha=0.01, beta=0.01, gamma=0.0),
     "fan512": dict(alpha=0.003, beta=0.003, gamma=0.0),
+    "cone128": dict(alpha=0.01, beta=0.01, gamma=0.0),
 }
 
 # probe images of eq. (H-fan) for the fan-beam runs (SplitMix64 seeds 1..FAN_PROBES); with 32
@@ -126,6 +127,40 @@ def write_golden(workload, seed, P, p, rho, hist):
     return out
 
 
+def run_cone(workload: str, seed: int, iters: int, checkpoint: str | None, every: int = 250):
+    """The same reference run for a cone-beam (3-D) workload, with oracle/cone.py."""
+    import synth
+    from . import cone as oc
+    W = synth.WORKLOADS[workload]
+    p = PARAMS[workload]
+    N, Nz, na, nr, nd, R = W["N"], W["Nz"], W["n_angles"], W["n_rows"], W["n_det"], W["src_dist"]
+    g = oc.ConeGeometry(N, Nz, na, nr, nd, R, synth.fan_pitch(N, R, nd, W["cover"]),
+                        synth.cone_row_pitch(N, Nz, R, nr, W["cover"]))
+    pr = synth.ct3d_problem(seed, N, Nz, na, nr, nd, W["n_ellipses"], W["noise_frac"], lambda x: oc.K(x, g))
+    P = oc.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=p["alpha"], beta=p["beta"], tv=W["tv"])
+    mus, rho = oc.a3_scaled_mu(P, oc.mu_probes(P, FAN_PROBES, p["gamma"]))
+    Minv = lambda r: oc.circulant_solve(r, mus)
+    st, k0, hist = oc.zero_state(P), 0, []
+    if checkpoint and os.path.exists(checkpoint):
+        z = np.load(checkpoint)
+        st = oc.State(z["x"], z["u"], (z["vx"], z["vy"], z["vz"]))
+        k0, hist = int(z["k"]), [tuple(h) for h in z["hist"]]
+    t0 = time.time()
+    out = None
+    for k in range(k0, iters):
+        st = oc.ncs_step(P, st, Minv)
+        if (k + 1) % every == 0 or k + 1 == iters:
+            f = oc.objective(P, st.x)
+            hist.append((k + 1, f))
+            print("%s seed %d iter %d f %.12e  (%.0fs)" % (workload, seed, k + 1, f, time.time() - t0), flush=True)
+            if checkpoint:
+                np.savez(checkpoint + ".tmp.npz", x=st.x, u=st.u, vx=st.v[0], vy=st.v[1], vz=st.v[2], k=k + 1,
+                         hist=np.array(hist))
+                os.replace(checkpoint + ".tmp.npz", checkpoint)
+            out = write_golden(workload, seed, P, p, rho, hist)
+    return out
+
+
 def load(workload: str, seed: int = 0):
     with open(golden_path(workload, seed)) as fh:
         return json.load(fh)
@@ -138,4 +173,8 @@ if __name__ == "__main__":
     ap.add_argument("--iters", type=int, default=8000)
     ap.add_argument("--checkpoint", default=None)
     a = ap.parse_args()
-    run(a.workload, a.seed, a.iters, a.checkpoint)
+    import synth
+    if synth.WORKLOADS[a.workload].get("geometry") == "cone":
+        run_cone(a.workload, a.seed, a.iters, a.checkpoint)
+    else:
+        run(a.workload, a.seed, a.iters, a.checkpoint)

@@ -28,4 +28,8 @@ from .phantom import (  # noqa: F401
     WORKLOADS,
     batch_sides,
     fan_pitch,
+    cone_row_pitch,
+    draw_ellipsoids,
+    rasterize3,
+    ct3d_problem,
 )

@@ -70,6 +70,55 @@ def rasterize(ell: Ellipses, N: int) -> np.ndarray:
     return img
 
 
+@dataclasses.dataclass(frozen=True)
+class Ellipsoids:
+    """Ellipsoid parameters in the normalised frame [-1, 1]^3 (one row per ellipsoid): centre,
+    semi-axes, rotation phi about the w axis, additive intensity."""
+    c: np.ndarray      # (n, 3)
+    ax: np.ndarray     # (n, 3)
+    phi: np.ndarray
+    rho: np.ndarray
+
+
+def draw_ellipsoids(rng: np.random.Generator, n: int) -> Ellipsoids:
+    """Draw n ellipsoids: centres U[-0.8,0.8]^3, semi-axes U[0.05,0.5]^3, rotation about w
+    U[0,pi), intensity U[0,1], in that fixed order."""
+    c = rng.uniform(-0.8, 0.8, size=(n, 3))
+    ax = rng.uniform(0.05, 0.5, size=(n, 3))
+    phi = rng.uniform(0.0, math.pi, size=n)
+    rho = rng.uniform(0.0, 1.0, size=n)
+    return Ellipsoids(c, ax, phi, rho)
+
+
+def rasterize3(ell: Ellipsoids, N: int, Nz: int) -> np.ndarray:
+    """Voxel value = sum of the intensities of the ellipsoids that contain the voxel centre
+    (float64, shape (Nz, N, N)); the volume spans [-1, 1] along each axis."""
+    U, V = _pixel_grid(N)
+    w = ((np.arange(Nz, dtype=np.float64) - (Nz - 1) / 2.0) * (2.0 / Nz))[:, None, None]
+    vol = np.zeros((Nz, N, N), dtype=np.float64)
+    for k in range(len(ell.rho)):
+        du, dv, dw = U[None] - ell.c[k, 0], V[None] - ell.c[k, 1], w - ell.c[k, 2]
+        c, s = math.cos(ell.phi[k]), math.sin(ell.phi[k])
+        p = (du * c + dv * s) / ell.ax[k, 0]
+        q = (-du * s + dv * c) / ell.ax[k, 1]
+        r = dw / ell.ax[k, 2]
+        vol += np.where(p * p + q * q + r * r <= 1.0, ell.rho[k], 0.0)
+    return vol
+
+
+def ct3d_problem(seed: int, N: int, Nz: int, n_views: int, n_rows: int, n_det: int, n_ellipsoids: int,
+                 noise_frac: float, project) -> dict:
+    """Seeded 3-D TV-CT instance: b = project(x_true) + N(0, sigma^2), sigma = noise_frac *
+    max(project(x_true)); `project` maps the float32 volume (Nz, N, N) to its (n_views,
+    n_rows, n_det) sinogram.  Draw order: the ellipsoids, then the noise.  Arrays float32."""
+    rng = np.random.default_rng(seed)
+    ell = draw_ellipsoids(rng, n_ellipsoids)
+    x_true = _f32(rasterize3(ell, N, Nz))
+    z = rng.standard_normal((n_views, n_rows, n_det))
+    b, sigma = ct_data(project(x_true), z, noise_frac)
+    return dict(kind="ct", seed=seed, N=N, Nz=Nz, x_true=x_true, b=b, sigma=sigma)
+
+
 def angles(n_angles: int) -> np.ndarray:
     """theta_a = a*pi/n_angles (float64)."""
     return np.arange(n_angles, dtype=np.float64) * (math.pi / n_angles)
@@ -186,7 +235,17 @@ WORKLOADS = {
                   n_ellipses=10, noise_frac=0.01, lam=0.01, tv="aniso"),
     "fan512": dict(kind="ct", geometry="fan", N=512, n_angles=720, n_det=768, src_dist=1024.0, cover=1.02,
                    n_ellipses=20, noise_frac=0.005, lam=0.005, tv="iso"),
+    # Cone-beam TV-CT (circular orbit, cylindrical detector): 128 x 128 x 32 volume, 180 views
+    # on a full turn, 32 rows x 192 channels, source at twice the side, 12 ellipsoids.
+    "cone128": dict(kind="ct", geometry="cone", N=128, Nz=32, n_angles=180, n_rows=32, n_det=192,
+                    src_dist=256.0, cover=1.05, n_ellipses=12, noise_frac=0.005, lam=0.005, tv="iso"),
 }
+
+
+def cone_row_pitch(N: int, Nz: int, src_dist: float, n_rows: int, cover: float = 1.05) -> float:
+    """Slope step between detector rows whose slopes span the volume's top and bottom faces
+    seen from the nearest point of its circumscribed cylinder, widened by `cover`."""
+    return 2.0 * (Nz / 2.0) / (src_dist - N / math.sqrt(2.0)) * cover / n_rows
 
 
 def fan_pitch(N: int, src_dist: float, n_det: int, cover: float = 1.02) -> float:

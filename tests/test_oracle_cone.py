@@ -147,3 +147,16 @@ def test_cone_ncs_fixed_point_is_dense_admm_minimiser():
     assert np.linalg.norm(st.u - (oc.K(st.x, g) - b)) <= 1e-8 * np.linalg.norm(st.u)
     r = oc.AT_apply(P, st.u, st.v)
     assert np.linalg.norm(r) <= 1e-8 * np.linalg.norm(oc.KT(st.u, g))
+
+
+def test_ellipsoid_phantom_volume():
+    """The 3-D phantom generator: a sphere of radius 1/2 at the centre fills (4/3) pi (1/2)^3
+    of the [-1, 1]^3 volume's 8, and a rotation about w leaves a sphere unchanged."""
+    import synth
+    ell = synth.phantom.Ellipsoids(np.zeros((1, 3)), np.full((1, 3), 0.5), np.array([0.7]), np.array([2.0]))
+    vol = synth.rasterize3(ell, 64, 64)
+    frac = float(np.mean(vol > 0))
+    assert abs(frac - (4.0 / 3.0) * math.pi * 0.125 / 8.0) < 0.02 * frac
+    assert set(np.unique(vol)) <= {0.0, 2.0}
+    ell0 = synth.phantom.Ellipsoids(np.zeros((1, 3)), np.full((1, 3), 0.5), np.array([0.0]), np.array([2.0]))
+    assert np.array_equal(vol, synth.rasterize3(ell0, 64, 64))
