@@ -322,3 +322,28 @@ def admm_textbook(P: Problem, n_iter: int, Ad: np.ndarray):
         x = pinv @ (Ad.T @ (z + bb + ld))
         ld = ld + z - Ad @ x + bb
     return x.reshape(P.g.shape)
+
+
+def lambda_max_AtA(P: Problem, seed: int = 0, tol: float = 1e-9, max_iter: int = 500) -> float:
+    """lambda_max(A^T A) by power iteration with the Rayleigh quotient (SplitMix64 start)."""
+    x = splitmix64_uniform(seed, P.g.n).reshape(P.g.shape)
+    x /= np.linalg.norm(x)
+    lm, old = 0.0, None
+    for _ in range(max_iter):
+        w = AtA_apply(P, x)
+        lm = float(np.sum(x * w))
+        x = w / np.linalg.norm(w)
+        if old is not None and abs(lm - old) <= tol * abs(lm):
+            break
+        old = lm
+    return lm
+
+
+def pdhg_gamma(P: Problem, margin: float = 1e-2) -> float:
+    """gamma_P = alpha lambda_max(A^T A) (1 + margin): the step condition of eq. (PDHG)."""
+    return P.alpha * lambda_max_AtA(P) * (1.0 + margin)
+
+
+def pdhg_step(P: Problem, st: State, gamma_p: float) -> State:
+    """Eq. (PDHG): x+ = x - gamma_P^{-1} A^T u, then NCS's dual update (M = gamma_P I)."""
+    return ncs_step(P, st, lambda r: r / gamma_p)

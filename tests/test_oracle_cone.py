@@ -160,3 +160,27 @@ def test_ellipsoid_phantom_volume():
     assert set(np.unique(vol)) <= {0.0, 2.0}
     ell0 = synth.phantom.Ellipsoids(np.zeros((1, 3)), np.full((1, 3), 0.5), np.array([0.0]), np.array([2.0]))
     assert np.array_equal(vol, synth.rasterize3(ell0, 64, 64))
+
+
+def test_cone_pdhg_reaches_the_same_minimiser():
+    """PDHG (eq. (PDHG), M = gamma_P I) on the same 3-D problem converges to the dense-ADMM
+    minimiser too (slower: to 1e-4 after 4000 iterations)."""
+    import synth
+    N, Nz, na, nr, nd, R = 8, 4, 12, 4, 12, 14.0
+    g = oc.ConeGeometry(N, Nz, na, nr, nd, R, cover_pitch(N, R, nd), row_pitch=0.1)
+    rng = np.random.default_rng(4)
+    x_true = np.broadcast_to(synth.ct_phantom(0, N, 4, 4, 3)[0], (Nz, N, N)) * (1.0 + 0.1 * rng.random((Nz, 1, 1)))
+    b = oc.K(x_true, g) + 0.01 * rng.standard_normal(g.sino_shape)
+    P = oc.Problem(g, b, lam=0.5, alpha=1.0, beta=3.0, tv="aniso")
+    gp = oc.pdhg_gamma(P)
+    st = oc.zero_state(P)
+    for _ in range(4000):
+        st = oc.pdhg_step(P, st, gp)
+    Pa = oc.Problem(g, b, lam=0.5, alpha=10.0, beta=10.0, tv="aniso")
+    xstar = oc.admm_textbook(Pa, 2500, oc.dense_A(Pa))
+    assert np.linalg.norm(st.x - xstar) <= 1e-4 * np.linalg.norm(xstar)
+    # gamma_P from the largest eigenvalue of the dense A^T A, times alpha (1 + 1e-2); the power
+    # iteration's Rayleigh quotient approaches it from below
+    lm_dense = float(np.linalg.eigvalsh(oc.dense_A(P).T @ oc.dense_A(P)).max())
+    exact = P.alpha * lm_dense * 1.01
+    assert exact * (1 - 1e-6) <= gp <= exact * (1 + 1e-12)
