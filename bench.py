@@ -41,13 +41,54 @@ ADMM_PARAMS = dict(alpha=0.1, beta=0.1, n_cg=10)
 ADMM_CAP = 1000                     # outer steps
 CHECK_EVERY = 10
 TTG_TOL = 1e-4
-TTG_CAP = 2000
+TTG_CAP = 2000                      # NCS and ADMM iteration cap of the time-to-gap runs
+PDHG_CAP = 20000                    # PDHG needs ~10^4 iterations on this workload
 METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
-# DRAM bytes (read + write) per launch of the current kernels, from one ncu capture
-# (profiles/ncu_k_gather_k_fwd_ct512.md); set to None when a kernel changes.
-NCU_TRAFFIC = {"joseph_gather": None, "joseph_fwd": 8508672.0}
-# warp instructions executed per launch (smsp__inst_executed.sum, same capture)
-NCU_WARP_INSTR = {"joseph_gather": None, "joseph_fwd": 128230021.0}
+# class name of the library's per-kernel timers -> kernel name in ncu's launch list
+NCU_KERNEL = {"joseph_gather": "k_gather", "joseph_fwd": "k_fwd"}
+
+
+def load_counters(workload):
+    """ncu counters per launch of the library's kernels for a workload, from the committed
+    capture summary profiles/counters_<workload>.txt.  Each data line reads
+
+        <ncu kernel name> <source file> <sha256 of that file> <dram bytes> <warp instructions>
+
+    A kernel's counters are used only while its source file still has the recorded hash
+    (a changed kernel gets null counters until it is captured again)."""
+    import hashlib
+    out = {}
+    path = os.path.join(ROOT, "profiles", "counters_%s.txt" % workload)
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return out
+    for ln in lines:
+        f = ln.split()
+        if len(f) != 5 or ln.startswith("#"):
+            continue
+        name, src, sha, dram, winst = f
+        try:
+            cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()
+        except OSError:
+            continue
+        out[name] = {"traffic": float(dram), "warp_instr": float(winst), "current": cur == sha,
+                     "source": src}
+    return out
+
+
+def counters_for(cnt, cls, ncu_name=None):
+    """(dram bytes, warp instructions) per launch of a kernel class, or (None, None) when
+    there is no current capture of it."""
+    c = cnt.get(ncu_name or NCU_KERNEL.get(cls, cls))
+    if not c or not c["current"]:
+        return None, None
+    return c["traffic"], c["warp_instr"]
+
+
+def sm_count(dev):
+    import torch
+    return torch.cuda.get_device_properties(dev).multi_processor_count
 
 
 def load_peaks():
@@ -305,15 +346,172 @@ def admm_ttg(ncs, N, na, nd, W, b, f_star, dev, grid=False):
         cfgs += [dict(alpha=a, beta=a, n_cg=c) for a in (0.01, 0.03, 0.1, 0.3, 1.0) for c in (3, 10)
                  if (a, c) != (ADMM_PARAMS["alpha"], ADMM_PARAMS["n_cg"])]
     out = []
+    x0 = None
     for c in cfgs:
+        t0 = time.perf_counter()
         aplan = ncs.Plan(N, na, nd, W["lam"], c["alpha"], beta=c["beta"], tv=W["tv"], check_every=CHECK_EVERY,
                          h_probes=NCS_PARAMS["h_probes"])
+        setup = _sync_ms(t0)
         x = torch.zeros(N * N, device=dev)
         rep = aplan.admm_solve(b, x, tol=TTG_TOL, max_outer=ADMM_CAP, n_cg=c["n_cg"], f_star=f_star)
         aplan.close()
         out.append(dict(c, outer=rep["iters"], time_ms=rep["time_ms"], gap=rep["gap"], status=rep["status"],
-                        operator_passes=rep["iters"] * (c["n_cg"] + 2)))
-    return out if grid else out[0]
+                        operator_passes=rep["iters"] * (c["n_cg"] + 2), with_setup_ms=rep["time_ms"] + setup))
+        if x0 is None:
+            x0 = x.cpu().numpy().astype("float64")
+    return (out if grid else out[0]), x0
+
+
+def projector_roofline(name, ms_per_launch, nnz, peaks, dev, counters, ncu_name=None):
+    """Roofline object of a projector kernel (K or K^T): 2 flops per nonzero of K against
+    the FP32 FMA peak derived from the device's SM count, 128 FP32 lanes per SM and the
+    maximum SM clock ("alu"); with a current ncu capture, its DRAM traffic per launch and
+    an issue roofline (warp instructions per launch over the event-timed duration against
+    SMs x 4 schedulers x 1 warp instruction per cycle)."""
+    if name not in ("joseph_gather", "joseph_fwd", "joseph_fwd_resid"):
+        return None
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    sms = sm_count(dev)
+    fp32_peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12      # FMA = 2 flops
+    t = ms_per_launch / 1000.0
+    achieved = 2.0 * nnz / t / 1e12
+    traffic, wi = counters_for(counters, name, ncu_name)
+    roof = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": traffic,
+            "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
+            "peak_kind": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (sms, sm_mhz)}
+    if wi:
+        issue_peak = sms * 4 * sm_mhz * 1e6 / 1e12
+        issue = wi / t / 1e12
+        roof["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "Twarp-inst/s", "frac": issue / issue_peak,
+                         "warp_instructions_per_launch": wi,
+                         "peak_kind": "%d SMs x 4 schedulers x 1 warp-instruction/cycle x %.0f MHz (derived)"
+                                      % (sms, sm_mhz)}
+    else:
+        roof["issue"] = None
+    return roof
+
+
+def _sync_ms(t0):
+    import torch
+    torch.cuda.synchronize()
+    return 1000.0 * (time.perf_counter() - t0)
+
+
+def time_to_gap(args, rank, ncs, plan, W, N, na, nd, dev):
+    """NCS, PDHG and ADMM-PCG from zero to the 1e-4 relative gap against the oracle's f*
+    on every seed with a stored record.  Returns (summary, stops): stops[(seed, solver)] is
+    the host copy of the returned x, re-evaluated by the oracle in the CPU leg."""
+    import statistics
+    import torch
+    n = N * N
+    seeds = [args.seed + rank] + [sd for sd in range(5) if sd != args.seed + rank]
+    runs, stops = [], {}
+    # setup, timed on the host around plan creation (synchronising): NCS builds the Joseph
+    # tables, the DC entry, eq. (H-fan) over 32 probes and the (A3) power iteration; PDHG's
+    # plan skips M's power iteration (one step, its M is unused) and then computes
+    # lambda_max(A^T A) by its own power iteration
+    t0 = time.perf_counter()
+    nplan = ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], gamma=NCS_PARAMS["gamma"],
+                     tv=W["tv"], check_every=CHECK_EVERY, h_probes=NCS_PARAMS["h_probes"])
+    ncs_setup = _sync_ms(t0)
+    t0 = time.perf_counter()
+    pplan = ncs.Plan(N, na, nd, W["lam"], PDHG_PARAMS["alpha"], beta=PDHG_PARAMS["beta"], tv=W["tv"],
+                     check_every=CHECK_EVERY, power_max_iter=1)
+    pdhg_tables = _sync_ms(t0)
+    t0 = time.perf_counter()
+    lmax, _ = pplan.power_bound()
+    pdhg_lmax = _sync_ms(t0)
+    pdhg_setup = pdhg_tables + pdhg_lmax
+    for sd in seeds:
+        gold = load_golden(WORKLOAD, sd)
+        if not gold:
+            continue
+        f_star = gold["f_star"]
+        bs = torch.from_numpy(make_inputs(sd, gpu_projector(plan, dev))[1]["b"].ravel()).to(dev)
+        run = {"seed": sd, "f_star": f_star, "oracle_iters": gold.get("iterations"),
+               "f_star_tight": bool(gold.get("tight", False)),
+               "f_star_decrease_last_1000_rel": gold["decrease_last_1000"] / abs(f_star)}
+        if "b_sum" in gold:
+            # the oracle's f* belongs to the sinogram made with its own K; this run's b
+            # (made with the library's K) must agree to float32 rounding
+            bd = bs.double()
+            run["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
+                                 "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
+        xs = torch.zeros(n, device=dev)
+        rep = nplan.solve(bs, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
+        run["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        run["ncs"]["with_setup_ms"] = rep["time_ms"] + ncs_setup
+        stops[(sd, "ncs")] = xs.cpu().numpy().astype("float64")
+        xs.zero_()
+        rep = pplan.pdhg_solve(bs, xs, tol=TTG_TOL, max_iter=PDHG_CAP, f_star=f_star)
+        run["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        run["pdhg"]["with_setup_ms"] = rep["time_ms"] + pdhg_setup
+        stops[(sd, "pdhg")] = xs.cpu().numpy().astype("float64")
+        adm, xa = admm_ttg(ncs, N, na, nd, W, bs, f_star, dev, args.admm_grid and not runs)
+        run["admm"] = adm
+        stops[(sd, "admm")] = xa
+        runs.append(run)
+    nplan.close()
+    pplan.close()
+    if not runs:
+        return None, stops
+    med = lambda xs_: statistics.median(xs_) if xs_ else None
+    ttg = {"tol": TTG_TOL, "cap": {"ncs": TTG_CAP, "pdhg": PDHG_CAP, "admm_outer": ADMM_CAP},
+           "seeds": [r["seed"] for r in runs], "runs": runs,
+           "setup_ms": {"ncs": ncs_setup, "pdhg": pdhg_setup, "pdhg_tables": pdhg_tables,
+                        "pdhg_lambda_max": pdhg_lmax, "lambda_max_AtA": lmax,
+                        "what": "host wall time of plan creation (NCS: tables, h_dc, 32 probes of eq. (H-fan), "
+                                "(A3) power iteration; PDHG: tables + power iteration for lambda_max(A^T A))"}}
+    for solver in ("ncs", "pdhg"):
+        ok = [r[solver] for r in runs if r[solver]["status"] == 0]
+        ttg[solver + "_converged_gpu_objective"] = len(ok)
+        ttg[solver + "_median_ms"] = med([r["time_ms"] for r in ok])
+        ttg[solver + "_median_ms_with_setup"] = med([r["with_setup_ms"] for r in ok])
+        ttg[solver + "_median_iters"] = med([r["iters"] for r in ok])
+    adm = [r["admm"] for r in runs]
+    adm = [a[0] if isinstance(a, list) else a for a in adm]
+    adm_ok = [a for a in adm if a["status"] == 0]
+    ttg.update({"admm": ADMM_PARAMS, "admm_converged_gpu_objective": len(adm_ok),
+                "admm_median_ms": med([a["time_ms"] for a in adm_ok]),
+                "admm_median_outer": med([a["outer"] for a in adm_ok])})
+    return ttg, stops
+
+
+def oracle_check_stops(ttg, stops):
+    """The CPU leg's check of the time-to-gap runs: the FP64 oracle's objective at every
+    stopping point, on the sinogram the stored f* was computed for (made with the oracle's
+    own K), gives the oracle gap (f(x) - f*)/|f*|.  A seed counts as converged for a solver
+    only when that gap is <= the tolerance and the stored f* record is tight."""
+    import numpy as np
+    from oracle import operators as oop, solvers as osv
+    import synth
+    W = synth.WORKLOADS[WORKLOAD]
+    N, na, nd = W["N"], W["n_angles"], W["n_det"]
+    g = oop.Geometry(N, na, nd)
+    proj = oop.projector(N, na, nd)
+    for r in ttg["runs"]:
+        pr = synth.ct_problem(r["seed"], N, na, nd, W["n_ellipses"], W["noise_frac"], proj)
+        P = osv.Problem(g, pr["b"].astype(np.float64), lam=W["lam"], alpha=1.0, beta=1.0, tv=W["tv"])
+        for solver in ("ncs", "pdhg", "admm"):
+            x = stops.get((r["seed"], solver))
+            tgt = r[solver][0] if isinstance(r[solver], list) else r[solver]
+            if x is None:
+                continue
+            f = osv.objective(P, x.reshape(N, N))
+            tgt["oracle_f"] = f
+            tgt["oracle_gap"] = (f - r["f_star"]) / abs(r["f_star"])
+    for solver in ("ncs", "pdhg", "admm"):
+        conv = []
+        for r in ttg["runs"]:
+            tgt = r[solver][0] if isinstance(r[solver], list) else r[solver]
+            if "oracle_gap" in tgt and r["f_star_tight"] and tgt["status"] == 0 and tgt["oracle_gap"] <= ttg["tol"]:
+                conv.append(r["seed"])
+        ttg[solver + "_converged_oracle"] = len(conv)
+        ttg[solver + "_converged_oracle_seeds"] = conv
+    ttg["oracle_check"] = ("FP64 oracle objective at every stop on the oracle-made sinogram; a seed counts as "
+                           "converged only with a tight f* record (last 1000 oracle iterations lowered f by "
+                           "<= 1e-7 relative) and an oracle gap <= tol")
 
 
 def run_ours(args, ws, rank, local):
@@ -384,26 +582,7 @@ def run_ours(args, ws, rank, local):
     dom_ms, dom_n = kern_timed[dom_name] if kern_timed.get(dom_name, (0, 0))[1] else kern[dom_name]
     clk_sum = clk.summary()
     nnz = plan.nnz()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12      # FMA = 2 flops
-    roof = None
-    if dom_name in ("joseph_gather", "joseph_fwd", "joseph_fwd_resid"):
-        flops = 2.0 * nnz
-        achieved = flops / (dom_ms / dom_n / 1000.0) / 1e12
-        roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": achieved / fp32_peak_tflops, "traffic": NCU_TRAFFIC.get(dom_name),
-                "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
-                "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
-        # the kernel is bound by instruction issue: its measured instruction count per
-        # launch over the event-timed duration against 152 SMs x 4 schedulers x clock
-        wi = NCU_WARP_INSTR.get(dom_name)
-        if wi:
-            issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
-            issue = wi / (dom_ms / dom_n / 1000.0) / 1e12
-            roof["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "Twarp-inst/s", "frac": issue / issue_peak,
-                             "warp_instructions_per_launch": wi,
-                             "peak_kind": "152 SMs x 4 schedulers x 1 warp-instruction/cycle x %.0f MHz (derived)"
-                                          % sm_mhz}
+    roof = projector_roofline(dom_name, dom_ms / dom_n, nnz, peaks, dev, load_counters(WORKLOAD))
     # whole-iteration algorithmic bytes (FP32 state read + written once, b read, spectrum round trips)
     it_bytes = 4.0 * (10 * n + 3 * m)
     it_gbs = it_bytes / (t_ms / args.steps / 1000.0) / 1e9
@@ -432,63 +611,14 @@ def run_ours(args, ws, rank, local):
         e2e = {"value": reduce_sum(k_e2e, ws) / reduce_max(dt, ws), "unit": "it/s",
                "h2d_bytes_per_step": 4 * m, "d2h_bytes_per_step": 4 * n}
 
-    # ---- time to 1e-4 gap, NCS vs PDHG (same GPU, same inputs, zero start), on every
-    # seed of the workload that has the oracle's f* (this rank's seed first)
+    # ---- time to 1e-4 gap, NCS vs PDHG vs ADMM (same GPU, same inputs, zero start), on every
+    # seed of the workload that has the oracle's f* (this rank's seed first); each solver's
+    # setup (plan tables, M and its (A3) power iteration for NCS, lambda_max(A^T A) for PDHG)
+    # is timed too, and every stopping point is kept for the oracle's own check (CPU leg)
     ttg = None
+    stops = {}
     if not args.skip_ttg:
-        seeds = [args.seed + rank] + [sd for sd in range(5) if sd != args.seed + rank]
-        runs = []
-        pplan = None
-        for sd in seeds:
-            gold = load_golden(WORKLOAD, sd)
-            if not gold:
-                continue
-            f_star = gold["f_star"]
-            bs = b if sd == args.seed + rank else torch.from_numpy(
-                make_inputs(sd, gpu_projector(plan, dev))[1]["b"].ravel()).to(dev)
-            run = {"seed": sd, "f_star": f_star, "oracle_iters": gold.get("iterations")}
-            if "b_sum" in gold:
-                # the oracle's f* belongs to the sinogram made with its own K; this run's b
-                # (made with the library's K) must agree to float32 rounding
-                bd = bs.double()
-                run["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
-                                     "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
-            xs = torch.zeros(n, device=dev)
-            rep = plan.solve(bs, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
-            run["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-            if rep["status"] != 0 and args.ttg_extended:
-                xs.zero_()
-                rep = plan.solve(bs, xs, tol=TTG_TOL, max_iter=args.ttg_extended, f_star=f_star)
-                run["ncs_extended"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-            if pplan is None:
-                pplan = ncs.Plan(N, na, nd, W["lam"], PDHG_PARAMS["alpha"], beta=PDHG_PARAMS["beta"], tv=W["tv"],
-                                 check_every=CHECK_EVERY)
-            xs.zero_()
-            rep = pplan.pdhg_solve(bs, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
-            run["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-            if not runs and rep["status"] != 0 and args.pdhg_extended:
-                xs.zero_()
-                rep = pplan.pdhg_solve(bs, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=f_star)
-                run["pdhg_extended"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
-            run["admm"] = admm_ttg(ncs, N, na, nd, W, bs, f_star, dev, args.admm_grid and not runs)
-            runs.append(run)
-        if pplan is not None:
-            pplan.close()
-        if runs:
-            import statistics
-            ok = [r["ncs"] for r in runs if r["ncs"]["status"] == 0]
-            ttg = {"tol": TTG_TOL, "cap": TTG_CAP, "seeds": [r["seed"] for r in runs], "runs": runs,
-                   "ncs_converged": len(ok),
-                   "ncs_median_ms": statistics.median(r["time_ms"] for r in ok) if ok else None,
-                   "ncs_median_iters": statistics.median(r["iters"] for r in ok) if ok else None,
-                   "pdhg_converged": sum(1 for r in runs if r["pdhg"]["status"] == 0),
-                   "pdhg_median_gap_at_cap": statistics.median(r["pdhg"]["gap"] for r in runs)}
-            adm = [r["admm"] if isinstance(r["admm"], dict) else r["admm"][0] for r in runs]
-            adm_ok = [a for a in adm if a["status"] == 0]
-            ttg.update({"admm": ADMM_PARAMS, "admm_converged": len(adm_ok),
-                        "admm_median_ms": statistics.median(a["time_ms"] for a in adm_ok) if adm_ok else None,
-                        "admm_median_outer": statistics.median(a["outer"] for a in adm_ok) if adm_ok else None})
-
+        ttg, stops = time_to_gap(args, rank, ncs, plan, W, N, na, nd, dev)
     # ---- cuFFT as a timing reference for the hand-written FFT solve (A2, A3)
     fft_ref = None
     if rank == 0:
@@ -525,6 +655,8 @@ def run_ours(args, ws, rank, local):
         if ttg and ttg.get("ncs_median_iters"):
             cpu["time_to_gap_s_estimate"] = ttg["ncs_median_iters"] / r["rate"]
             cpu["time_to_gap_estimate_kind"] = "the GPU's iterations to the 1e-4 gap / the oracle's iterations per second"
+        if ttg:
+            oracle_check_stops(ttg, stops)
 
     if rank == 0:
         line = {
@@ -684,12 +816,6 @@ def run_pet(args, ws, rank, local):
 FAN_NCS = dict(alpha=0.01, beta=0.01, h_probes=128)   # {1,3} x 10^p grid on this workload (seed 0)
 FAN_PDHG = dict(alpha=0.001, beta=0.001)
 FAN_ADMM = dict(alpha=0.1, beta=0.1, n_cg=10)          # the 512x512 parallel beam's ADMM point
-# per launch of the fan-beam kernels, from one ncu capture (profiles/ncu_k_gather_fan_k_fwd_fan512.md);
-# None when a kernel changes
-FAN_NCU_TRAFFIC = {"joseph_gather": 14109952.0, "joseph_fwd": 19752192.0}
-FAN_NCU_WARP_INSTR = {"joseph_gather": 355371778.0, "joseph_fwd": 126397358.0}
-# the same for the pixel-quad K^T kernel (--fan-gather quads)
-FAN_NCU_QUADS = {"traffic": 14062848.0, "warp_instr": 644243860.0}
 
 
 def fan_plan(ncs, W, params, **kw):
@@ -763,23 +889,10 @@ def run_fan(args, ws, rank, local):
     dom_name = max(kern.items(), key=lambda kv: kv[1][0])[0]
     dom_ms, dom_n = kern_timed[dom_name] if kern_timed.get(dom_name, (0, 0))[1] else kern[dom_name]
     nnz = plan.nnz()
-    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    quads = dom_name == "joseph_gather" and args.fan_gather == "quads"
-    achieved = 2.0 * nnz / (dom_ms / dom_n / 1000.0) / 1e12
-    roof = {"kernel": dom_name, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp32_peak,
-            "traffic": FAN_NCU_QUADS["traffic"] if quads else FAN_NCU_TRAFFIC.get(dom_name),
-            "work": "2 flops per nonzero of K (%.4g nonzeros)" % nnz,
-            "peak_kind": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % sm_mhz}
-    wi = FAN_NCU_QUADS["warp_instr"] if quads else FAN_NCU_WARP_INSTR.get(dom_name)
-    if wi:
-        issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e12
-        issue = wi / (dom_ms / dom_n / 1000.0) / 1e12
-        roof["issue"] = {"achieved": issue, "peak": issue_peak, "unit": "Twarp-inst/s", "frac": issue / issue_peak,
-                         "warp_instructions_per_launch": wi,
-                         "peak_kind": "152 SMs x 4 schedulers x 1 warp-instruction/cycle x %.0f MHz (derived)"
-                                      % sm_mhz}
+    ncu_name = None
+    if dom_name == "joseph_gather":
+        ncu_name = "k_gather_fan" if args.fan_gather == "quads" else "k_gather_fan_lines"
+    roof = projector_roofline(dom_name, dom_ms / dom_n, nnz, peaks, dev, load_counters("fan512"), ncu_name)
     tot_ms = sum(t for t, _ in kern.values())
     kernels = {k: {"ms_per_launch": t / c if c else None, "launches": c, "share": t / tot_ms if tot_ms else None}
                for k, (t, c) in kern.items()}

@@ -436,8 +436,9 @@ int ncs_unet_inject_wait_timeout(ncs_unet* net);
  * default stream).  Asynchronous, apart from the host-to-device copy of the
  * angle table, which returns once the table is staged.
  * Sizes N > NCS_STATIC_MAX_N or n_angles > NCS_STATIC_MAX_ANGLES return
- * NCS_ERR_UNSUPPORTED; N < 8, null pointers or an empty geometry return
- * NCS_ERR_BADARG.  All calls share the array: calls whose work overlaps on the
+ * NCS_ERR_UNSUPPORTED, and so do a det_spacing in (0, 1) and the geometries that
+ * ncs_plan_create rejects with NCS_ERR_UNSUPPORTED; N < 8, null pointers or an
+ * empty geometry return NCS_ERR_BADARG.  All calls share the array: calls whose work overlaps on the
  * GPU (several streams or host threads) race and must be serialised by the
  * caller.  The first call on a device looks up the array's address with that
  * device current; make it before any stream capture. */

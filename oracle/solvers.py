@@ -246,6 +246,59 @@ def admm_textbook(P: Problem, n_iter: int, Ad: np.ndarray, x0=None, lam0=None, r
     return xs
 
 
+def explicit_inverse(AtA: np.ndarray) -> np.ndarray:
+    """(A^T A)^+ as an explicit dense matrix: the inverse through a Cholesky factor when
+    A^T A is positive definite, else the eigendecomposition pseudo-inverse (Sec. 2)."""
+    import scipy.linalg as sla
+    n = AtA.shape[0]
+    try:
+        c = sla.cho_factor(AtA, check_finite=False)
+        return sla.cho_solve(c, np.eye(n), check_finite=False)
+    except np.linalg.LinAlgError:
+        return np.linalg.pinv(AtA, hermitian=True)
+
+
+def admm_explicit(P: Problem, n_iter: int, AtA_inv: np.ndarray, x0=None, record=None):
+    """The textbook ADMM of admm_textbook (Appendix, "Derivation from ADMM"), CT only, with
+    A applied as the operators K and D (A = [K; (beta/alpha) D]) and the x-update through
+    an explicit dense (A^T A)^+:
+      z+ = prox_{(1/alpha) g}(A x - b - lambda)
+      x+ = (A^T A)^+ A^T (z+ + b + lambda)
+      lambda+ = lambda + z+ - A x+ + b
+    Returns the list of x iterates x^1..x^n (record(k, x) is called on each)."""
+    assert P.kind == "ct"
+    N = P.g.N
+    a = P.alpha
+    f = P.beta / P.alpha
+    x = np.zeros((N, N)) if x0 is None else np.array(x0, dtype=np.float64).reshape(N, N)
+    lu = np.zeros_like(P.b)
+    lh = np.zeros((N, N - 1))
+    lv = np.zeros((N - 1, N))
+    Kx = K(x, P.g)
+    dh, dv = D(x)
+    xs = []
+    for k in range(n_iter):
+        zu = (Kx - P.b - lu) / (1.0 + 1.0 / a)           # prox of (1/alpha) * 1/2||.||^2
+        t = P.lam / P.beta                                # (1/alpha) * lam alpha / beta
+        wh, wv = f * dh - lh, f * dv - lv
+        if P.tv == "aniso":
+            zh, zv = prox.soft(wh, t), prox.soft(wv, t)
+        else:
+            ph, pv = prox.soft_iso(_pad_h(wh), _pad_v(wv), t)
+            zh, zv = ph[:, :-1], pv[:-1, :]
+        rhs = KT(zu + P.b + lu, P.g) + f * DT(zh + lh, zv + lv)
+        x = (AtA_inv @ rhs.ravel()).reshape(N, N)
+        Kx = K(x, P.g)
+        dh, dv = D(x)
+        lu = lu + zu - Kx + P.b
+        lh = lh + zh - f * dh
+        lv = lv + zv - f * dv
+        xs.append(x.copy())
+        if record is not None:
+            record(k, x)
+    return xs
+
+
 def admm_pcg(P: Problem, n_iter: int, n_cg: int, Minv, x0=None, record=None):
     """ADMM in the textbook form of admm_textbook (Appendix, "Derivation from ADMM"),
     CT only, with the x-update (A^T A) x = A^T (z+ + b + lambda) solved approximately

@@ -10,7 +10,9 @@
 // It needs no plan and calls no allocating routine.
 //
 // Limits: image side N <= NCS_STATIC_MAX_N (512), n_angles <= NCS_STATIC_MAX_ANGLES
-// (2048); larger sizes are rejected with NCS_ERR_UNSUPPORTED.  The array
+// (2048); larger sizes are rejected with NCS_ERR_UNSUPPORTED, and so is a det_spacing
+// in (0, 1) (the gather needs rays at least a pixel apart) or a geometry outside the
+// range of ncs_plan_create.  The array
 // (about 4.1 MiB) lives on every GPU that loads the library until the process
 // exits.  Every call shares it, so calls whose work overlaps on the GPU (two
 // streams, or two host threads) race; serialise them.  The first call on a
@@ -116,8 +118,8 @@ bool angle_table(const ncs_geometry* geom, int N, std::vector<AngleParam>& ap)
 
 extern "C" int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float* y, float* x, void* cuda_stream)
 {
-    if (!geom || !y || !x || geom->n_angles < 1 || geom->n_det < 1) return NCS_ERR_BADARG;
-    if (N < 8 || N > NCS_STATIC_MAX_N || geom->n_angles > NCS_STATIC_MAX_ANGLES) return NCS_ERR_UNSUPPORTED;
+    if (!geom || !y || !x || geom->n_angles < 1 || geom->n_det < 1 || N < 8) return NCS_ERR_BADARG;
+    if (N > NCS_STATIC_MAX_N || geom->n_angles > NCS_STATIC_MAX_ANGLES) return NCS_ERR_UNSUPPORTED;
     if (geom->det_spacing != 0.0 && !(geom->det_spacing >= 1.0)) return NCS_ERR_UNSUPPORTED;
     std::vector<AngleParam> ap;
     if (!angle_table(geom, N, ap)) return NCS_ERR_UNSUPPORTED;

@@ -244,6 +244,10 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
     __shared__ __align__(8) unsigned long long full[TC_S], empty[TC_S], done;
     __shared__ uint32_t s_taddr;
     __shared__ volatile int s_fail;
+    // stages whose copies the producer issued, stages whose MMAs were issued, and whether the
+    // MMA lane committed its MMAs to `done`: on a failed wait the block drains exactly these
+    // before it reads or frees tensor memory
+    __shared__ volatile int s_issued, s_consumed, s_committed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int BN = a.BN;
     const int kcm = min(TC_KC, a.Cin);                 // channels a stage holds at most
@@ -254,6 +258,9 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
     const int y0 = p0 / a.W, x0 = p0 - y0 * a.W;
     if (tid == 0) {
         s_fail = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        s_committed = 0;
         for (int s = 0; s < TC_S; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
@@ -278,6 +285,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
             for (int it = 0; it < stages; ++it) {
                 const int s = it % TC_S;
                 if (it >= TC_S && !tc_wait(smem_u32(&empty[s]), (uint32_t)((it / TC_S) - 1) & 1u, a.wait_limit)) {
+                    __threadfence_block();
                     s_fail = 1;
                     break;
                 }
@@ -293,6 +301,7 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
                     tma_load_3d(As + (uint32_t)g * 2048u, &tin, c0 + 8 * g, x0 + dx, y0 + dy, fb);
                     tma_load_2d(Bs + (uint32_t)g * (uint32_t)BN * 16u, &tw, kk * a.Cin + c0 + 8 * g, co0, fb);
                 }
+                s_issued = it + 1;
             }
         }
         __syncwarp();
@@ -300,14 +309,18 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
         if (lane == 0) {
             // MMA issuer: K = 16 slabs of each stage into the TMEM accumulator
             const uint32_t idesc = tc_idesc(TC_M, BN);
-            bool ok = true;
             for (int it = 0; it < stages; ++it) {
                 const int s = it % TC_S;
+                if (s_fail) {
+                    // the producer gave up: no copies beyond the ones it issued will come
+                    __threadfence_block();
+                    if (it >= s_issued) break;
+                }
                 if (!tc_wait(smem_u32(&full[s]), (uint32_t)(it / TC_S) & 1u, a.wait_limit)) {
                     s_fail = 1;
-                    ok = false;
                     break;
                 }
+                s_consumed = it + 1;
                 if (a.no_mma) continue;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int kk = it / nch, c0 = (it - kk * nch) * TC_KC;
@@ -325,13 +338,25 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(smem_u32(&empty[s])) : "memory");
             }
-            if (ok && !a.no_mma)
+            // `done` tracks every MMA this lane issued, also after a failed wait, so that the
+            // block can wait for them before it frees tensor memory (the failure-path test
+            // issues none and leaves `done` alone, so its waits run out)
+            if (!a.no_mma) {
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(smem_u32(&done)) : "memory");
+                s_committed = 1;
+            }
         }
         __syncwarp();
     }
-    if (tid == 0 && !s_fail && !tc_wait(smem_u32(&done), 0u, a.wait_limit)) s_fail = 1;
+    __syncthreads();
+    if (tid == 0) {
+        // drain: the MMAs issued (committed to `done`), then the copies issued but never consumed
+        // (their `full` phases); both end because the hardware completes work already issued
+        if (!s_committed || !tc_wait(smem_u32(&done), 0u, a.wait_limit)) s_fail = 1;
+        for (int it = s_consumed; it < s_issued; ++it)
+            if (!tc_wait(smem_u32(&full[it % TC_S]), (uint32_t)(it / TC_S) & 1u, a.wait_limit)) s_fail = 1;
+    }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (!s_fail) {

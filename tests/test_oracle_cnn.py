@@ -49,10 +49,13 @@ def test_pool_up_adjoints():
 
 
 def test_bf16_rounding():
+    # bfloat16 keeps 8 significant bits: its ulp at 1 is 2^-7
     assert cnn.bf16(1.0) == 1.0
-    assert cnn.bf16(1.0 + 2.0 ** -9) == 1.0                   # tie -> even
-    assert cnn.bf16(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7   # tie -> even (up)
-    assert cnn.bf16(1.0 + 2.0 ** -8) == 1.0 + 2.0 ** -7 or cnn.bf16(1.0 + 2.0 ** -8) == 1.0
+    assert cnn.bf16(1.0 + 2.0 ** -9) == 1.0                   # a quarter ulp: down
+    assert cnn.bf16(1.0 + 3 * 2.0 ** -9) == 1.0 + 2.0 ** -7   # three quarters of an ulp: up
+    assert cnn.bf16(1.0 + 2.0 ** -8) == 1.0                   # a tie: to the even neighbour, down
+    assert cnn.bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6   # a tie: to the even neighbour, up
+    assert cnn.bf16(-(1.0 + 2.0 ** -8)) == -1.0               # ties to even on the negative side too
 
 
 @pytest.mark.parametrize("levels,base,H", [(2, 2, 8), (3, 2, 8)])

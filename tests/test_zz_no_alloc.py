@@ -1,8 +1,9 @@
 """ncs_apply_KT_static: the backprojection for callers that cannot allocate
 device memory (it takes its working memory from a static device array instead
 of a plan).  Checked through the C ABI against the plan-based ncs_apply_KT on
-two calls in a row, within the operator tolerance of the other tests, and for
-its size limit.  Kept in its own file, collected last."""
+two calls in a row, and against the FP64 oracle's K^T, within the operator
+tolerance of the other tests, and for its size limits and status codes.  Kept in
+its own file, collected last."""
 import ctypes
 
 import numpy as np
@@ -25,9 +26,11 @@ def _geom(binding, na, nd):
 def test_static_backprojection_matches_plan_on_two_calls(N, na, nd):
     import paper_1810_13100_gb300 as ncs
     from paper_1810_13100_gb300 import binding
+    from oracle import operators as oop
     L = binding.load_library()
     plan = ncs.Plan(N, na, nd, 0.01, 1.0, power_max_iter=2)
     g = _geom(binding, na, nd)
+    og = oop.Geometry(N, na, nd)
     gen = torch.Generator(device="cuda").manual_seed(11)
     for call in range(2):
         y = torch.rand(na * nd, device="cuda", generator=gen) * 2 - 1
@@ -42,6 +45,9 @@ def test_static_backprojection_matches_plan_on_two_calls(N, na, nd):
         r = ref.double().cpu().numpy()
         assert np.all(np.isfinite(a))
         assert np.linalg.norm(a - r) <= TOL * np.linalg.norm(r), call
+        # the same product from the FP64 oracle on the same float32 sinogram
+        o = oop.KT(y.double().cpu().numpy().reshape(na, nd), og).ravel()
+        assert np.linalg.norm(a - o) <= TOL * np.linalg.norm(o), call
     plan.close()
 
 
@@ -54,4 +60,8 @@ def test_static_backprojection_rejects_sizes_beyond_its_limit():
     assert L.ncs_apply_KT_static(ctypes.byref(g), 768, p, p, None) == binding.NCS_ERR_UNSUPPORTED
     g2 = _geom(binding, 4096, 10)
     assert L.ncs_apply_KT_static(ctypes.byref(g2), 64, p, p, None) == binding.NCS_ERR_UNSUPPORTED
+    assert L.ncs_apply_KT_static(ctypes.byref(g), 4, p, p, None) == binding.NCS_ERR_BADARG
+    g3 = _geom(binding, 8, 10)
+    g3.det_spacing = 0.5
+    assert L.ncs_apply_KT_static(ctypes.byref(g3), 64, p, p, None) == binding.NCS_ERR_UNSUPPORTED
     assert L.ncs_apply_KT_static(None, 64, p, p, None) == binding.NCS_ERR_BADARG
