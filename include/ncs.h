@@ -101,6 +101,11 @@ typedef struct {
     int fan_gather;        /* fan-beam plans only, the K^T kernel: 0 (default) or 2: ray-driven 32 x 32 tiles,
                               1: pixel-driven 2 x 2 quads (both exact transposes); with autotune = 1 the plan
                               times both and keeps the faster */
+    int pdhg_only;         /* 1: the plan serves PDHG (eq. (PDHG)) and the operator entry points only: M's
+                              eigenvalues, the probes of eq. (H-fan) and the (A3) power iteration are
+                              skipped at creation (PDHG needs only lambda_max(A^T A)); ncs_step, ncs_solve,
+                              admm_solve, ncs_apply_Minv, ncs_get_mu and ncs_batch_create then return
+                              NCS_ERR_UNSUPPORTED for it, and its report's rho is NaN.  0 (default): full plan */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */
@@ -117,7 +122,7 @@ typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and so
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
  * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
- * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0, fan_gather 0. */
+ * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0, fan_gather 0, pdhg_only 0. */
 void ncs_options_default(ncs_options* opt);
 
 /* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).

@@ -56,7 +56,7 @@ class Options(ctypes.Structure):
                 ("a3_margin", ctypes.c_double), ("power_max_iter", ctypes.c_int), ("power_tol", ctypes.c_double),
                 ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("autotune", ctypes.c_int), ("warm_dual", ctypes.c_int), ("h_probes", ctypes.c_int),
-                ("fan_gather", ctypes.c_int)]
+                ("fan_gather", ctypes.c_int), ("pdhg_only", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -200,7 +200,7 @@ class Plan:
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
                  power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
                  det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False, warm_dual=False,
-                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0, fan_gather="auto"):
+                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0, fan_gather="auto", pdhg_only=False):
         import torch
         L = load_library()
         self._L = L
@@ -244,6 +244,7 @@ class Plan:
         o.warm_dual = 1 if warm_dual else 0
         o.h_probes = int(h_probes)
         o.fan_gather = {"auto": 0, "quads": 1, "lines": 2}[fan_gather]
+        o.pdhg_only = 1 if pdhg_only else 0
         # With no stream given, the plan runs on a side stream that is ordered
         # after torch's current stream on entry to every call and before it on
         # exit, so results are visible to torch without extra synchronisation.

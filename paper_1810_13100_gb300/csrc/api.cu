@@ -40,6 +40,63 @@ namespace ncs {
 // beta_a + gamma_t and s = R sin(gamma_t) (every quantity in FP64, rounded once), stepped over
 // rows when |cos theta| >= |sin theta| with the parallel beam's crossing, interpolation and
 // path length.
+// Parallel beam (Sec. 2, eq. (radon-def)): ray t of angle theta is u cos + v sin = s_t with
+// s_t = (t - (n_det-1)/2) ds + offset.  Stepped over rows (|cos| >= |sin|; ties, decided
+// exactly on the integer angle index for the default angles, step over rows) it crosses row j
+// at column f = (s_t - v_j sin)/cos + (N-1)/2; stepped over columns it crosses column i at row
+// f = (N-1)/2 - (s_t - u_i cos)/sin.  Both are f = A t + B q + C, rounded once to 32.32 fixed point.
+bool angle_table(int N, int na, int nd, double ds, double offset, const double* angles, std::vector<AngleParam>& ap)
+{
+    const double cN = 0.5 * (N - 1);
+    const double s0 = -0.5 * (nd - 1) * ds + offset;
+    const double two32 = 4294967296.0;
+    ap.resize(na);
+    for (int a = 0; a < na; ++a) {
+        double th, c, sn;
+        int row;
+        if (angles) {
+            th = angles[a];
+            if (!std::isfinite(th)) return false;
+            c = std::cos(th);
+            sn = std::sin(th);
+            row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
+        } else {
+            th = a * M_PI / na;
+            c = std::cos(th);
+            sn = std::sin(th);
+            row = (4 * a <= na || 4 * a >= 3 * na) ? 1 : 0;   // exact test; ties step over rows
+        }
+        double A, B, C, W, invA;
+        if (row) {
+            A = ds / c;
+            B = sn / c;
+            C = (s0 - cN * sn) / c + cN;
+            W = 1.0 / std::fabs(c);
+            invA = c / ds;
+        } else {
+            A = -ds / sn;
+            B = c / sn;
+            C = cN - (s0 + cN * c) / sn;
+            W = 1.0 / std::fabs(sn);
+            invA = -sn / ds;
+        }
+        // every crossing evaluated (rays a tile's width beyond the detector included) stays
+        // well inside the 32.32 range
+        if (!(std::fabs(A) * (nd + 64.0) + std::fabs(B) * (N + 64.0) + std::fabs(C) < 1073741824.0)) return false;
+        AngleParam& q = ap[a];
+        q.Ai = std::llround(A * two32);
+        q.Bi = std::llround(B * two32);
+        q.Ci = std::llround(C * two32);
+        q.Af = (float)A;
+        q.Bf = (float)B;
+        q.Cf = (float)C;
+        q.W = (float)W;
+        q.invA = (float)invA;
+        q.row = row;
+    }
+    return true;
+}
+
 bool fan_ray_tables(int N, int na, int nd, double R, double pitch, double offset, const double* views_in,
                     std::vector<FanRay>& rays, std::vector<float>& rayw, std::vector<FanView>& views,
                     std::vector<double>* geo)
@@ -107,6 +164,8 @@ struct ncs_plan {
     bool own_stream = false;
     std::vector<AngleParam> h_ap;
     AngleParam* d_ap = nullptr;
+    int* d_order = nullptr;          // angle indices, row-branch ones first (the gather's work split)
+    int n_row = 0;
     // fan beam (ncs_plan_create_fan): per-ray coefficients, signed path lengths, views
     bool fan = false;
     std::vector<FanRay> h_rays;
@@ -290,6 +349,8 @@ int enq_gather(ncs_plan* p, int mode, const void* u, const void* v, float dscale
     GatherArgs g{};
     g.u = u;
     g.ap = p->d_ap;
+    g.order = p->d_order;
+    g.n_row = n_ang > 0 ? p->n_row : 0;      // n_ang is p->na, or 0 for D^T / kappa s alone
     g.rays = p->d_rays;
     g.rayw = p->d_rayw;
     g.views = p->d_views;
@@ -588,7 +649,7 @@ void free_plan(ncs_plan* p)
     p->recs.clear();
     p->ev_pool.clear();
     if (p->graph.exec) cudaGraphExecDestroy(p->graph.exec);
-    cudaFree(p->d_ap); cudaFree(p->d_rays); cudaFree(p->d_rayw); cudaFree(p->d_views); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
+    cudaFree(p->d_ap); cudaFree(p->d_order); cudaFree(p->d_rays); cudaFree(p->d_rayw); cudaFree(p->d_views); cudaFree(p->d_tw); cudaFree(p->d_invmu); cudaFree(p->d_mu);
     cudaFree(p->d_xbar); cudaFree(p->d_r); cudaFree(p->d_tmp);
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
@@ -659,8 +720,6 @@ int open_stream(ncs_plan* p)
     return NCS_OK;
 }
 
-// X = X_hi + X_lo with X_hi a multiple of 2^-10 (see AngleParam)
-double split_hi(double X) { return std::nearbyint(X * 1024.0) / 1024.0; }
 
 // Fan-beam rays (Sec. 4, fan beam geometry; equiangular detector): view a puts the source at
 // S_a = R (-sin beta_a, cos beta_a); channel t is the ray leaving S_a at the fan angle
@@ -700,66 +759,14 @@ int build_plan(ncs_plan* p, const ncs_geometry* geom)
     // per-angle Joseph coefficients in FP64, rounded once
     const double ds = (geom->det_spacing > 0.0) ? geom->det_spacing : 1.0;
     p->ds = ds;
-    const double cN = 0.5 * (N - 1);
-    const double s0 = -0.5 * (nd - 1) * ds + geom->det_offset;
-    p->h_ap.resize(na);
-    for (int a = 0; a < na; ++a) {
-        double th, c, sn;
-        int row;
-        if (geom->angles) {
-            th = geom->angles[a];
-            c = std::cos(th);
-            sn = std::sin(th);
-            row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
-        } else {
-            th = a * M_PI / na;
-            c = std::cos(th);
-            sn = std::sin(th);
-            row = (4 * a <= na || 4 * a >= 3 * na) ? 1 : 0;   // exact test; ties step over rows
-        }
-        double A, B, C, W, invA;
-        if (row) {
-            // column index where ray t crosses row j: u = (s_t - v_j sin)/cos, f = u + cN
-            A = ds / c;
-            B = sn / c;
-            C = (s0 - cN * sn) / c + cN;
-            W = 1.0 / std::fabs(c);
-            invA = c / ds;
-        } else {
-            // row index where ray t crosses column i: v = (s_t - u_i cos)/sin, f = cN - v
-            A = -ds / sn;
-            B = c / sn;
-            C = cN - (s0 + cN * c) / sn;
-            W = 1.0 / std::fabs(sn);
-            invA = -sn / ds;
-        }
-        AngleParam& q = p->h_ap[a];
-        auto hi = [](double X) { return split_hi(X); };
-        q.Ahi = (float)hi(A);
-        q.Alo = (float)(A - hi(A));
-        q.Bhi = (float)hi(B);
-        q.Blo = (float)(B - hi(B));
-        q.Chi = (float)hi(C);
-        q.Clo = (float)(C - hi(C));
-        q.W = (float)W;
-        q.invA = (float)invA;
-        // H = A_hi t + B_hi q + C_hi is exact only while every partial sum stays below 2^14
-        if (std::fabs(hi(A)) * (nd - 1) + std::fabs(hi(B)) * (N - 1) + std::fabs(hi(C)) >= 16384.0)
-            return NCS_ERR_UNSUPPORTED;
-        // the gather's two-phase shared-memory sums need consecutive rays to cross a line
-        // at least one pixel apart in FP32 as well: |A| exactly 1, or clear of 1 by twice the rounding of the
-        // difference of two evaluated crossings, 2 (1 + 2 L_max) 2^-24
-        {
-            const double Lmax = std::fabs(A - hi(A)) * (nd - 1) + std::fabs(B - hi(B)) * (N - 1) +
-                                std::fabs(C - hi(C));
-            const double tol = 2.0 * 2.0 * (1.0 + 2.0 * Lmax) * std::ldexp(1.0, -24);
-            if (std::fabs(A) != 1.0 && std::fabs(A) < 1.0 + tol) return NCS_ERR_UNSUPPORTED;
-        }
-        q.row = row;
-        q.pad0 = q.pad1 = q.pad2 = 0;
-    }
+    if (!angle_table(N, na, nd, ds, geom->det_offset, geom->angles, p->h_ap)) return NCS_ERR_UNSUPPORTED;
     CKS(dalloc(&p->d_ap, na));
     CK(cudaMemcpyAsync(p->d_ap, p->h_ap.data(), na * sizeof(AngleParam), cudaMemcpyHostToDevice, p->st));
+    std::vector<int> order;
+    angle_order(p->h_ap, order, &p->n_row);
+    CKS(dalloc(&p->d_order, na));
+    CK(cudaMemcpyAsync(p->d_order, order.data(), na * sizeof(int), cudaMemcpyHostToDevice, p->st));
+    CK(cudaStreamSynchronize(p->st));
     return build_common(p);
 }
 
@@ -804,6 +811,11 @@ int build_common(ncs_plan* p)
         return NCS_ERR_NOMEM;
     }
     if (td_num_blocks(N) > kMaxPartials) return NCS_ERR_UNSUPPORTED;
+    if (p->opt.pdhg_only) {
+        // PDHG needs no M: no eigenvalues, probes or (A3) power iteration
+        if (p->opt.autotune) CKS(autotune_plan(p));
+        return NCS_OK;
+    }
     // DC of H_R: ||K 1||^2 / ||1||^2 unless given
     if (std::isnan(p->h_dc)) {
         float* ones = p->d_tmp;
@@ -859,6 +871,13 @@ int build_common(ncs_plan* p)
 }
 
 int check_plan(const ncs_plan* p) { return p ? NCS_OK : NCS_ERR_BADARG; }
+
+// Entry points that need M: refused for a plan created with pdhg_only.
+int check_plan_m(const ncs_plan* p)
+{
+    if (!p) return NCS_ERR_BADARG;
+    return p->opt.pdhg_only ? NCS_ERR_UNSUPPORTED : NCS_OK;
+}
 
 // Time `reps` launches of fn on the plan's stream (ms per launch, CUDA events).
 template <class F>
@@ -939,6 +958,12 @@ int autotune_plan(ncs_plan* p)
         if (ms < best) { best = ms; best_parts = cand[c]; }
     }
     p->gparts = best_parts;
+    if (p->opt.pdhg_only) {            // no M: the FFT solve is never run
+        cudaFree(y);
+        cudaFree(xo);
+        cudaFree(xo2);
+        return rc;
+    }
     // FFT radix orders
     RadixPlan rp0 = p->rp, best_rp = p->rp;
     std::vector<int> r(rp0.r, rp0.r + rp0.n);
@@ -1233,6 +1258,7 @@ int new_plan(int nx, int ny, int n_angles, int n_det, double lambda, double alph
     if (o.nonneg && o.data != NCS_DATA_KL) return NCS_ERR_BADARG;
     if (o.warm_dual && o.prec != NCS_FP32) return NCS_ERR_BADARG;
     if (o.power_max_iter < 1 || !(o.power_tol >= 0.0)) return NCS_ERR_BADARG;
+    if (o.pdhg_only != 0 && o.pdhg_only != 1) return NCS_ERR_BADARG;
     RadixPlan rp;
     if (nx % 2 != 0 || nx > 4096 || !factor_radices(nx, &rp)) return NCS_ERR_UNSUPPORTED;
     ncs_plan* p = new (std::nothrow) ncs_plan();
@@ -1290,6 +1316,7 @@ void ncs_options_default(ncs_options* o)
     o->warm_dual = 0;
     o->h_probes = 0;
     o->fan_gather = 0;
+    o->pdhg_only = 0;
 }
 
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,
@@ -1366,7 +1393,7 @@ void ncs_plan_destroy(ncs_plan* p)
 
 int ncs_step(ncs_plan* p, float* x, float* u, float* v, float* s, const float* b, const float* bg, int n_iter)
 {
-    CKS(check_plan(p));
+    CKS(check_plan_m(p));
     if (!x || !u || !v || !b || n_iter < 1) return NCS_ERR_BADARG;
     if (p->nonneg && !s) return NCS_ERR_BADARG;
     if (!p->kl && bg) return NCS_ERR_BADARG;
@@ -1390,7 +1417,7 @@ int pdhg_step(ncs_plan* p, float* x, float* u, float* v, float* s, const float* 
 int ncs_solve(ncs_plan* p, const float* b, const float* bg, float* x, double tol, int max_iter, double f_star,
               ncs_report* rep)
 {
-    CKS(check_plan(p));
+    CKS(check_plan_m(p));
     return solve_common(p, 0, b, bg, x, tol, max_iter, f_star, rep);
 }
 
@@ -1404,7 +1431,7 @@ int pdhg_solve(ncs_plan* p, const float* b, const float* bg, float* x, double to
 int admm_solve(ncs_plan* p, const float* b, float* x, double tol, int max_outer, int n_cg, double f_star,
                ncs_report* rep)
 {
-    CKS(check_plan(p));
+    CKS(check_plan_m(p));
     return admm_common(p, b, x, tol, max_outer, n_cg, f_star, rep);
 }
 
@@ -1475,7 +1502,7 @@ int ncs_fbp(ncs_plan* p, const float* b, float* x)
 
 int ncs_apply_Minv(ncs_plan* p, const float* r, float* out)
 {
-    CKS(check_plan(p));
+    CKS(check_plan_m(p));
     if (!r || !out) return NCS_ERR_BADARG;
     CK(cudaSetDevice(p->dev));
     return enq_solve(p, r, p->d_invmu, 1, nullptr, nullptr, out);
@@ -1495,7 +1522,7 @@ int ncs_objective(ncs_plan* p, const float* x, const float* b, const float* bg, 
 
 int ncs_get_mu(ncs_plan* p, double* mu_host)
 {
-    CKS(check_plan(p));
+    CKS(check_plan_m(p));
     if (!mu_host) return NCS_ERR_BADARG;
     memcpy(mu_host, p->mu.data(), p->mu.size() * sizeof(double));
     return NCS_OK;
@@ -1527,6 +1554,7 @@ int ncs_batch_create(ncs_plan* const* plans, int n_plans, ncs_batch** out)
     if (!plans || n_plans < 1) return NCS_ERR_BADARG;
     for (int i = 0; i < n_plans; ++i) {
         if (!plans[i]) return NCS_ERR_BADARG;
+        if (plans[i]->opt.pdhg_only) return NCS_ERR_UNSUPPORTED;
         if (plans[i]->dev != plans[0]->dev) return NCS_ERR_BADARG;
         for (int j = 0; j < i; ++j)
             if (plans[j] == plans[i]) return NCS_ERR_BADARG;
@@ -1791,17 +1819,9 @@ int ncs_plan_nnz(ncs_plan* p, double* nnz)
         for (int a = 0; a < (p->fan ? 0 : p->na); ++a) {
             const AngleParam& q = p->h_ap[a];
             for (int t = 0; t < p->nd; ++t) {
-                const float tf = (float)t;
-                const float Hr = std::fma(q.Ahi, tf, q.Chi);
                 for (int j = 0; j < N; ++j) {
-                    const float jf = (float)j;
-                    const float H = std::fma(q.Bhi, jf, Hr);
-                    const float L = std::fma(q.Alo, tf, std::fma(q.Blo, jf, q.Clo));
-                    const float Hi = std::floor(H);
-                    const float fr = (H - Hi) + L;
-                    const float fl = std::floor(fr);
-                    const float w = fr - fl;
-                    const int i0 = (int)(Hi + fl);
+                    int i0;
+                    const float w = fix_weight(q.Ai * t + q.Bi * j + q.Ci, i0);
                     if (i0 >= 0 && i0 < N && 1.0f - w != 0.0f) cnt += 1.0;
                     if (i0 + 1 >= 0 && i0 + 1 < N && w != 0.0f) cnt += 1.0;
                 }

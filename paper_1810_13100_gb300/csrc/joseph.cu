@@ -31,15 +31,30 @@ namespace {
 constexpr int FWD_TB = 64;    // bins per block
 constexpr int FWD_SEG = 4;    // row segments per ray
 
-// Integer index k0 and interpolation weight w of the crossing f = H + L, where
-// H = A_hi t + B_hi q + C_hi is exact and L = A_lo t + (B_lo q + C_lo) is small.
-// The one expression both kernels use, so they hold the same FP32 matrix.
-__device__ __forceinline__ float split_weight(float H, float L, float& k0)
+// floor(v) for |v| < 2^22 on the FP32 pipe (no conversion instructions): v + 1.5 * 2^23
+// rounded toward -infinity is the integer floor(v) + 1.5 * 2^23, since floats in [2^23, 2^24)
+// are spaced 1 apart; subtracting 1.5 * 2^23 again is exact.  bits gets the sum's bit
+// pattern, which exceeds FLOOR_MAG_BITS by floor(v).
+constexpr float FLOOR_MAG = 12582912.0f;       // 1.5 * 2^23
+constexpr int FLOOR_MAG_BITS = 0x4B400000;      // its bit pattern
+__device__ __forceinline__ float floor_fp32(float v, int& bits)
 {
-    const float Hi = floorf(H);
+    const float m = __fadd_rd(v, FLOOR_MAG);
+    bits = __float_as_int(m);
+    return m - FLOOR_MAG;
+}
+
+// Integer index k0 and interpolation weight w of the crossing f = H + L, where
+// H = A_hi t + B_hi q + C_hi is exact and L = A_lo t + (B_lo q + C_lo) is small:
+// k0 = floor(H) + floor(frac(H) + L), w = (frac(H) + L) - that second floor.
+// The one expression every projector kernel uses, so they hold the same FP32 matrix.
+__device__ __forceinline__ float split_weight(float H, float L, int& k0)
+{
+    int bh, bf;
+    const float Hi = floor_fp32(H, bh);
     const float fr = (H - Hi) + L;
-    const float fl = floorf(fr);
-    k0 = Hi + fl;
+    const float fl = floor_fp32(fr, bf);
+    k0 = (bh - FLOOR_MAG_BITS) + (bf - FLOOR_MAG_BITS);
     return fr - fl;
 }
 
@@ -63,44 +78,41 @@ k_fwd(FwdArgs g)
     __shared__ double dred[FWD_TB];
     const int a = blockIdx.y;
     const int t = blockIdx.x * FWD_TB + threadIdx.x;
-    float Ahi, Alo, Bhi, Blo, Chi, Clo, Wr;
+    // FAN: the ray's split coefficients (see FanRay); parallel beam: the angle's 32.32 ones
+    float Bhi = 0.f, Blo = 0.f, Chi = 0.f, Clo = 0.f, Wr, B, f0 = 0.f;
+    long long Fi = 0, Bi = 0;
     int row;
+    const float ft = (float)t;
     if (FAN) {
         const size_t r = (size_t)a * g.n_det + min(t, g.n_det - 1);
         const float4 q = __ldg(g.rays + r);
         const float ws = __ldg(g.rayw + r);
-        Ahi = 0.0f;
-        Alo = 0.0f;
         Bhi = q.x;
         Blo = q.y;
         Chi = q.z;
         Clo = q.w;
         Wr = fabsf(ws);
         row = ws < 0.0f ? 0 : 1;
+        B = Bhi + Blo;
+        f0 = Chi + Clo;
     } else {
         const AngleParam p = g.ap[a];
-        Ahi = p.Ahi;
-        Alo = p.Alo;
-        Bhi = p.Bhi;
-        Blo = p.Blo;
-        Chi = p.Chi;
-        Clo = p.Clo;
         Wr = p.W;
         row = p.row;
+        B = p.Bf;
+        f0 = fmaf(p.Af, ft, p.Cf);
+        Fi = p.Ai * (long long)t + p.Ci;       // crossing of line 0, 32.32
+        Bi = p.Bi;
     }
     const void* im2 = row ? g.img2 : g.imgT2;
     const int pitch = pair_pitch(g.N);
     const int N = g.N;
     float acc = 0.0f;
     if (t < g.n_det) {
-        const float ft = (float)t;
-        const float Hr = FAN ? Chi : fmaf(Ahi, ft, Chi);    // exact
-        const float B = Bhi + Blo;
         // Rows where the ray can touch the image: f in [-1, N).  Found in FP32
         // with a 2-row margin (|B| <= 1, so f stays in (-4, N + 3) on every
         // processed row and the pair image's zero border absorbs the steps
         // outside the image).
-        const float f0 = Hr + (FAN ? Clo : fmaf(Alo, ft, Clo));
         int jlo = 0, jhi = N;
         if (fabsf(B) > 1e-6f) {
             float j1 = (-1.0f - f0) / B, j2 = ((float)N - f0) / B;
@@ -116,15 +128,27 @@ k_fwd(FwdArgs g)
         const int chunk = (len + FWD_SEG - 1) / FWD_SEG;
         const int js = jlo + threadIdx.y * chunk;
         const int je = min(jhi, js + chunk);
-        for (int j = js; j < je; ++j) {
-            const float jf = (float)j;
-            float k0f;
-            const float w = FAN ? split_weight(fmaf(Bhi, jf, Chi), fmaf(Blo, jf, Clo), k0f)
-                                : split_weight(fmaf(Bhi, jf, Hr), fmaf(Alo, ft, fmaf(Blo, jf, Clo)), k0f);
-            const int i0 = (int)k0f;
-            const float2 xv = St<PBF>::ld2(im2, (size_t)j * pitch + PAIR_PAD + i0);
-            acc = fmaf(1.0f - w, xv.x, acc);
-            acc = fmaf(w, xv.y, acc);
+        if (FAN) {
+            for (int j = js; j < je; ++j) {
+                const float jf = (float)j;
+                int i0;
+                const float w = split_weight(fmaf(Bhi, jf, Chi), fmaf(Blo, jf, Clo), i0);
+                const float2 xv = St<PBF>::ld2(im2, (size_t)j * pitch + PAIR_PAD + i0);
+                acc = fmaf(1.0f - w, xv.x, acc);
+                acc = fmaf(w, xv.y, acc);
+            }
+        } else {
+            long long F = Fi + Bi * (long long)js;
+            const char* rowp = static_cast<const char*>(im2) + ((size_t)js * pitch + PAIR_PAD) * 2 * St<PBF>::bytes;
+            for (int j = js; j < je; ++j) {
+                int i0;
+                const float w = fix_weight(F, i0);
+                const float2 xv = St<PBF>::ld2(rowp, i0);
+                acc = fmaf(1.0f - w, xv.x, acc);
+                acc = fmaf(w, xv.y, acc);
+                F += Bi;
+                rowp += (size_t)pitch * 2 * St<PBF>::bytes;
+            }
         }
     }
     red[threadIdx.y][threadIdx.x] = acc;
@@ -176,120 +200,10 @@ k_fwd(FwdArgs g)
     }
 }
 
-constexpr int GT = 32;     // gather tile side (pixels)
-constexpr int GW = 8;      // warps per gather block
-
-// Per line pair (2p, 2p + 1) of a tile for one angle: the exact B_hi q + C_hi and the
-// remainder B_lo q + C_lo of both lines, the first ray that can reach either line, and
-// the first line's index.
-struct PairEntry {
-    float4 h;      // Hq, Lq of line 2p; Hq, Lq of line 2p + 1
-    int tl, line, pad0, pad1;
-};
-
-// All (ray, line) pairs of one angle that reach a 32 x 32 tile, accumulated by
-// one warp into its private shared-memory tile A.  ROW: the angle steps over
-// image rows (line = row, window along columns); otherwise over columns.  o0 is
-// the tile's first index along the interpolation axis.  Each lane takes one ray
-// on two adjacent lines (one load of u and W u serve both weights); lanes take
-// consecutive rays of a line pair, so the loads of u coalesce.  A pixel receives at
-// most one "right" weight (1 - w) and one "left" weight w per angle (rays of one
-// angle cross a line at least a pixel apart), and the two lines of a pair are
-// different rows of A, so the two phases never write one address twice.  CHECK:
-// test the line and ray ranges (edge tiles and rays beyond the detector).
-template <bool ROW, bool CHECK, bool SBF>
-__device__ __forceinline__ void gather_pairs(const AngleParam& p, const void* ua, int n_det, int N,
-                                             int o0, int RPP, int lane, const PairEntry* tab, float (*A)[GT + 1])
-{
-    constexpr int NP = GT / 2;
-    int lo = lane / RPP, r = lane - lo * RPP;
-    const int steps = (NP * RPP + 31) / 32;
-    for (int it = 0; it < steps; ++it) {
-        float vR0 = 0.0f, vL0 = 0.0f, vR1 = 0.0f, vL1 = 0.0f;
-        int k0 = -2, k1 = -2;
-        if (lo < NP) {
-            const PairEntry e = tab[lo];
-            const int t = e.tl + r;
-            if (!CHECK || (unsigned)t < (unsigned)n_det) {
-                const float tf = (float)t;
-                const float Wu = p.W * St<SBF>::ld(ua, t);
-                float kf;
-                if (!CHECK || e.line < N) {
-                    const float w = split_weight(fmaf(p.Ahi, tf, e.h.x), fmaf(p.Alo, tf, e.h.y), kf);
-                    k0 = (int)kf - o0;
-                    vR0 = fmaf(-w, Wu, Wu);
-                    vL0 = w * Wu;
-                }
-                if (!CHECK || e.line + 1 < N) {
-                    const float w = split_weight(fmaf(p.Ahi, tf, e.h.z), fmaf(p.Alo, tf, e.h.w), kf);
-                    k1 = (int)kf - o0;
-                    vR1 = fmaf(-w, Wu, Wu);
-                    vL1 = w * Wu;
-                }
-            }
-        }
-        const int q0 = 2 * lo, q1 = q0 + 1;
-        if ((unsigned)k0 < (unsigned)GT) {
-            if (ROW) A[q0][k0] += vR0;
-            else A[k0][q0] += vR0;
-        }
-        if ((unsigned)k1 < (unsigned)GT) {
-            if (ROW) A[q1][k1] += vR1;
-            else A[k1][q1] += vR1;
-        }
-        __syncwarp();
-        if ((unsigned)(k0 + 1) < (unsigned)GT) {
-            if (ROW) A[q0][k0 + 1] += vL0;
-            else A[k0 + 1][q0] += vL0;
-        }
-        if ((unsigned)(k1 + 1) < (unsigned)GT) {
-            if (ROW) A[q1][k1 + 1] += vL1;
-            else A[k1 + 1][q1] += vL1;
-        }
-        __syncwarp();
-        r += 32;
-        while (r >= RPP) {
-            r -= RPP;
-            ++lo;
-        }
-    }
-}
-
-template <bool ROW, bool SBF>
-__device__ __forceinline__ void gather_angle(const AngleParam& p, const void* ua, int n_det, int N,
-                                             int o0, int l0, int lane, PairEntry* tab, float (*A)[GT + 1])
-{
-    constexpr int NP = GT / 2;
-    const float lf0 = (float)l0;
-    const float base0 = fmaf(p.Bhi, lf0, p.Chi) + fmaf(p.Blo, lf0, p.Clo);      // ~ B l0 + C
-    const float ta = ((float)o0 - 1.0f - base0) * p.invA;
-    const float tb = ((float)o0 + (float)GT - base0) * p.invA;
-    const float T0 = fminf(ta, tb) - 1e-3f;                                      // first ray of line l0
-    const float dT = -(p.Bhi + p.Blo) * p.invA;                                  // shift per line, |dT| <= 1
-    const int RPL = (int)ceilf((float)(GT + 1) * fabsf(p.invA) + 2e-3f) + 1;     // rays per line
-    const int RPP = RPL + 1;              // rays per line pair: the lines' first rays differ by <= 1
-    if (lane < NP) {
-        const int la = 2 * lane;
-        const int tla = (int)floorf(fmaf((float)la, dT, T0));
-        const int tlb = (int)floorf(fmaf((float)(la + 1), dT, T0));
-        const float lfa = (float)(l0 + la), lfb = lfa + 1.0f;
-        PairEntry e;
-        e.h = make_float4(fmaf(p.Bhi, lfa, p.Chi), fmaf(p.Blo, lfa, p.Clo),       // Hq exact
-                          fmaf(p.Bhi, lfb, p.Chi), fmaf(p.Blo, lfb, p.Clo));
-        e.tl = min(tla, tlb);
-        e.line = l0 + la;
-        e.pad0 = e.pad1 = 0;
-        tab[lane] = e;
-    }
-    __syncwarp();
-    // interior: every line inside the image and every ray on the detector
-    const int t_first = min(tab[0].tl, tab[NP - 1].tl);
-    const int t_last = max(tab[0].tl, tab[NP - 1].tl) + RPP - 1;
-    const bool inside = (l0 + GT <= N) && t_first >= 0 && t_last < n_det;
-    if (inside) gather_pairs<ROW, false, SBF>(p, ua, n_det, N, o0, RPP, lane, tab, A);
-    else gather_pairs<ROW, true, SBF>(p, ua, n_det, N, o0, RPP, lane, tab, A);
-    __syncwarp();
-}
+constexpr int GT = 32;             // gather tile side (pixels)
+constexpr int GW = 8;              // warps per gather block
+constexpr int GP = GT + 1;         // pitch of a warp tile
+constexpr int GU = 96;             // staged W u per warp: the rays one angle's walks visit (<= 2 GT + 2)
 
 // Gather epilogue for pixel (j, i) with K^T u summed in r: adds dscale D^T v and kappa s
 // (A^T of Sec. 4), then stores r (GATHER_R) or applies the PDHG primal update.
@@ -318,48 +232,132 @@ __device__ __forceinline__ void gather_epilogue(const GatherArgs& g, int j, int 
     }
 }
 
+// K^T for the parallel beam (no atomics on data).  A block owns a 32 x 32 pixel tile and a slice
+// z of the angles: entries z, z + P, z + 2P, ... of the list of row-branch angles and of the list
+// of column-branch angles (so that every slice holds angles of both branches); warps 0-3 take
+// the slice's row-branch angles, warps 4-7 its column-branch ones, round robin.  For one angle, lane l owns line l of the tile (row l, or
+// column l) and walks the tile's 32 positions along it in order, holding the 32 sums of its
+// line in registers across all its angles.  Rays are visited in order of their crossing with
+// the line, F = Ai t + Bi q + Ci in 32.32 fixed point (the forward kernel's exact expression,
+// so the two kernels hold the same matrix): the crossing at k0 with weight w puts (1 - w) W u_t
+// on position k0 and w W u_t on k0 + 1, and since rays cross a line at distinct k0 (|A| >= 1),
+// position k receives at most the w-part of the ray at k - 1 and the (1 - w)-part of the ray at
+// k; the walk advances to the next ray after taking a w-part.  W u of the warp's rays is staged
+// in shared memory per angle (zero beyond the detector).  At the end the warps write their lines
+// to shared tiles, summed per pixel in a fixed order; with several slices the last block of a
+// tile (an arrival counter) sums the slices in slice order.
 template <int MODE, bool SBF, bool IBF>
 __global__ void __launch_bounds__(GT * GW)
 k_gather(GatherArgs g)
 {
-    __shared__ float acc[GW][GT][GT + 1];
-    __shared__ PairEntry lines[GW][GT / 2];
+    __shared__ float tiles[GW][GT * GP];      // warp tiles: pixel (r, c) at r GP + c
+    __shared__ float su[GW][GU];
     __shared__ int s_last;
     const int N = g.N;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int i0 = blockIdx.x * GT, j0 = blockIdx.y * GT;
-    float (*A)[GT + 1] = acc[wid];
+    float* U = su[wid];
     if (g.iter && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *g.iter += 1ull;
-    for (int rr = 0; rr < GT; ++rr) A[rr][lane] = 0.0f;
-    __syncwarp();
-    // this block's slice of the angles; warps take whole angles round robin
+    const bool rowwarp = wid < GW / 2;
+    const int wsub = rowwarp ? wid : wid - GW / 2;
+    const int q = (rowwarp ? j0 : i0) + lane;       // this lane's line: a row, or a column
+    const int o0 = rowwarp ? i0 : j0;               // the tile's first position along it
+    const bool live = q < N;
+    float acc[GT];
+#pragma unroll
+    for (int k = 0; k < GT; ++k) acc[k] = 0.0f;
     const int P = gridDim.z, part = blockIdx.z;
-    const int a_beg = (int)(((long long)g.n_ang * part) / P);
-    const int a_end = (int)(((long long)g.n_ang * (part + 1)) / P);
-    for (int a = a_beg + wid; a < a_end; a += GW) {
-        const AngleParam p = g.ap[a];
+    // this warp's angles: entries part + P (wsub + 4 m) of its branch's list
+    const int n_row = min(max(g.n_row, 0), g.n_ang);
+    const int nb = rowwarp ? n_row : g.n_ang - n_row;
+    const int* ord = g.order + (rowwarp ? 0 : n_row);
+    for (int r = part + P * wsub; r < nb; r += P * (GW / 2)) {
+        const int a = __ldg(ord + r);
+        const AngleParam& pa = g.ap[a];
+        const long long Ai = __ldg(&pa.Ai), Bi = __ldg(&pa.Bi), Ci = __ldg(&pa.Ci);
+        const float Bf = __ldg(&pa.Bf), Cf = __ldg(&pa.Cf), W = __ldg(&pa.W), invA = __ldg(&pa.invA);
+        // walk order: increasing crossing, so t goes up when Ai > 0 and down when Ai < 0
+        const bool upw = Ai > 0;
+        const int dir = upw ? 1 : -1;
+        const long long step = upw ? Ai : -Ai;
+        // crossing of ray t relative to the tile's first position: G = Ai t + Bi q + Ci - o0 2^32
+        const long long Gq = Bi * (long long)q + Ci - ((long long)o0 << 32);
+        // the first ray in walk order whose crossing is >= -1 (it gives position 0 its w-part):
+        // the FP32 estimate of where the crossing is -1 is within 0.05 rays, so the rounded
+        // estimate is that ray or the one before it
+        const float c = fmaf(Bf, (float)q, Cf) - (float)o0;
+        const float tr = (-1.0f - c) * invA;
+        int t0 = upw ? __float2int_rd(tr + 0.05f) : __float2int_ru(tr - 0.05f);
+        long long G = Ai * (long long)t0 + Gq;
+        if ((int)(G >> 32) < -1) {
+            t0 += dir;
+            G += step;
+        }
+        // the lane visits at most GT + 1 rays from t0; stage W u for the warp's rays
+        int tlo = upw ? t0 : t0 - GT, thi = upw ? t0 + GT : t0;
+        if (!live) {
+            tlo = 0x3FFFFFFF;
+            thi = -0x3FFFFFFF;
+        }
+        const int Tmin = __reduce_min_sync(0xffffffffu, tlo);
+        const int Tmax = __reduce_max_sync(0xffffffffu, thi);
+        const int nU = min(Tmax - Tmin + 1, GU);     // <= 2 GT + 2: the bound never binds
         const void* ua = static_cast<const char*>(g.u) + (size_t)a * g.n_det * St<SBF>::bytes;
-        if (p.row) gather_angle<true, SBF>(p, ua, g.n_det, N, i0, j0, lane, lines[wid], A);
-        else gather_angle<false, SBF>(p, ua, g.n_det, N, j0, i0, lane, lines[wid], A);
+        for (int e = lane; e < nU; e += 32) {
+            const int t = Tmin + e;
+            U[e] = (t >= 0 && t < g.n_det) ? W * St<SBF>::ld(ua, t) : 0.0f;
+        }
+        __syncwarp();
+        if (live) {
+            int ui = t0 - Tmin;
+            int k0;
+            float w = fix_weight(G, k0);
+            float wu = U[ui];
+            float vr = fmaf(-w, wu, wu), vl = w * wu;
+            // branch-free: only the step to the next ray is conditional; the weight and W u of
+            // the current ray are recomputed at every position
+#pragma unroll
+            for (int k = 0; k < GT; ++k) {
+                const bool adv = k0 == k - 1;
+                acc[k] += adv ? vl : 0.0f;
+                if (adv) {
+                    G += step;
+                    ui += dir;
+                }
+                w = fix_weight(G, k0);
+                wu = U[ui];
+                vr = fmaf(-w, wu, wu);
+                vl = w * wu;
+                acc[k] += k0 == k ? vr : 0.0f;
+            }
+        }
+        __syncwarp();
+    }
+    // each warp's lines into its tile (row lanes along rows, column lanes along columns)
+    float* T = tiles[wid];
+#pragma unroll
+    for (int k = 0; k < GT; ++k) {
+        if (rowwarp) T[lane * GP + k] = acc[k];
+        else T[k * GP + lane] = acc[k];
     }
     __syncthreads();
     // sum the warp tiles in a fixed order; thread -> pixels (q*8 + wid, lane)
     float tot[GT / GW];
 #pragma unroll
-    for (int q = 0; q < GT / GW; ++q) {
-        const int rr = q * GW + wid;
+    for (int qq = 0; qq < GT / GW; ++qq) {
+        const int rr = qq * GW + wid;
         float sum = 0.0f;
 #pragma unroll
-        for (int w = 0; w < GW; ++w) sum += acc[w][rr][lane];
-        tot[q] = sum;
+        for (int w = 0; w < GW; ++w) sum += tiles[w][rr * GP + lane];
+        tot[qq] = sum;
     }
     if (P > 1) {
         // angle slices of this tile: the last block to arrive sums them in slice order
         const size_t NN = (size_t)N * N;
 #pragma unroll
-        for (int q = 0; q < GT / GW; ++q) {
-            const int j = j0 + q * GW + wid, i = i0 + lane;
-            if (j < N && i < N) g.part[(size_t)part * NN + (size_t)j * N + i] = tot[q];
+        for (int qq = 0; qq < GT / GW; ++qq) {
+            const int j = j0 + qq * GW + wid, i = i0 + lane;
+            if (j < N && i < N) g.part[(size_t)part * NN + (size_t)j * N + i] = tot[qq];
         }
         __threadfence();
         __syncthreads();
@@ -369,20 +367,20 @@ k_gather(GatherArgs g)
         if (!s_last) return;
         __threadfence();
 #pragma unroll
-        for (int q = 0; q < GT / GW; ++q) {
-            const int j = j0 + q * GW + wid, i = i0 + lane;
+        for (int qq = 0; qq < GT / GW; ++qq) {
+            const int j = j0 + qq * GW + wid, i = i0 + lane;
             float sum = 0.0f;
             if (j < N && i < N)
                 for (int pp = 0; pp < P; ++pp) sum += __ldcg(g.part + (size_t)pp * NN + (size_t)j * N + i);
-            tot[q] = sum;
+            tot[qq] = sum;
         }
         if (tid == 0) g.counters[tile] = 0;
     }
 #pragma unroll
-    for (int q = 0; q < GT / GW; ++q) {
-        const int j = j0 + q * GW + wid, i = i0 + lane;
+    for (int qq = 0; qq < GT / GW; ++qq) {
+        const int j = j0 + qq * GW + wid, i = i0 + lane;
         if (j >= N || i >= N) continue;
-        gather_epilogue<MODE, IBF>(g, j, i, tot[q]);
+        gather_epilogue<MODE, IBF>(g, j, i, tot[qq]);
     }
 }
 
@@ -391,9 +389,9 @@ constexpr int FQY = 8;     // so a block covers 32 columns x 16 rows
 
 // Weights that one crossing (integer part k0, fraction w) of a line puts on the two
 // positions p and p + 1 of that line: 1 - w where k0 is the position, w where k0 is one less.
-__device__ __forceinline__ void quad_weights(int p, float k0f, float w, float& c0, float& c1)
+__device__ __forceinline__ void quad_weights(int p, int k0, float w, float& c0, float& c1)
 {
-    const int d = p - (int)k0f;
+    const int d = p - k0;
     c0 = d == 0 ? 1.0f - w : (d == 1 ? w : 0.0f);
     c1 = d == -1 ? 1.0f - w : (d == 0 ? w : 0.0f);
 }
@@ -451,7 +449,8 @@ k_gather_fan(GatherArgs g)
                 const float l0 = row ? fj : fi;             // the quad's first line for this ray
                 const float l1 = l0 + 1.0f;
                 const int p0 = row ? i : j;                 // its first position along the line
-                float kA, kB, cA0, cA1, cB0, cB1;
+                int kA, kB;
+                float cA0, cA1, cB0, cB1;
                 const float wA = split_weight(fmaf(q.x, l0, q.z), fmaf(q.y, l0, q.w), kA);
                 const float wB = split_weight(fmaf(q.x, l1, q.z), fmaf(q.y, l1, q.w), kB);
                 quad_weights(p0, kA, wA, cA0, cA1);
@@ -597,10 +596,10 @@ k_gather_fan_lines(GatherArgs g)
                 int sidx = (lane * 11) % n;
                 for (int k = 0; k < n; ++k) {
                     const int e = s0 + sidx;
-                    float k0f;
-                    const float w = split_weight(fmaf(S[0][e], lf, S[2][e]), fmaf(S[1][e], lf, S[3][e]), k0f);
+                    int k0;
+                    const float w = split_weight(fmaf(S[0][e], lf, S[2][e]), fmaf(S[1][e], lf, S[3][e]), k0);
                     const float Wu = S[4][e];
-                    const int kk = (int)k0f - o0;
+                    const int kk = k0 - o0;
                     if ((unsigned)kk < (unsigned)LT) {
                         float& d = rowpass ? A[lane][kk] : A[kk][lane];
                         d = fmaf(1.0f - w, Wu, d);
@@ -760,6 +759,7 @@ cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st)
         else gather_fan_dispatch<GATHER_PDHG>(a, grid, block, st);
         return cudaGetLastError();
     }
+    if (a.n_ang > 0 && (!a.u || !a.ap || !a.order || a.n_row < 0 || a.n_row > a.n_ang)) return cudaErrorInvalidValue;
     const int b = (a.N + GT - 1) / GT;
     dim3 grid(b, b, a.parts), block(GT * GW);
     if (mode == GATHER_R) gather_dispatch<GATHER_R>(a, grid, block, st);

@@ -4,7 +4,9 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
+#include <string.h>
 
 #include <vector>
 
@@ -32,7 +34,7 @@ struct St<false> {
     __device__ static float ld(const void* p, size_t i) { return __ldg(static_cast<const float*>(p) + i); }
     __device__ static float get(const void* p, size_t i) { return static_cast<const float*>(p)[i]; }
     __device__ static void put(void* p, size_t i, float v) { static_cast<float*>(p)[i] = v; }
-    __device__ static float2 ld2(const void* p, size_t i) { return __ldg(static_cast<const float2*>(p) + i); }
+    __device__ static float2 ld2(const void* p, ptrdiff_t i) { return __ldg(static_cast<const float2*>(p) + i); }
     __device__ static void put2(void* p, size_t i, float a, float b)
     {
         static_cast<float2*>(p)[i] = make_float2(a, b);
@@ -63,7 +65,7 @@ struct St<true> {
     {
         static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(v);
     }
-    __device__ static float2 ld2(const void* p, size_t i)
+    __device__ static float2 ld2(const void* p, ptrdiff_t i)
     {
         return __bfloat1622float2(__ldg(static_cast<const __nv_bfloat162*>(p) + i));
     }
@@ -73,30 +75,42 @@ struct St<true> {
     }
 };
 
-// Per-angle Joseph coefficients, FP64 on the host, rounded once.
-// A ray (a, t) crosses stepping line q (an image row, or a row of x^T for
-// column-branch angles) at the fractional index f = A t + B q + C along the
-// interpolation axis.  To keep the interpolation weight accurate in FP32 at
-// large N, each coefficient is split as X = X_hi + X_lo with X_hi a multiple of
-// 2^-10: then H = A_hi t + B_hi q + C_hi is exact in FP32 (|H| < 2^14) in any
-// evaluation order, and the small remainder L = A_lo t + (B_lo q + C_lo) is
-// evaluated in that fixed order.  The integer part of f is floor(H) +
-// floor((H - floor(H)) + L) and the weight is the fractional part of the
-// same sum, so the forward projector and the gather evaluate identical bits.
-// W = 1/|cos| or 1/|sin| is the path length per step; invA ~ 1/A locates the
-// rays that reach a pixel in the gather.
+// Per-angle Joseph coefficients of the parallel beam, FP64 on the host, rounded once to
+// 32.32 fixed point.  A ray (a, t) crosses stepping line q (an image row, or a row of x^T for
+// column-branch angles) at the fractional index f = A t + B q + C along the interpolation
+// axis.  With Ai, Bi, Ci the integers nearest to A 2^32, B 2^32, C 2^32, the kernels evaluate
+// F = Ai t + Bi q + Ci exactly in 64-bit integers, in any order, directly or by steps of Ai or
+// Bi: the crossing's integer part is k0 = F >> 32 and its interpolation weight is the top 23
+// bits of the low word, w = (low >> 9) 2^-23, exact in FP32 together with 1 - w (fix_weight).
+// So the forward projector and the gather hold the same FP32 matrix, and consecutive rays
+// (|A| >= 1) always cross a line at distinct k0.  Af, Bf, Cf are FP32 copies of A, B, C for
+// range estimates only; W = 1/|cos| or 1/|sin| is the path length per step; invA ~ 1/A.
 struct AngleParam {
-    float Ahi, Alo, Bhi, Blo;
-    float Chi, Clo, W, invA;
+    long long Ai, Bi, Ci;
+    float Af, Bf, Cf, W, invA;
     int row;       // 1: stepped over rows of x; 0: over rows of x^T
-    int pad0, pad1, pad2;
 };
+
+// Index k0 and weight w of a 32.32 fixed-point crossing F (see AngleParam): k0 = floor(F / 2^32)
+// and w = the fraction truncated to 23 bits, built as the float 1.m minus 1 (exact).
+__host__ __device__ inline float fix_weight(long long F, int& k0)
+{
+    k0 = (int)(F >> 32);
+    const unsigned bits = 0x3F800000u | ((unsigned)(unsigned long long)F >> 9);
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(bits) - 1.0f;
+#else
+    float f;
+    memcpy(&f, &bits, sizeof f);
+    return f - 1.0f;
+#endif
+}
 
 // Fan-beam rays (Sec. 4, fan beam geometry), one entry per ray r = a * n_det + t, FP64 on
 // the host and rounded once.  Ray r crosses stepping line q (a row of x, or a row of x^T)
-// at f = B q + C; as for AngleParam, B and C are split into a multiple of 2^-10 and a
-// remainder, so H = Bhi q + Chi is exact and L = Blo q + Clo small: the same split_weight
-// evaluation as the parallel beam with no per-bin term.  FanRay = (Bhi, Blo, Chi, Clo);
+// at f = B q + C; B and C are split into a multiple of 2^-10 and a remainder, so that
+// H = Bhi q + Chi is exact in FP32 (|H| < 2^14) and L = Blo q + Clo small, and every fan-beam
+// kernel evaluates the crossing with the same split_weight.  FanRay = (Bhi, Blo, Chi, Clo);
 // the path length W goes in a separate float array, +W for a ray stepped over rows of x,
 // -W for one stepped over rows of x^T.  A ray that passes no pixel has B = 0, C = -8, W = 0.
 // FanView = (Su, Sv, du, dv): the source position of the view and the unit direction of
@@ -150,6 +164,8 @@ enum GatherMode {
 struct GatherArgs {
     const void* u;       // sinogram (float, or bfloat16 if sino_bf)
     const AngleParam* ap;
+    const int* order;    // parallel beam: angle indices, the n_row row-branch ones first (angle_order)
+    int n_row;
     int N, n_ang, n_det;
     int parts;           // angle slices per tile (gridDim.z)
     float* part;         // scratch: parts * N * N partial sums (parts > 1)
@@ -202,6 +218,24 @@ struct RadixPlan {
     int n;               // number of stages
     int r[12];           // radices (2, 3, 4 or 8)
 };
+
+// Host: the parallel-beam angle table (see AngleParam) for N x N images and n_det bins at
+// spacing ds (>= 1) with centre offset, angles a pi / na or the given ones.  Returns false when
+// an angle is not finite or the crossings leave the range of the 32.32 fixed point.
+bool angle_table(int N, int na, int nd, double ds, double offset, const double* angles,
+                 std::vector<AngleParam>& ap);
+
+// Host: the angle indices with the row-branch angles first, each group in increasing order;
+// *n_row gets the number of row-branch angles.
+inline void angle_order(const std::vector<AngleParam>& ap, std::vector<int>& order, int* n_row)
+{
+    order.clear();
+    for (int a = 0; a < (int)ap.size(); ++a)
+        if (ap[a].row) order.push_back(a);
+    *n_row = (int)order.size();
+    for (int a = 0; a < (int)ap.size(); ++a)
+        if (!ap[a].row) order.push_back(a);
+}
 
 // Host: the fan-beam ray tables of N x N images for n_views x n_det rays (see FanRay): FP64,
 // rounded once.  geo (optional) receives (cos, sin, s) of every ray in FP64.  Returns false

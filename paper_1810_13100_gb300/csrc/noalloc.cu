@@ -21,7 +21,6 @@
 #include "../../include/ncs.h"
 #include "ncs_internal.cuh"
 
-#include <cmath>
 #include <mutex>
 #include <vector>
 
@@ -33,12 +32,14 @@ constexpr int kTile = 32;
 constexpr int kMaxTiles = (NCS_STATIC_MAX_N / kTile) * (NCS_STATIC_MAX_N / kTile);
 constexpr int kMaxParts = 4;
 constexpr size_t kParamBytes = sizeof(AngleParam) * NCS_STATIC_MAX_ANGLES;
+constexpr size_t kOrderBytes = sizeof(int) * NCS_STATIC_MAX_ANGLES;
 constexpr size_t kCounterBytes = sizeof(int) * kMaxTiles;
 constexpr size_t kPartBytes = sizeof(float) * kMaxParts * NCS_STATIC_MAX_N * NCS_STATIC_MAX_N;
-constexpr size_t kScratchBytes = kParamBytes + kCounterBytes + kPartBytes;
-static_assert(kParamBytes % 256 == 0 && kCounterBytes % 256 == 0, "scratch regions stay 256-byte aligned");
+constexpr size_t kScratchBytes = kParamBytes + kOrderBytes + kCounterBytes + kPartBytes;
+static_assert(kParamBytes % 256 == 0 && kOrderBytes % 256 == 0 && kCounterBytes % 256 == 0,
+              "scratch regions stay 256-byte aligned");
 
-// The working memory of ncs_apply_KT_static: [angle table | counters | partials].
+// The working memory of ncs_apply_KT_static: [angle table | angle order | counters | partials].
 static __device__ __align__(256) unsigned char g_kt_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -67,53 +68,6 @@ int scratch_address(unsigned char** out)
     return NCS_OK;
 }
 
-// Per-angle Joseph coefficients, the same FP64 construction as a plan's.
-bool angle_table(const ncs_geometry* geom, int N, std::vector<AngleParam>& ap)
-{
-    const int na = geom->n_angles, nd = geom->n_det;
-    const double ds = geom->det_spacing > 0.0 ? geom->det_spacing : 1.0;
-    const double cN = 0.5 * (N - 1);
-    const double s0 = -0.5 * (nd - 1) * ds + geom->det_offset;
-    ap.resize(na);
-    auto hi = [](double X) { return std::nearbyint(X * 1024.0) / 1024.0; };
-    for (int a = 0; a < na; ++a) {
-        double th, c, sn;
-        int row;
-        if (geom->angles) {
-            th = geom->angles[a];
-            if (!std::isfinite(th)) return false;
-            c = std::cos(th);
-            sn = std::sin(th);
-            row = std::fabs(c) >= std::fabs(sn) ? 1 : 0;
-        } else {
-            th = a * M_PI / na;
-            c = std::cos(th);
-            sn = std::sin(th);
-            row = (4 * a <= na || 4 * a >= 3 * na) ? 1 : 0;
-        }
-        double A, B, C, W, invA;
-        if (row) {
-            A = ds / c; B = sn / c; C = (s0 - cN * sn) / c + cN; W = 1.0 / std::fabs(c); invA = c / ds;
-        } else {
-            A = -ds / sn; B = c / sn; C = cN - (s0 + cN * c) / sn; W = 1.0 / std::fabs(sn); invA = -sn / ds;
-        }
-        if (std::fabs(hi(A)) * (nd - 1) + std::fabs(hi(B)) * (N - 1) + std::fabs(hi(C)) >= 16384.0) return false;
-        {   // rays at least one pixel apart in FP32 (the bound of ncs_plan_create)
-            const double Lmax = std::fabs(A - hi(A)) * (nd - 1) + std::fabs(B - hi(B)) * (N - 1) +
-                                std::fabs(C - hi(C));
-            if (std::fabs(A) != 1.0 && std::fabs(A) < 1.0 + 4.0 * (1.0 + 2.0 * Lmax) * std::ldexp(1.0, -24))
-                return false;
-        }
-        AngleParam& q = ap[a];
-        q.Ahi = (float)hi(A); q.Alo = (float)(A - hi(A));
-        q.Bhi = (float)hi(B); q.Blo = (float)(B - hi(B));
-        q.Chi = (float)hi(C); q.Clo = (float)(C - hi(C));
-        q.W = (float)W; q.invA = (float)invA;
-        q.row = row; q.pad0 = q.pad1 = q.pad2 = 0;
-    }
-    return true;
-}
-
 }  // namespace
 
 extern "C" int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float* y, float* x, void* cuda_stream)
@@ -121,18 +75,26 @@ extern "C" int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float*
     if (!geom || !y || !x || geom->n_angles < 1 || geom->n_det < 1 || N < 8) return NCS_ERR_BADARG;
     if (N > NCS_STATIC_MAX_N || geom->n_angles > NCS_STATIC_MAX_ANGLES) return NCS_ERR_UNSUPPORTED;
     if (geom->det_spacing != 0.0 && !(geom->det_spacing >= 1.0)) return NCS_ERR_UNSUPPORTED;
+    // per-angle Joseph coefficients, the same FP64 construction as a plan's
     std::vector<AngleParam> ap;
-    if (!angle_table(geom, N, ap)) return NCS_ERR_UNSUPPORTED;
+    const double ds = geom->det_spacing > 0.0 ? geom->det_spacing : 1.0;
+    if (!angle_table(N, geom->n_angles, geom->n_det, ds, geom->det_offset, geom->angles, ap))
+        return NCS_ERR_UNSUPPORTED;
     unsigned char* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != NCS_OK) return rc;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     AngleParam* d_ap = reinterpret_cast<AngleParam*>(base);
-    int* d_count = reinterpret_cast<int*>(base + kParamBytes);
-    float* d_part = reinterpret_cast<float*>(base + kParamBytes + kCounterBytes);
+    int* d_order = reinterpret_cast<int*>(base + kParamBytes);
+    int* d_count = reinterpret_cast<int*>(base + kParamBytes + kOrderBytes);
+    float* d_part = reinterpret_cast<float*>(base + kParamBytes + kOrderBytes + kCounterBytes);
     const int tiles = (int)gather_tiles(N);
-    // the angle table, and arrival counters that must start at zero
+    std::vector<int> order;
+    int n_row = 0;
+    angle_order(ap, order, &n_row);
+    // the angle table and order, and arrival counters that must start at zero
     if (cudaMemcpyAsync(d_ap, ap.data(), ap.size() * sizeof(AngleParam), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(d_order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemsetAsync(d_count, 0, (size_t)tiles * sizeof(int), st) != cudaSuccess) {
         cudaGetLastError();
         return NCS_ERR_CUDA;
@@ -140,6 +102,8 @@ extern "C" int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float*
     GatherArgs g{};
     g.u = y;
     g.ap = d_ap;
+    g.order = d_order;
+    g.n_row = n_row;
     g.N = N;
     g.n_ang = geom->n_angles;
     g.n_det = geom->n_det;

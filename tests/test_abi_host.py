@@ -79,6 +79,10 @@ def test_plan_create_rejects_bad_parameters(lib):
     o = binding.default_options()
     o.power_max_iter = 0
     assert _create(lib, 64, opt=o)[0] == -1
+    o = binding.default_options()
+    assert o.pdhg_only == 0
+    o.pdhg_only = 2
+    assert _create(lib, 64, opt=o)[0] == -1
     assert lib.ncs_plan_create(None, 64, 64, 0.1, 1.0, None, None) == -1
 
 

@@ -112,3 +112,34 @@ def test_iterations_full_size_sampled():
     for k, errs in run_pair("ct", 512, 720, 730, "iso", lam=0.005, alpha=1.0, beta=3.0, iters=[3]):
         for name, e in errs.items():
             assert e <= 1e-4, (k, name, e)
+
+
+def test_pdhg_only_plan():
+    """A pdhg_only plan (no M, no (A3) power iteration) runs the same PDHG iterates as a
+    full plan, bit for bit, and refuses the entry points that need M."""
+    import paper_1810_13100_gb300 as ncs
+    N, na, nd = 64, 90, 92
+    pr = synth.ct_problem(2, N, na, nd, 8, 0.01, oproj(N, na, nd))
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    res = []
+    for only in (False, True):
+        plan = ncs.Plan(N, na, nd, 0.3, 1.0, beta=3.0, tv="iso", pdhg_only=only)
+        x = torch.zeros(N * N, device="cuda")
+        u = torch.zeros(na * nd, device="cuda")
+        v = torch.zeros(2 * N * N, device="cuda")
+        plan.pdhg_step(x, u, v, None, b, n_iter=15)
+        torch.cuda.synchronize()
+        res.append(to_np(x))
+        if only:
+            with pytest.raises(ncs.NCSError) as ei:
+                plan.step(x, u, v, None, b, n_iter=1)
+            assert ei.value.code == -2
+            with pytest.raises(ncs.NCSError) as ei:
+                plan.solve(b, x, tol=1e-4, max_iter=10)
+            assert ei.value.code == -2
+            with pytest.raises(ncs.NCSError):
+                plan.apply_Minv(x)
+            lm, rho = plan.power_bound()
+            assert lm > 0 and np.isnan(rho)
+        plan.close()
+    assert np.array_equal(res[0], res[1])

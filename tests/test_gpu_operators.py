@@ -116,15 +116,21 @@ def test_user_angles_with_exact_ties():
     assert rel_l2(to_np(xt), oop.KT(yv, g)) <= TOL
 
 
-def test_angle_too_close_to_an_axis_is_rejected():
-    """Rays 1/cos(1e-4) - 1 = 5e-9 pixels over one pixel apart: in FP32 two rays could
-    share a crossing pixel, so the plan refuses the geometry instead of computing a
-    K^T that is not K's transpose; a ray spacing of exactly one (theta = 0) is fine."""
-    import paper_1810_13100_gb300 as ncs
-    with pytest.raises(ncs.NCSError) as e:
-        plan_for(32, 3, 46, angles=[0.0, 1e-4, 1.0], power_max_iter=2)
-    assert e.value.code == -2
-    plan_for(32, 3, 46, angles=[0.0, 1e-2, 1.0], power_max_iter=2).close()
+def test_angle_close_to_an_axis():
+    """Rays 1/cos(1e-4) - 1 = 5e-9 pixels more than one pixel apart: the 32.32 fixed-point
+    crossings still put consecutive rays at distinct positions, so K and K^T stay an exact
+    pair and match the oracle."""
+    th = [0.0, 1e-4, 1.0, math.pi / 2 - 1e-4]
+    N, nd = 32, 46
+    g = oop.Geometry(N, len(th), nd, theta=np.array(th))
+    plan = plan_for(N, len(th), nd, angles=th, power_max_iter=2)
+    x = f32(np.random.default_rng(3).uniform(0, 1, (N, N)))
+    yv = f32(np.random.default_rng(4).uniform(0, 1, (len(th), nd)))
+    y = plan.apply_K(torch.from_numpy(x.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(y), oop.K(x, g)) <= TOL
+    xt = plan.apply_KT(torch.from_numpy(yv.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(xt), oop.KT(yv, g)) <= TOL
+    plan.close()
 
 
 @pytest.mark.parametrize("N", [8, 48, 96, 512])
