@@ -41,6 +41,10 @@ ADMM_PARAMS = dict(alpha=0.1, beta=0.1, n_cg=10)
 ADMM_CAP = 1000                     # outer steps
 CHECK_EVERY = 10
 TTG_TOL = 1e-4
+# the solvers stop at their own FP64 objective gap <= TTG_STOP; evaluated on FP32 state, that
+# objective lies within ~1e-6 relative of the oracle's, so the 2% margin keeps the oracle's gap
+# of the returned x at or below TTG_TOL
+TTG_STOP = 0.98e-4
 TTG_CAP = 2000                      # NCS and ADMM iteration cap of the time-to-gap runs
 PDHG_CAP = 20000                    # PDHG needs ~10^4 iterations on this workload
 METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
@@ -48,7 +52,7 @@ METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % 
 NCU_KERNEL = {"joseph_gather": "k_gather", "joseph_fwd": "k_fwd"}
 
 
-def load_counters(workload):
+def load_counters(workload, directory=None):
     """ncu counters per launch of the library's kernels for a workload, from the committed
     capture summary profiles/counters_<workload>.txt.  Each data line reads
 
@@ -58,7 +62,7 @@ def load_counters(workload):
     (a changed kernel gets null counters until it is captured again)."""
     import hashlib
     out = {}
-    path = os.path.join(ROOT, "profiles", "counters_%s.txt" % workload)
+    path = os.path.join(directory or os.path.join(ROOT, "profiles"), "counters_%s.txt" % workload)
     try:
         lines = open(path).read().splitlines()
     except OSError:
@@ -353,7 +357,7 @@ def admm_ttg(ncs, N, na, nd, W, b, f_star, dev, grid=False):
                          h_probes=NCS_PARAMS["h_probes"])
         setup = _sync_ms(t0)
         x = torch.zeros(N * N, device=dev)
-        rep = aplan.admm_solve(b, x, tol=TTG_TOL, max_outer=ADMM_CAP, n_cg=c["n_cg"], f_star=f_star)
+        rep = aplan.admm_solve(b, x, tol=TTG_STOP, max_outer=ADMM_CAP, n_cg=c["n_cg"], f_star=f_star)
         aplan.close()
         out.append(dict(c, outer=rep["iters"], time_ms=rep["time_ms"], gap=rep["gap"], status=rep["status"],
                         operator_passes=rep["iters"] * (c["n_cg"] + 2), with_setup_ms=rep["time_ms"] + setup))
@@ -438,12 +442,12 @@ def time_to_gap(args, rank, ncs, plan, W, N, na, nd, dev):
             run["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
                                  "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
         xs = torch.zeros(n, device=dev)
-        rep = nplan.solve(bs, xs, tol=TTG_TOL, max_iter=TTG_CAP, f_star=f_star)
+        rep = nplan.solve(bs, xs, tol=TTG_STOP, max_iter=TTG_CAP, f_star=f_star)
         run["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
         run["ncs"]["with_setup_ms"] = rep["time_ms"] + ncs_setup
         stops[(sd, "ncs")] = xs.cpu().numpy().astype("float64")
         xs.zero_()
-        rep = pplan.pdhg_solve(bs, xs, tol=TTG_TOL, max_iter=PDHG_CAP, f_star=f_star)
+        rep = pplan.pdhg_solve(bs, xs, tol=TTG_STOP, max_iter=PDHG_CAP, f_star=f_star)
         run["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
         run["pdhg"]["with_setup_ms"] = rep["time_ms"] + pdhg_setup
         stops[(sd, "pdhg")] = xs.cpu().numpy().astype("float64")
@@ -456,7 +460,7 @@ def time_to_gap(args, rank, ncs, plan, W, N, na, nd, dev):
     if not runs:
         return None, stops
     med = lambda xs_: statistics.median(xs_) if xs_ else None
-    ttg = {"tol": TTG_TOL, "cap": {"ncs": TTG_CAP, "pdhg": PDHG_CAP, "admm_outer": ADMM_CAP},
+    ttg = {"tol": TTG_TOL, "gpu_stop_tol": TTG_STOP, "cap": {"ncs": TTG_CAP, "pdhg": PDHG_CAP, "admm_outer": ADMM_CAP},
            "seeds": [r["seed"] for r in runs], "runs": runs,
            "setup_ms": {"ncs": ncs_setup, "pdhg": pdhg_setup, "pdhg_tables": pdhg_tables,
                         "pdhg_lambda_max": pdhg_lmax, "lambda_max_AtA": lmax,
@@ -474,6 +478,7 @@ def time_to_gap(args, rank, ncs, plan, W, N, na, nd, dev):
     adm_ok = [a for a in adm if a["status"] == 0]
     ttg.update({"admm": ADMM_PARAMS, "admm_converged_gpu_objective": len(adm_ok),
                 "admm_median_ms": med([a["time_ms"] for a in adm_ok]),
+                "admm_median_ms_with_setup": med([a["with_setup_ms"] for a in adm_ok]),
                 "admm_median_outer": med([a["outer"] for a in adm_ok])})
     return ttg, stops
 
@@ -542,10 +547,18 @@ def run_ours(args, ws, rank, local):
     for k in range(args.warmup):
         one_step(k)
     torch.cuda.synchronize()
+    # the dominant kernel class, from an untimed pass with every kernel bracketed; inside the
+    # timed region only it carries events
+    plan.profile(True)
+    for k in range(CHECK_EVERY):
+        one_step(k)
+    torch.cuda.synchronize()
+    pre = plan.profile_read()
+    plan.profile(False)
+    dom_name = max(pre.items(), key=lambda kv: kv[1][0])[0]
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    # inside the timed region only the dominant kernel (the K^T gather) carries events
-    plan.profile_mask(["joseph_gather"])
+    plan.profile_mask([dom_name])
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -578,7 +591,6 @@ def run_ours(args, ws, rank, local):
 
     # ---- roofline of the dominant kernel (algorithmic work / its duration in the timed region)
     peaks, peak_kind = load_peaks()
-    dom_name = max(kern.items(), key=lambda kv: kv[1][0])[0]
     dom_ms, dom_n = kern_timed[dom_name] if kern_timed.get(dom_name, (0, 0))[1] else kern[dom_name]
     clk_sum = clk.summary()
     nnz = plan.nnz()
@@ -935,6 +947,100 @@ def run_fan(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+CONE_NCS = dict(alpha=0.01, beta=0.01, h_probes=128)    # the reference run's step and M (oracle/fstar.py)
+
+
+def run_cone(args, ws, rank, local):
+    """The 128 x 128 x 32 cone-beam TV-CT workload (Sec. 4, cone beam geometry; 180 source positions
+    on a full turn at 256 voxels from the centre, 32 detector rows x 192 equiangular channels, 12
+    ellipsoids, 0.5% noise, isotropic TV lambda 0.005): 3-D NCS iterations/s (L2 flushed before
+    each step, the FP64 objective every 10 steps), per-kernel times, and NCS from zero to the
+    1e-4 gap against the oracle's stored minimum (reported without a convergence claim while that
+    record is not tight)."""
+    import numpy as np
+    import torch
+    import paper_1810_13100_gb300 as ncs
+    import synth
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = synth.WORKLOADS["cone128"]
+    N, Nz, na, nr, nd, R = W["N"], W["Nz"], W["n_angles"], W["n_rows"], W["n_det"], W["src_dist"]
+    pitch = synth.fan_pitch(N, R, nd, W["cover"])
+    rp = synth.cone_row_pitch(N, Nz, R, nr, W["cover"])
+    seed = args.seed + rank
+    t0 = time.perf_counter()
+    plan = ncs.ConePlan(N, Nz, na, nr, nd, R, pitch, rp, W["lam"], CONE_NCS["alpha"], beta=CONE_NCS["beta"],
+                        tv=W["tv"], h_probes=CONE_NCS["h_probes"], check_every=CHECK_EVERY)
+    setup_ms = _sync_ms(t0)
+    cone = ncs.Cone(N, Nz, na, nr, nd, R, pitch, rp)
+
+    def project(x):
+        t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32).ravel()).to(dev)
+        return cone.apply_K(t).cpu().numpy().astype(np.float64).reshape(na, nr, nd)
+
+    pr = synth.ct3d_problem(seed, N, Nz, na, nr, nd, W["n_ellipses"], W["noise_frac"], project)
+    b = torch.from_numpy(pr["b"].ravel()).to(dev)
+    n, m = N * N * Nz, na * nr * nd
+    x = torch.zeros(n, device=dev); u = torch.zeros(m, device=dev); v = torch.zeros(3 * n, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream, cur = plan.stream, torch.cuda.current_stream()
+
+    def one_step(k):
+        plan.step(x, u, v, b, n_iter=1)
+        if (k + 1) % CHECK_EVERY == 0:
+            plan.objective(x, b)
+
+    for k in range(args.warmup):
+        one_step(k)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            stream.wait_stream(cur)
+            starts[k].record(stream)
+            one_step(k)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+    barrier(ws)
+    t_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
+    t_max = reduce_max(t_ms, ws)
+    value = reduce_sum(args.steps, ws) / (t_max / 1000.0)
+    ttg = None
+    gold = load_golden("cone128", seed)
+    if gold and not args.skip_ttg:
+        fs = gold["f_star"]
+        bd = b.double()
+        xs = torch.zeros(n, device=dev)
+        rep = plan.solve(b, xs, tol=TTG_STOP, max_iter=4000, f_star=fs)
+        ttg = {"tol": TTG_TOL, "gpu_stop_tol": TTG_STOP, "f_star": fs, "oracle_iters": gold.get("iterations"),
+               "f_star_tight": bool(gold.get("tight", False)),
+               "f_star_decrease_last_1000_rel": gold["decrease_last_1000"] / abs(fs),
+               "b_rel_diff": {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
+                              "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]},
+               "ncs": {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}, "setup_ms": setup_ms}
+        ttg["ncs"]["with_setup_ms"] = rep["time_ms"] + setup_ms
+        if not ttg["f_star_tight"]:
+            ttg["claim"] = "none: the stored reference minimum is not tight (its last 1000 oracle iterations " \
+                           "lowered f by more than 1e-7 relative)"
+    plan.close()
+    cone.close()
+    if rank == 0:
+        line = {"metric": "cone-beam 3-D TV-CT NCS iterations/s (128x128x32, 180 views x 32 rows x 192 channels)",
+                "value": value, "unit": "it/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "128x128x32 cone-beam TV-CT, 180 views on [0, 2pi), 32 rows x 192 channels, "
+                                       "source at 256 voxels, 12 ellipsoids, 0.5%% noise, iso TV lambda 0.005, "
+                                       "seed %d" % seed, "ncs": CONE_NCS,
+                           "l2": "flushed before every step (256 MiB write, untimed)"},
+                "setup_ms": setup_ms, "time_to_gap": ttg, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def unet_conv_flops(H, W, levels, base):
     """FLOPs of one forward pass of the U-Net's 3x3 convolutions (2 per multiply-add)."""
     c = [base << l for l in range(levels)]
@@ -1016,7 +1122,7 @@ def main():
                     help="PDHG iteration cap on the first seed when it misses the gap within the cap")
     ap.add_argument("--admm-grid", action="store_true",
                     help="time the ADMM comparator over a grid of alpha and n_cg on the first seed")
-    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256", "fan512"])
+    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256", "fan512", "cone128"])
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--fan-gather", default="auto", choices=["auto", "lines", "quads"],
                     help="fan-beam K^T kernel (fan512 workload)")
@@ -1036,6 +1142,8 @@ def main():
         run_pet(args, ws, rank, local)
     elif args.workload == "fan512":
         run_fan(args, ws, rank, local)
+    elif args.workload == "cone128":
+        run_cone(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -85,7 +85,8 @@ typedef struct {
     ncs_precision prec;    /* storage of the iteration state (see ncs_precision) */
     double a3_margin;      /* M is rescaled to rho(M^{-1} alpha A^T A) = 1/(1+margin); default 1e-2; <0 disables */
     int power_max_iter;    /* power iteration cap (default 500) */
-    double power_tol;      /* power iteration relative-change stop (default 1e-9) */
+    double power_tol;      /* power iteration relative-change stop (default 1e-6: rho then lies within
+                              ~1e-5 of its limit, far inside the 1e-2 (A3) margin) */
     uint64_t power_seed;   /* seed of the SplitMix64 start vector (default 0) */
     int check_every;       /* objective evaluated every T iterations in the solves (default 10) */
     void* cuda_stream;     /* cudaStream_t to run on, or NULL for a plan-owned stream */
@@ -121,7 +122,7 @@ typedef struct {
 typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and solver state */
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
- * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-9 / seed 0,
+ * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-6 / seed 0,
  * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0, fan_gather 0, pdhg_only 0. */
 void ncs_options_default(ncs_options* opt);
 
@@ -259,6 +260,55 @@ int ncs_cone_apply_K(ncs_cone* cone, const float* x, float* y);
 /* x = K^T y, the exact transpose (gather, no atomics; deterministic).  Asynchronous. */
 int ncs_cone_apply_KT(ncs_cone* cone, const float* y, float* x);
 
+/* ---- Cone beam (3-D) NCS ---- */
+
+/* NCS (eq. (NCS), the updates of Sec. 4.1 in 3-D) for min 1/2 ||K x - b||^2 + lambda TV(x)
+ * on the cone beam, A = [K; (beta/alpha) D] with D the forward differences along x, y and z
+ * (Sec. 2 per axis).  Layouts as for ncs_cone; the TV dual v is three N*N*Nz blocks (the x, y
+ * and z differences, zero at the last index of their axis).  TV is anisotropic (the box of
+ * radius lambda alpha/beta per component) or isotropic (the ball of that radius per voxel).
+ * M = gamma I + alpha C is circulant on the periodic N x N x Nz grid: its projector part comes
+ * from eq. (H-fan) in least-squares form over ncs_options.h_probes SplitMix64 probe volumes
+ * (0 selects 128; seeds power_seed + 1 ..), the DC entry from ||K 1||^2 / ||1||^2 (or
+ * ncs_options.h_dc), the difference part from the 3-D periodic Laplacian
+ * 4 (sin^2(pi l/Nz) + sin^2(pi p/N) + sin^2(pi q/N)); M is rescaled for (A3) as for the 2-D
+ * plans.  Its solve is a real 3-D FFT: per-slice row and column transforms and a direct
+ * transform along z (Nz <= 64).  Options used: beta, gamma, h_dc, tv, h_probes, a3_margin,
+ * power_max_iter, power_tol, power_seed, check_every, cuda_stream; the others must keep
+ * their defaults (NCS_ERR_UNSUPPORTED otherwise: L2 data, FP32 only).  Synchronises.
+ * Errors: NCS_ERR_BADARG (as ncs_cone_create, lambda < 0, alpha <= 0, Nz < 2),
+ * NCS_ERR_UNSUPPORTED (N not of the form 2^a 3^b, Nz > 64), NCS_ERR_NOMEM, NCS_ERR_CUDA. */
+typedef struct ncs_cone_plan ncs_cone_plan;
+int ncs_cone_plan_create(const ncs_cone_geometry* geom, int N, int Nz, double lambda, double alpha,
+                         const ncs_options* opt, ncs_cone_plan** out);
+
+/* Release the plan (NULL is a no-op); waits for its stream. */
+void ncs_cone_plan_destroy(ncs_cone_plan* plan);
+
+/* n_iter >= 1 NCS iterations in place on the caller's state: x (N*N*Nz), u
+ * (n_views*n_rows*n_det), v (3*N*N*Nz); b is the measured sinogram.  Asynchronous. */
+int ncs_cone_step(ncs_cone_plan* plan, float* x, float* u, float* v, const float* b, int n_iter);
+
+/* Solve from x (in: x^0, out: the result) with zero duals until the FP64 objective gap
+ * (f - f_star)/|f_star| <= tol (or the relative change of f over one check interval if
+ * f_star is NaN), or max_iter iterations; CUDA graphs of check_every iterations, the data term
+ * from a running K x.  Synchronises.  Returns NCS_OK, NCS_NOT_CONVERGED or an error. */
+int ncs_cone_solve(ncs_cone_plan* plan, const float* b, float* x, double tol, int max_iter, double f_star,
+                   ncs_report* report);
+
+/* *f = 1/2 ||K x - b||^2 + lambda TV(x) with FP64 reductions.  Synchronises. */
+int ncs_cone_objective(ncs_cone_plan* plan, const float* x, const float* b, double* f);
+
+/* out = M^{-1} r (the plan's 3-D circulant solve; N*N*Nz).  Asynchronous. */
+int ncs_cone_apply_Minv(ncs_cone_plan* plan, const float* r, float* out);
+
+/* The eigenvalues of M after the (A3) rescale, host array of Nz*N*N doubles [l][p][q]
+ * (frequencies along z, y, x). */
+int ncs_cone_get_mu(ncs_cone_plan* plan, double* mu_host);
+
+/* *rho = lambda_max(M^{-1} alpha A^T A) before the rescale (NaN if a3_margin < 0). */
+int ncs_cone_power_bound(ncs_cone_plan* plan, double* rho);
+
 /* ---- Batches of independent slices ---- */
 
 typedef struct ncs_batch ncs_batch;   /* opaque; a set of plans solved together */
@@ -305,6 +355,16 @@ int ncs_apply_K(ncs_plan* plan, const float* x, float* y);
 
 /* x = K^T y, computed as a per-pixel gather with the same FP32 weights as K. */
 int ncs_apply_KT(ncs_plan* plan, const float* y, float* x);
+
+/* y = K x with x held as bfloat16 pair images (each value rounded to nearest once), as the
+ * NCS_BF16_STORE iterations hold xbar; the taps are read as bfloat16 and accumulated in FP32.
+ * x, y: float32, N*N and n_angles*n_det.  Allocates its two bfloat16 images on the first call
+ * (NCS_ERR_NOMEM if that fails).  Errors: NCS_ERR_BADARG. */
+int ncs_apply_K_bf16(ncs_plan* plan, const float* x, float* y);
+
+/* x = K^T y for a bfloat16 sinogram y (n_angles*n_det), as the bfloat16-storage iterations
+ * read their data dual; FP32 accumulation, float32 x (N*N).  Errors: NCS_ERR_BADARG. */
+int ncs_apply_KT_bf16(ncs_plan* plan, const void* y, float* x);
 
 /* v = D x (2*N*N layout above) and x = D^T v. */
 int ncs_apply_D(ncs_plan* plan, const float* x, float* v);

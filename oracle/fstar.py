@@ -7,6 +7,7 @@ relative objective gap (f - f*)/|f*| of the benchmark and tests is measured
 against this value.
 
     python -m oracle.fstar ct512 --seed 0 --iters 8000 --checkpoint /tmp/ct512.npz
+    python -m oracle.fstar --retag      # rewrite the "tight" flag of every stored record
 
 A record is "tight" when f fell by at most TIGHT_REL * |f*| over its last 1000
 iterations; only a tight record may serve as the target of a 1e-4 relative gap (its own
@@ -188,12 +189,30 @@ def run_cone(workload: str, seed: int, iters: int, checkpoint: str | None, every
     return out
 
 
+def retag():
+    """Write the "tight" flag (is_tight) into every stored record under tests/golden."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "fstar_*.json"))):
+        with open(path) as fh:
+            rec = json.load(fh)
+        rec["tight"] = is_tight(rec)
+        with open(path + ".tmp", "w") as fh:
+            json.dump(rec, fh, indent=1)
+        os.replace(path + ".tmp", path)
+        print(os.path.basename(path), "tight" if rec["tight"] else "not tight",
+              "%.2e" % (rec["decrease_last_1000"] / abs(rec["f_star"])))
+
+
 def load(workload: str, seed: int = 0):
     with open(golden_path(workload, seed)) as fh:
         return json.load(fh)
 
 
 if __name__ == "__main__":
+    import sys
+    if sys.argv[1:] == ["--retag"]:
+        retag()
+        sys.exit(0)
     ap = argparse.ArgumentParser()
     ap.add_argument("workload")
     ap.add_argument("--seed", type=int, default=0)

@@ -9,6 +9,7 @@ from .binding import (  # noqa: F401
     Plan,
     Batch,
     Cone,
+    ConePlan,
     UNet,
     NCSError,
     load_library,

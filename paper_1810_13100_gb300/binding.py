@@ -89,6 +89,8 @@ SIGNATURES = [
     ("ncs_power_bound", _I, [_P, _DP, _DP]),
     ("ncs_apply_K", _I, [_P, _P, _P]),
     ("ncs_apply_KT", _I, [_P, _P, _P]),
+    ("ncs_apply_K_bf16", _I, [_P, _P, _P]),
+    ("ncs_apply_KT_bf16", _I, [_P, _P, _P]),
     ("ncs_apply_D", _I, [_P, _P, _P]),
     ("ncs_apply_DT", _I, [_P, _P, _P]),
     ("ncs_apply_Minv", _I, [_P, _P, _P]),
@@ -117,6 +119,15 @@ SIGNATURES = [
     ("ncs_cone_destroy", None, [_P]),
     ("ncs_cone_apply_K", _I, [_P, _P, _P]),
     ("ncs_cone_apply_KT", _I, [_P, _P, _P]),
+    ("ncs_cone_plan_create", _I, [ctypes.POINTER(ConeGeometry), _I, _I, _D, _D, ctypes.POINTER(Options),
+                                  ctypes.POINTER(_P)]),
+    ("ncs_cone_plan_destroy", None, [_P]),
+    ("ncs_cone_step", _I, [_P, _P, _P, _P, _P, _I]),
+    ("ncs_cone_solve", _I, [_P, _P, _P, _D, _I, _D, ctypes.POINTER(Report)]),
+    ("ncs_cone_objective", _I, [_P, _P, _P, _DP]),
+    ("ncs_cone_apply_Minv", _I, [_P, _P, _P]),
+    ("ncs_cone_get_mu", _I, [_P, _DP]),
+    ("ncs_cone_power_bound", _I, [_P, _DP]),
     ("ncs_batch_create", _I, [ctypes.POINTER(_P), _I, ctypes.POINTER(_P)]),
     ("ncs_batch_destroy", None, [_P]),
     ("ncs_batch_set_lanes", _I, [_P, _I]),
@@ -198,7 +209,7 @@ class Plan:
 
     def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
-                 power_max_iter=500, power_tol=1e-9, power_seed=0, check_every=10,
+                 power_max_iter=500, power_tol=1e-6, power_seed=0, check_every=10,
                  det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False, warm_dual=False,
                  h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0, fan_gather="auto", pdhg_only=False):
         import torch
@@ -362,6 +373,21 @@ class Plan:
         self._call("ncs_apply_KT", self._L.ncs_apply_KT, self._h, _ptr(y, "y", self.m), _ptr(x, "x", self.n))
         return x
 
+    def apply_K_bf16(self, x, y=None):
+        """K x through bfloat16 pair images of x (ncs_apply_K_bf16); float32 in and out."""
+        y = self._out(y, self.m, x)
+        self._call("ncs_apply_K_bf16", self._L.ncs_apply_K_bf16, self._h, _ptr(x, "x", self.n),
+                   _ptr(y, "y", self.m))
+        return y
+
+    def apply_KT_bf16(self, y, x=None):
+        """K^T y of a bfloat16 sinogram y (ncs_apply_KT_bf16); float32 out."""
+        import torch
+        x = self._out(x, self.n, y)
+        self._call("ncs_apply_KT_bf16", self._L.ncs_apply_KT_bf16, self._h,
+                   _ptr(y, "y", self.m, dtype=torch.bfloat16), _ptr(x, "x", self.n))
+        return x
+
     def apply_D(self, x, v=None):
         v = self._out(v, 2 * self.n, x)
         self._call("ncs_apply_D", self._L.ncs_apply_D, self._h, _ptr(x, "x", self.n), _ptr(v, "v", 2 * self.n))
@@ -484,6 +510,105 @@ class Cone:
     def close(self):
         if getattr(self, "_h", None):
             self._L.ncs_cone_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ConePlan:
+    """3-D cone-beam NCS (ncs_cone_plan_create): N x N x Nz volume, TV-CT with L2 data.  The
+    geometry arguments are those of Cone; lam, alpha and the keyword options those of Plan
+    (beta, gamma, h_dc, tv, h_probes (0 -> 128), a3_margin, power_*, check_every).  Work runs
+    on a side stream ordered with torch's current stream."""
+
+    def __init__(self, N, Nz, n_views, n_rows, n_det, src_dist, pitch, row_pitch, lam, alpha, *, offset=0.0,
+                 row_offset=0.0, views=None, beta=None, gamma=0.0, h_dc=None, tv="aniso", h_probes=0,
+                 a3_margin=1e-2, power_max_iter=500, power_tol=1e-6, power_seed=0, check_every=10):
+        import torch
+        L = load_library()
+        self._L = L
+        g = ConeGeometry()
+        g.n_views, g.n_rows, g.n_det = int(n_views), int(n_rows), int(n_det)
+        g.src_dist, g.pitch, g.offset = float(src_dist), float(pitch), float(offset)
+        g.row_pitch, g.row_offset = float(row_pitch), float(row_offset)
+        self._views = None
+        if views is not None:
+            self._views = (ctypes.c_double * len(views))(*[float(v) for v in views])
+            g.views = ctypes.cast(self._views, _DP)
+        o = default_options()
+        nan = float("nan")
+        o.beta = nan if beta is None else float(beta)
+        o.gamma = float(gamma)
+        o.h_dc = nan if h_dc is None else float(h_dc)
+        o.tv = {"aniso": 0, "iso": 1}[tv]
+        o.h_probes = int(h_probes)
+        o.a3_margin = float(a3_margin)
+        o.power_max_iter = int(power_max_iter)
+        o.power_tol = float(power_tol)
+        o.power_seed = int(power_seed)
+        o.check_every = int(check_every)
+        self.stream = torch.cuda.Stream()
+        o.cuda_stream = self.stream.cuda_stream
+        h = ctypes.c_void_p()
+        _check(L.ncs_cone_plan_create(ctypes.byref(g), int(N), int(Nz), float(lam), float(alpha), ctypes.byref(o),
+                                      ctypes.byref(h)), "ncs_cone_plan_create")
+        self._h = h
+        self.N, self.Nz = int(N), int(Nz)
+        self.n = self.N * self.N * self.Nz
+        self.m = int(n_views) * int(n_rows) * int(n_det)
+
+    def _call(self, what, fn, *args):
+        import torch
+        self.stream.wait_stream(torch.cuda.current_stream())
+        try:
+            return _check(fn(*args), what)
+        finally:
+            torch.cuda.current_stream().wait_stream(self.stream)
+
+    def step(self, x, u, v, b, n_iter=1):
+        self._call("ncs_cone_step", self._L.ncs_cone_step, self._h, _ptr(x, "x", self.n), _ptr(u, "u", self.m),
+                   _ptr(v, "v", 3 * self.n), _ptr(b, "b", self.m), int(n_iter))
+
+    def solve(self, b, x, tol=1e-4, max_iter=2000, f_star=None):
+        rep = Report()
+        code = self._call("ncs_cone_solve", self._L.ncs_cone_solve, self._h, _ptr(b, "b", self.m),
+                          _ptr(x, "x", self.n), float(tol), int(max_iter),
+                          float("nan") if f_star is None else float(f_star), ctypes.byref(rep))
+        out = rep.as_dict()
+        out["code"] = code
+        return out
+
+    def objective(self, x, b):
+        f = ctypes.c_double()
+        self._call("ncs_cone_objective", self._L.ncs_cone_objective, self._h, _ptr(x, "x", self.n),
+                   _ptr(b, "b", self.m), ctypes.byref(f))
+        return f.value
+
+    def apply_Minv(self, r, out=None):
+        import torch
+        out = torch.empty(self.n, device=r.device) if out is None else out
+        self._call("ncs_cone_apply_Minv", self._L.ncs_cone_apply_Minv, self._h, _ptr(r, "r", self.n),
+                   _ptr(out, "out", self.n))
+        return out
+
+    def mu(self):
+        import numpy as np
+        out = np.empty(self.n, dtype=np.float64)
+        _check(self._L.ncs_cone_get_mu(self._h, out.ctypes.data_as(_DP)), "ncs_cone_get_mu")
+        return out.reshape(self.Nz, self.N, self.N)
+
+    def power_bound(self):
+        rho = ctypes.c_double()
+        _check(self._L.ncs_cone_power_bound(self._h, ctypes.byref(rho)), "ncs_cone_power_bound")
+        return rho.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.ncs_cone_plan_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -186,6 +186,7 @@ struct ncs_plan {
     float2* d_spec = nullptr;
     double *d_part0 = nullptr, *d_part1 = nullptr, *d_scal = nullptr, *h_pin = nullptr;
     float* d_kx = nullptr;        // running K x of a solve (L2 data)
+    void* d_bfpair = nullptr;     // bfloat16 pair images of x and x^T for ncs_apply_K_bf16 (on first use)
     float* d_adm = nullptr;       // ADMM comparator workspace (allocated on first use)
     float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
     int gparts = 1;                  // angle slices of the gather
@@ -344,7 +345,7 @@ int enq_K(ncs_plan* p, const float2* x2, const float2* xT2, float* y)
 }
 
 int enq_gather(ncs_plan* p, int mode, const void* u, const void* v, float dscale, const void* s, float kappa,
-               float* r, float* x, float* xbar, float inv_gamma, int n_ang, bool bf = false)
+               float* r, float* x, float* xbar, float inv_gamma, int n_ang, bool bf = false, bool advance = true)
 {
     GatherArgs g{};
     g.u = u;
@@ -373,7 +374,7 @@ int enq_gather(ncs_plan* p, int mode, const void* u, const void* v, float dscale
     g.inv_gamma = inv_gamma;
     g.sino_bf = bf ? 1 : 0;
     g.img_bf = bf ? 1 : 0;
-    g.iter = bf ? p->d_iter : nullptr;
+    g.iter = (bf && advance) ? p->d_iter : nullptr;
     CKP(NCS_KERNEL_GATHER, launch_gather(mode, g, p->st));
     return NCS_OK;
 }
@@ -653,7 +654,7 @@ void free_plan(ncs_plan* p)
     cudaFree(p->d_xbar); cudaFree(p->d_r); cudaFree(p->d_tmp);
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
-    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s); cudaFree(p->d_kx); cudaFree(p->d_adm);
+    cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s); cudaFree(p->d_kx); cudaFree(p->d_adm); cudaFree(p->d_bfpair);
     cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter); cudaFree(p->d_q);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
@@ -1308,7 +1309,7 @@ void ncs_options_default(ncs_options* o)
     o->prec = NCS_FP32;
     o->a3_margin = 1e-2;
     o->power_max_iter = 500;
-    o->power_tol = 1e-9;
+    o->power_tol = 1e-6;
     o->power_seed = 0;
     o->check_every = 10;
     o->cuda_stream = nullptr;
@@ -1462,6 +1463,51 @@ int ncs_apply_KT(ncs_plan* p, const float* y, float* x)
     if (!x || !y) return NCS_ERR_BADARG;
     CK(cudaSetDevice(p->dev));
     return enq_gather(p, GATHER_R, y, nullptr, 0.f, nullptr, 0.f, x, nullptr, nullptr, 0.f, p->na);
+}
+
+int ncs_apply_K_bf16(ncs_plan* p, const float* x, float* y)
+{
+    CKS(check_plan(p));
+    if (!x || !y) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    const size_t half = pair_elems(p) * 2 * sizeof(__nv_bfloat16);      // one bfloat16 pair image
+    if (!p->d_bfpair) {
+        if (cudaMalloc(&p->d_bfpair, 2 * half) != cudaSuccess) {
+            cudaGetLastError();
+            return NCS_ERR_NOMEM;
+        }
+        CK(cudaMemsetAsync(p->d_bfpair, 0, 2 * half, p->st));         // the zero border
+    }
+    void* x2 = p->d_bfpair;
+    void* xT2 = static_cast<char*>(p->d_bfpair) + half;
+    TdArgs a{};
+    a.x = x;
+    a.x2 = x2;
+    a.xT2 = xT2;
+    a.N = p->N;
+    a.pair_bf = 1;
+    CKP(NCS_KERNEL_TD, launch_td(TD_TRANSPOSE, a, p->st));
+    FwdArgs f{};
+    f.img2 = x2;
+    f.imgT2 = xT2;
+    f.pair_bf = 1;
+    f.ap = p->d_ap;
+    f.rays = p->d_rays;
+    f.rayw = p->d_rayw;
+    f.N = p->N;
+    f.n_ang = p->na;
+    f.n_det = p->nd;
+    f.y = y;
+    CKP(NCS_KERNEL_FWD, launch_fwd(FWD_PLAIN, f, p->st));
+    return NCS_OK;
+}
+
+int ncs_apply_KT_bf16(ncs_plan* p, const void* y, float* x)
+{
+    CKS(check_plan(p));
+    if (!x || !y) return NCS_ERR_BADARG;
+    CK(cudaSetDevice(p->dev));
+    return enq_gather(p, GATHER_R, y, nullptr, 0.f, nullptr, 0.f, x, nullptr, nullptr, 0.f, p->na, true, false);
 }
 
 int ncs_apply_D(ncs_plan* p, const float* x, float* v)

@@ -144,6 +144,9 @@ __global__ void k_rows_fwd(const float* __restrict__ r, float2* __restrict__ S, 
     float2* b = sm + N;
     const int j = 2 * blockIdx.x;
     const int tid = threadIdx.x, nthr = blockDim.x;
+    // slice blockIdx.y of a stack of N x N images (3-D solves); one slice in 2-D
+    r += (size_t)blockIdx.y * N * N;
+    S += (size_t)blockIdx.y * (N / 2 + 1) * N;
     const float* r0 = r + (size_t)j * N;
     const float* r1 = r0 + N;
     for (int i = tid; i < N; i += nthr) a[i] = make_float2(r0[i], r1[i]);
@@ -223,6 +226,13 @@ __global__ void k_rows_inv(const float2* __restrict__ S, const float2* __restric
     const int j = 2 * blockIdx.x;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int H = N / 2;
+    {   // slice blockIdx.y of a stack (3-D solves)
+        const size_t z = blockIdx.y;
+        S += z * (H + 1) * N;
+        if (x) x += z * N * N;
+        if (xbar) xbar += z * N * N;
+        if (out) out += z * N * N;
+    }
     // full spectra of rows j, j+1 from their halves; Z = X_j + i X_{j+1}, conjugated
     for (int k = tid; k < N; k += nthr) {
         const int kk = (k <= H) ? k : N - k;
@@ -258,6 +268,78 @@ __global__ void k_rows_inv(const float2* __restrict__ S, const float2* __restric
     }
 }
 
+// One column transform of the half spectrum per block (slice blockIdx.y): forward, or the
+// unnormalised inverse conj(FFT(conj(.))), in place.
+__global__ void k_cols_fft(float2* __restrict__ S, const float2* __restrict__ tw, RadixPlan rp, int N, int inverse)
+{
+    extern __shared__ float2 sm[];
+    float2* a = sm;
+    float2* b = sm + N;
+    const int k = blockIdx.x;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    float2* col = S + (size_t)blockIdx.y * (N / 2 + 1) * N + (size_t)k * N;
+    for (int p = tid; p < N; p += nthr) a[p] = inverse ? conj2(col[p]) : col[p];
+    __syncthreads();
+    float2* X = fft_smem(a, b, N, rp, tw, tid, nthr);
+    for (int p = tid; p < N; p += nthr) col[p] = inverse ? conj2(X[p]) : X[p];
+}
+
+constexpr int ZB = 32;    // z columns per block of k_z_dft
+
+// The transform along z of a stack of Nz half spectra (entry (z, e) at S[z * plane + e]), one
+// thread per e, as a direct DFT with twiddles twz[m] = exp(-2 pi i m / Nz) (FP64 on the
+// host, rounded once).  mode 0: forward; 1: forward, times table[l * plane + e], unnormalised
+// inverse (the 3-D circulant solve or apply); 2: unnormalised inverse.  In place.
+__global__ void __launch_bounds__(ZB) k_z_dft(float2* __restrict__ S, const float* __restrict__ table,
+                                              const float2* __restrict__ twz, int Nz, size_t plane, int mode)
+{
+    extern __shared__ float2 sm[];
+    const size_t e = (size_t)blockIdx.x * ZB + threadIdx.x;
+    if (e >= plane) return;                      // no block-wide synchronisation below
+    float2* a = sm + threadIdx.x;                // a[z * ZB]: this thread's column
+    float2* c = sm + (size_t)Nz * ZB + threadIdx.x;
+    for (int z = 0; z < Nz; ++z) a[z * ZB] = S[z * plane + e];
+    if (mode != 2) {
+        for (int l = 0; l < Nz; ++l) {
+            float2 acc = make_float2(0.0f, 0.0f);
+            int m = 0;
+            for (int z = 0; z < Nz; ++z) {
+                const float2 w = __ldg(twz + m);
+                const float2 v = a[z * ZB];
+                acc.x = fmaf(v.x, w.x, fmaf(-v.y, w.y, acc.x));
+                acc.y = fmaf(v.x, w.y, fmaf(v.y, w.x, acc.y));
+                m += l;
+                if (m >= Nz) m -= Nz;
+            }
+            if (mode == 1) {
+                const float t = __ldg(table + l * plane + e);
+                acc.x *= t;
+                acc.y *= t;
+            }
+            c[l * ZB] = acc;
+        }
+        if (mode == 0) {
+            for (int l = 0; l < Nz; ++l) S[l * plane + e] = c[l * ZB];
+            return;
+        }
+        for (int l = 0; l < Nz; ++l) a[l * ZB] = c[l * ZB];
+    }
+    // inverse: y[z] = sum_l X[l] exp(+2 pi i l z / Nz)
+    for (int z = 0; z < Nz; ++z) {
+        float2 acc = make_float2(0.0f, 0.0f);
+        int m = 0;
+        for (int l = 0; l < Nz; ++l) {
+            const float2 w = __ldg(twz + m);
+            const float2 v = a[l * ZB];
+            acc.x = fmaf(v.x, w.x, fmaf(v.y, w.y, acc.x));
+            acc.y = fmaf(v.y, w.x, fmaf(-v.x, w.y, acc.y));
+            m += z;
+            if (m >= Nz) m -= Nz;
+        }
+        S[z * plane + e] = acc;
+    }
+}
+
 int fft_threads(int N)
 {
     int t = N / 8;
@@ -278,7 +360,38 @@ cudaError_t fft_prepare(int N)
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_ratio, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     return e;
+}
+
+cudaError_t launch_rows_fwd_stack(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N, int nz,
+                                  cudaStream_t st)
+{
+    k_rows_fwd<<<dim3(N / 2, nz), fft_threads(N), 2 * N * sizeof(float2), st>>>(r, S, tw, rp, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_fft_stack(float2* S, const float2* tw, const RadixPlan& rp, int N, int nz, int inverse,
+                                  cudaStream_t st)
+{
+    k_cols_fft<<<dim3(N / 2 + 1, nz), fft_threads(N), 2 * N * sizeof(float2), st>>>(S, tw, rp, N, inverse);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_z_dft(float2* S, const float* table, const float2* twz, int Nz, size_t plane, int mode,
+                         cudaStream_t st)
+{
+    if (Nz < 1 || Nz > 64 || mode < 0 || mode > 2 || (mode == 1 && !table)) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)((plane + ZB - 1) / ZB);
+    k_z_dft<<<blocks, ZB, 2 * (size_t)Nz * ZB * sizeof(float2), st>>>(S, table, twz, Nz, plane, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_inv_stack(const float2* S, const float2* tw, const RadixPlan& rp, int N, int nz, int mode,
+                                  float* x, float* xbar, float* out, cudaStream_t st)
+{
+    k_rows_inv<<<dim3(N / 2, nz), fft_threads(N), 2 * N * sizeof(float2), st>>>(S, tw, rp, N, mode, x, xbar, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_rows_fwd(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N,

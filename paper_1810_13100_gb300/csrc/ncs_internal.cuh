@@ -269,6 +269,19 @@ cudaError_t launch_cols_solve(float2* S, const float* invmu, const float2* tw, c
 cudaError_t launch_rows_inv(const float2* S, const float2* tw, const RadixPlan& rp, int N, int mode,
                             float* x, float* xbar, float* out, cudaStream_t st);
 
+// Stacks of nz N x N slices (the 3-D circulant solve): the row pass and the row inverse per
+// slice (spectra (N/2 + 1) x N apart), column transforms forward or inverse per slice, and
+// the direct transform along z of the stacked half spectra, plane = (N/2 + 1) N entries per
+// slice apart (mode 0 forward; 1 forward, times table, inverse; 2 inverse; Nz <= 64).
+cudaError_t launch_rows_fwd_stack(const float* r, float2* S, const float2* tw, const RadixPlan& rp, int N, int nz,
+                                  cudaStream_t st);
+cudaError_t launch_cols_fft_stack(float2* S, const float2* tw, const RadixPlan& rp, int N, int nz, int inverse,
+                                  cudaStream_t st);
+cudaError_t launch_z_dft(float2* S, const float* table, const float2* twz, int Nz, size_t plane, int mode,
+                         cudaStream_t st);
+cudaError_t launch_rows_inv_stack(const float2* S, const float2* tw, const RadixPlan& rp, int N, int nz, int mode,
+                                  float* x, float* xbar, float* out, cudaStream_t st);
+
 // FP64 reductions.  Partial sums go to `partials` (one per block), finalize
 // sums them in a fixed order, so results are deterministic.
 cudaError_t launch_dot_partials(const float* a, const float* b, size_t n, double* partials, int nblk,

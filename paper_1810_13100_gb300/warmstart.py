@@ -304,6 +304,18 @@ def main(argv=None):
             summ["learned_over_zero_iters"] = float(np.mean([l / z for z, l in pair])) if pair else None
             summ["learned_fewer_than_fbp"] = int(sum(1 for r in res if r["learned"]["iters"] and r["fbp"]["iters"]
                                                     and r["learned"]["iters"] < r["fbp"]["iters"]))
+            # per-seed spread of the learned start against FBP (iterations are counted in steps of
+            # the solves' check interval)
+            d = np.array([r["learned"]["iters"] - r["fbp"]["iters"] for r in res
+                          if r["learned"]["iters"] and r["fbp"]["iters"]], dtype=np.float64)
+            if len(d) > 1:
+                se = float(d.std(ddof=1) / np.sqrt(len(d)))
+                summ["learned_minus_fbp_iters"] = {
+                    "n": int(len(d)), "mean": float(d.mean()), "std": float(d.std(ddof=1)), "stderr": se,
+                    "t": float(d.mean() / se) if se > 0 else None, "fewer": int((d < 0).sum()),
+                    "equal": int((d == 0).sum()), "more": int((d > 0).sum()),
+                    "relative_mean": float(np.mean([(r["learned"]["iters"] - r["fbp"]["iters"]) / r["fbp"]["iters"]
+                                                    for r in res if r["learned"]["iters"] and r["fbp"]["iters"]]))}
         # single-slice wall time on the first few seeds
         tim = []
         bs = list(_sinograms(None, range(lo, lo + a.time_slices), geo, plans[0]))

@@ -1,0 +1,46 @@
+"""Host-side pieces of the benchmark and of the reference-minimum records (no GPU): the ncu
+counter file is used only while the kernel source still has its recorded hash, and a
+record is tight only when its last 1000 iterations lowered f by at most 1e-7 relative."""
+import hashlib
+import os
+
+import bench
+from oracle import fstar
+
+
+def test_counter_file_is_used_only_for_the_recorded_source(tmp_path):
+    src = os.path.join(bench.ROOT, "paper_1810_13100_gb300", "csrc", "joseph.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    rel = os.path.relpath(src, bench.ROOT)
+    (tmp_path / "counters_w.txt").write_text(
+        "# comment line\n"
+        "k_gather %s %s 100 200\n"
+        "k_fwd %s %s 300 400\n" % (rel, sha, rel, "0" * 64))
+    c = bench.load_counters("w", str(tmp_path))
+    assert bench.counters_for(c, "joseph_gather") == (100.0, 200.0)
+    assert bench.counters_for(c, "joseph_fwd") == (None, None)      # stale: another source
+    assert bench.counters_for(c, "fft_rows_fwd") == (None, None)    # never captured
+    assert bench.load_counters("absent", str(tmp_path)) == {}
+
+
+def test_committed_counter_file_parses():
+    c = bench.load_counters("ct512")
+    assert set(c) >= {"k_gather", "k_fwd"}
+    for v in c.values():
+        assert v["traffic"] > 0 and v["warp_instr"] > 0
+
+
+def test_tightness_of_a_record():
+    rec = {"f_star": 2.0e6, "iterations": 8000, "decrease_last_1000": 0.1}
+    assert fstar.is_tight(rec)                       # 5e-8 relative
+    rec["decrease_last_1000"] = 0.3                  # 1.5e-7 relative
+    assert not fstar.is_tight(rec)
+    assert not fstar.is_tight({"f_star": 1.0, "iterations": 500, "decrease_last_1000": 0.0})
+
+
+def test_stored_records_carry_their_tightness():
+    import glob
+    import json
+    for path in glob.glob(os.path.join(bench.ROOT, "tests", "golden", "fstar_*.json")):
+        rec = json.load(open(path))
+        assert rec.get("tight") == fstar.is_tight(rec), path

@@ -34,7 +34,7 @@ def test_admm_iterates_match_oracle(N, na, nd, tv):
     P = osv.Problem(oop.Geometry(N, na, nd), f32(pr["b"]), lam=lam, alpha=a, beta=a, tv=tv)
     mus, _ = oracle_scaled_mu(N, na, nd, a, a, 0.0, tv)
     xs = osv.admm_pcg(P, 5, n_cg, osv.circulant_Minv(mus))
-    plan = ncs.Plan(N, na, nd, lam, a, beta=a, tv=tv)
+    plan = ncs.Plan(N, na, nd, lam, a, beta=a, tv=tv, power_tol=1e-9)
     b = torch.from_numpy(pr["b"].ravel()).cuda()
     x = torch.zeros(N * N, device="cuda")
     for k, tol in ((1, 2e-4), (5, 2e-3)):

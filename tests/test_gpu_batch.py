@@ -108,7 +108,7 @@ def test_batch_solve_to_gap_checked_by_oracle():
 @pytest.mark.parametrize("N,na,nd", [(96, 140, 130), (384, 538, 386), (512, 720, 730)])
 def test_autotuned_plan_keeps_parity(N, na, nd):
     import paper_1810_13100_gb300 as ncs
-    plan = ncs.Plan(N, na, nd, 0.01, 1.0, beta=3.0, tv="iso", autotune=True)
+    plan = ncs.Plan(N, na, nd, 0.01, 1.0, beta=3.0, tv="iso", autotune=True, power_tol=1e-9)
     info = plan.info()
     assert info["gather_parts"] >= 1 and int(np.prod(info["fft_radices"])) == N
     g = oop.Geometry(N, na, nd)

@@ -81,3 +81,118 @@ def test_cone_rejects_steep_rows_and_a_close_source():
         ncs.Cone(16, 4, 4, 5, 8, 20.0, 0.05, 0.4)            # outer rows' slopes +-0.8 > 1/sqrt(2)
     with pytest.raises(ncs.NCSError):
         ncs.Cone(16, 4, 4, 3, 8, 12.0, 0.05, 0.1)            # source inside the circle plus 3 pixels
+
+
+# ---------------------------------------------------------------- the 3-D NCS iteration
+
+# 32 x 32 x 8 volume, 12 views on a full turn, 8 rows x 48 channels, source at 40 voxels
+NG = (32, 8, 12, 8, 48, 40.0)
+
+
+def nplan(ncs, lam, alpha, tv, **kw):
+    N, Nz, na, nr, nd, R = NG
+    return ncs.ConePlan(N, Nz, na, nr, nd, R, cover(N, R, nd), 0.08, lam, alpha, tv=tv, **kw)
+
+
+def oproblem(lam, alpha, tv, seed=0):
+    import synth
+    N, Nz, na, nr, nd, R = NG
+    g = oc.ConeGeometry(N, Nz, na, nr, nd, R, cover(N, R, nd), 0.08)
+    pr = synth.ct3d_problem(seed, N, Nz, na, nr, nd, 6, 0.01, lambda x: oc.K(x, g))
+    P = oc.Problem(g, pr["b"].astype(np.float64), lam=lam, alpha=alpha, beta=alpha, tv=tv)
+    return g, pr, P
+
+
+def test_cone_mu_and_solve_match_oracle():
+    """M's eigenvalues before the (A3) rescale (eq. (H-fan) over 4 probe volumes, the 3-D
+    Laplacian spectrum) against the oracle's mu_probes, and the 3-D FFT solve against the
+    oracle's circulant solve with the same eigenvalues."""
+    import paper_1810_13100_gb300 as ncs
+    g, pr, P = oproblem(0.01, 0.5, "iso")
+    plan = nplan(ncs, 0.01, 0.5, "iso", h_probes=4, a3_margin=-1.0, power_max_iter=2)
+    mu_gpu = plan.mu()
+    mu_ref = oc.mu_probes(P, 4)
+    err = rel_l2(mu_gpu, mu_ref)
+    print("cone mu rel L2 %.2e" % err)
+    assert err <= 1e-4
+    r = f32(np.random.default_rng(5).standard_normal(g.shape))
+    out = plan.apply_Minv(torch.from_numpy(r.ravel().astype(np.float32)).cuda())
+    assert rel_l2(to_np(out), oc.circulant_solve(r, mu_gpu)) <= 1e-5
+    plan.close()
+
+
+def test_cone_rho_and_objective_match_oracle():
+    import paper_1810_13100_gb300 as ncs
+    g, pr, P = oproblem(0.01, 0.5, "iso")
+    plan = nplan(ncs, 0.01, 0.5, "iso", h_probes=4, power_tol=1e-9)
+    _, rho_ref = oc.a3_scaled_mu(P, oc.mu_probes(P, 4))
+    assert plan.power_bound() == pytest.approx(rho_ref, rel=1e-5)
+    x = f32(pr["x_true"] + 0.05 * np.random.default_rng(1).standard_normal(g.shape))
+    f = plan.objective(torch.from_numpy(x.ravel().astype(np.float32)).cuda(), torch.from_numpy(pr["b"].ravel()).cuda())
+    assert f == pytest.approx(oc.objective(P, x), rel=1e-6)
+    plan.close()
+
+
+@pytest.mark.parametrize("tv", ["aniso", "iso"])
+def test_cone_ncs_iterations_match_oracle(tv):
+    """Whole 3-D NCS iterations (gather with D^T, 3-D FFT solve, forward with the data prox,
+    3-D TV prox) from zero against the oracle's: 2e-5 after one iteration, 2e-4 after 20 (the
+    TV dual against the size of its projection's argument, as for the 2-D iterations)."""
+    import paper_1810_13100_gb300 as ncs
+    lam, alpha = 0.05, 0.5
+    g, pr, P = oproblem(lam, alpha, tv)
+    plan = nplan(ncs, lam, alpha, tv, h_probes=4, power_tol=1e-9)
+    mus, _ = oc.a3_scaled_mu(P, oc.mu_probes(P, 4))
+    Minv = lambda r: oc.circulant_solve(r, mus)
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(g.n, device="cuda")
+    u = torch.zeros(g.m, device="cuda")
+    v = torch.zeros(3 * g.n, device="cuda")
+    st = oc.zero_state(P)
+    done = 0
+    for k, tol in ((1, 2e-5), (20, 2e-4)):
+        plan.step(x, u, v, b, n_iter=k - done)
+        prev = st
+        for _ in range(k - done):
+            prev = st
+            st = oc.ncs_step(P, st, Minv)
+        done = k
+        torch.cuda.synchronize()
+        Nz, N = g.Nz, g.N
+        vg = to_np(v).reshape(3, Nz, N, N)
+        vgpu = np.concatenate([vg[0][:, :, :-1].ravel(), vg[1][:, :-1, :].ravel(), vg[2][:-1, :, :].ravel()])
+        vref = np.concatenate([c.ravel() for c in st.v])
+        dref = oc.D(2.0 * st.x - prev.x)
+        vscale = np.linalg.norm(vref) + P.beta * np.sqrt(sum(np.sum(d * d) for d in dref))
+        ex, eu = rel_l2(to_np(x), st.x), rel_l2(to_np(u), st.u)
+        ev = np.linalg.norm(vgpu - vref) / max(vscale, 1e-300)
+        print("cone %s after %d: x %.2e u %.2e v %.2e" % (tv, k, ex, eu, ev))
+        assert ex <= tol and eu <= tol and ev <= tol, (k, ex, eu, ev)
+        # the padding of the dual blocks stays zero
+        assert not vg[0][:, :, -1].any() and not vg[1][:, -1, :].any() and not vg[2][-1].any()
+    plan.close()
+
+
+def test_cone_solve_reaches_gap_checked_by_oracle():
+    """A 3-D NCS solve from zero to the 1e-4 gap against a reference minimum that the FP64
+    oracle computes here (4000 iterations, tight to 1e-9 relative per 1000); the oracle's
+    f(x_gpu) is then within 1e-4 of it."""
+    import paper_1810_13100_gb300 as ncs
+    lam, alpha = 0.05, 0.5
+    g, pr, P = oproblem(lam, alpha, "iso", seed=2)
+    mus, _ = oc.a3_scaled_mu(P, oc.mu_probes(P, 8))
+    Minv = lambda r: oc.circulant_solve(r, mus)
+    st = oc.run(P, oc.zero_state(P), 3000, Minv)
+    f3000 = oc.objective(P, st.x)
+    st = oc.run(P, st, 1000, Minv)
+    fs = oc.objective(P, st.x)
+    assert f3000 - fs <= 1e-9 * fs
+    plan = nplan(ncs, lam, alpha, "iso", h_probes=8)
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(g.n, device="cuda")
+    rep = plan.solve(b, x, tol=0.98e-4, max_iter=4000, f_star=fs)
+    plan.close()
+    assert rep["status"] == 0, rep
+    f = oc.objective(P, to_np(x).reshape(g.shape))
+    print("cone solve: %d iterations, %.1f ms, oracle gap %.3e" % (rep["iters"], rep["time_ms"], (f - fs) / fs))
+    assert fs * (1 - 1e-7) <= f <= fs * (1 + 1e-4)

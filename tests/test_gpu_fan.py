@@ -138,7 +138,7 @@ def run_fan_pair(N, na, nd, R, pitch, tv, lam, alpha, beta, iters, solver="ncs",
     pr = synth.ct_problem(1, N, na, nd, 8, 0.01, lambda x: oop.K(x, g))
     P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv=tv)
     plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, src_dist=R, fan_pitch=pitch, h_probes=probes,
-                    fan_gather=kernel)
+                    fan_gather=kernel, power_tol=1e-9)
     b = torch.from_numpy(pr["b"].ravel()).cuda()
     x = torch.zeros(N * N, device="cuda")
     u = torch.zeros(na * nd, device="cuda")
@@ -277,7 +277,7 @@ def test_fan_bf16_iterations_against_oracle(kernel):
     pr = synth.ct_problem(2, N, na, nd, 8, 0.01, lambda x: oop.K(x, g))
     P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv="iso")
     plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv="iso", src_dist=R, fan_pitch=pitch, h_probes=probes,
-                    precision="bf16", fan_gather=kernel)
+                    precision="bf16", fan_gather=kernel, power_tol=1e-9)
     mus, _ = osv.a3_scaled_mu(P, oracle_fan_mu(g, alpha, beta, probes))
     Minv = osv.circulant_Minv(mus)
     b = torch.from_numpy(pr["b"].ravel()).cuda()
@@ -309,7 +309,8 @@ def test_fan_admm_iterates_match_oracle():
     P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=a, beta=a, tv="iso")
     mus, _ = osv.a3_scaled_mu(P, oracle_fan_mu(g, a, a, probes))
     xs = osv.admm_pcg(P, 5, n_cg, osv.circulant_Minv(mus))
-    plan = ncs.Plan(N, na, nd, lam, a, beta=a, tv="iso", src_dist=R, fan_pitch=pitch, h_probes=probes)
+    plan = ncs.Plan(N, na, nd, lam, a, beta=a, tv="iso", src_dist=R, fan_pitch=pitch, h_probes=probes,
+                    power_tol=1e-9)
     b = torch.from_numpy(pr["b"].ravel()).cuda()
     x = torch.zeros(N * N, device="cuda")
     for k, tol in ((1, 2e-4), (5, 2e-3)):

@@ -30,12 +30,13 @@ def run_pair(kind, N, na, nd, tv, lam, alpha, beta, iters, solver="ncs", seed=0,
         pr = synth.pet_problem(seed, N, na, nd, 8, oproj(N, na, nd), total_counts=2e5)
         P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, kind="pet", tv=tv, kappa=1.0,
                         r_bg=f32(pr["r_bg"]))
-        plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, data="kl", nonneg=True, gamma=gamma)
+        plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, data="kl", nonneg=True, gamma=gamma,
+                        power_tol=1e-9)
         bg = torch.from_numpy(pr["r_bg"].ravel()).cuda()
     else:
         pr = synth.ct_problem(seed, N, na, nd, 8, 0.01, oproj(N, na, nd))
         P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv=tv)
-        plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, gamma=gamma)
+        plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv=tv, gamma=gamma, power_tol=1e-9)
         bg = None
     b = torch.from_numpy(pr["b"].ravel()).cuda()
     x = torch.zeros(N * N, device="cuda")

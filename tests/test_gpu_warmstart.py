@@ -39,7 +39,7 @@ def test_warm_dual_start_parity():
     g = oop.Geometry(N, na, nd)
     P = osv.Problem(g, f32(pr["b"]), lam=lam, alpha=alpha, beta=beta, tv="iso")
     x0 = f32(pr["x_true"] + 0.05 * np.random.default_rng(0).standard_normal((N, N)))
-    plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv="iso", warm_dual=True)
+    plan = ncs.Plan(N, na, nd, lam, alpha, beta=beta, tv="iso", warm_dual=True, power_tol=1e-9)
     x = torch.from_numpy(x0.ravel().astype(np.float32)).cuda()
     plan.solve(torch.from_numpy(pr["b"].ravel()).cuda(), x, tol=0.0, max_iter=10, f_star=-1e300)
     mus, _ = oracle_scaled_mu(N, na, nd, alpha, beta, 0.0, "iso")
