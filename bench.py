@@ -998,6 +998,7 @@ def run_cone(args, ws, rank, local):
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        torch.cuda.nvtx.range_push("timed")
         for k in range(args.steps):
             flush.fill_(float(k))
             stream.wait_stream(cur)
@@ -1005,6 +1006,7 @@ def run_cone(args, ws, rank, local):
             one_step(k)
             ends[k].record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     barrier(ws)
     t_ms = sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends))
     t_max = reduce_max(t_ms, ws)

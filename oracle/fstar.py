@@ -135,14 +135,14 @@ def is_tight(rec: dict) -> bool:
     1000 iterations (a record without that history is not tight)."""
     if rec.get("iterations", 0) < 1000:
         return False
-    return rec["decrease_last_1000"] <= TIGHT_REL * abs(rec["f_star"])
+    return bool(rec["decrease_last_1000"] <= TIGHT_REL * abs(rec["f_star"]))
 
 
 def write_golden(workload, seed, P, p, rho, hist, out_path=None):
     f_star = min(h[1] for h in hist)
     last = [h for h in hist if h[0] >= hist[-1][0] - 1000]
-    out = dict(workload=workload, seed=seed, f_star=f_star, iterations=hist[-1][0], rho=rho,
-               params=p, decrease_last_1000=last[0][1] - last[-1][1],
+    out = dict(workload=workload, seed=seed, f_star=float(f_star), iterations=int(hist[-1][0]), rho=float(rho),
+               params=p, decrease_last_1000=float(last[0][1] - last[-1][1]),
                b_sum=float(P.b.sum()), b_sumsq=float((P.b * P.b).sum()),
                note="FP64 oracle NCS (Sec. 4.1/4.2 updates) from zero; f_star is the lowest objective seen; "
                     "b = K x_true + noise with the oracle's K; b_sum / b_sumsq fingerprint that b")
@@ -155,12 +155,14 @@ def write_golden(workload, seed, P, p, rho, hist, out_path=None):
 
 
 def run_cone(workload: str, seed: int, iters: int, checkpoint: str | None, every: int = 250,
-             out_path: str | None = None):
+             out_path: str | None = None, alpha: float | None = None):
     """The same reference run for a cone-beam (3-D) workload, with oracle/cone.py."""
     import synth
     from . import cone as oc
     W = synth.WORKLOADS[workload]
-    p = PARAMS[workload]
+    p = dict(PARAMS[workload])
+    if alpha is not None:
+        p.update(alpha=alpha, beta=alpha)
     N, Nz, na, nr, nd, R = W["N"], W["Nz"], W["n_angles"], W["n_rows"], W["n_det"], W["src_dist"]
     g = oc.ConeGeometry(N, Nz, na, nr, nd, R, synth.fan_pitch(N, R, nd, W["cover"]),
                         synth.cone_row_pitch(N, Nz, R, nr, W["cover"]))
@@ -224,6 +226,6 @@ if __name__ == "__main__":
     a = ap.parse_args()
     import synth
     if synth.WORKLOADS[a.workload].get("geometry") == "cone":
-        run_cone(a.workload, a.seed, a.iters, a.checkpoint, out_path=a.out)
+        run_cone(a.workload, a.seed, a.iters, a.checkpoint, out_path=a.out, alpha=a.alpha)
     else:
         run(a.workload, a.seed, a.iters, a.checkpoint, alpha=a.alpha, probes=a.probes, out_path=a.out)

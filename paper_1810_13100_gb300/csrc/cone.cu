@@ -8,16 +8,18 @@
 //
 // K (k_cone_fwd): one thread per (view, row, channel, line segment).  The ray is stepped over
 // the in-plane lines of its trace; the in-plane crossing and weight come from the fan beam's
-// split coefficients (split_weight, as in joseph.cu), the slice coordinate from
-// g = sigma (Bz q + Cz) + (Nz-1)/2 evaluated in FP64 (Bz q + Cz is the in-plane distance from
-// the source to the crossing on line q), and the four taps are interpolated bilinearly in
-// (position, slice) with bounds-checked loads; the sum is scaled by |W| sqrt(1 + sigma^2).
+// split coefficients (split_weight, as in joseph.cu), the slice coordinate
+// g = sigma (Bz q + Cz) + (Nz-1)/2 (Bz q + Cz is the in-plane distance from the source to the
+// crossing on line q) from a per-ray 32.32 fixed-point pair evaluated exactly in 64-bit
+// integers (fix_weight), and the four taps are interpolated bilinearly in (position, slice)
+// with bounds-checked loads; the sum is scaled by |W| sqrt(1 + sigma^2).
 //
 // K^T (k_cone_gather, no atomics): one thread per 2 x 2 in-plane pixel quad of one slice.
 // Per view it scans the channels whose in-plane trace can reach the quad (the fan-beam quad
 // window) and, for each, the rows whose slope can put a slice weight on slice k over the
 // quad's lines (from the in-plane distance of the quad, widened by 2.5 pixels and 1% of a
-// slice), and evaluates exactly the forward kernel's in-plane weight and FP64 slice coordinate.
+// slice), and evaluates exactly the forward kernel's in-plane weight and fixed-point slice
+// coordinate.
 // Views, channels and rows are summed in increasing order, so the result is deterministic.
 #include "../../include/ncs.h"
 #include "ncs_internal.cuh"
@@ -39,8 +41,8 @@ struct ncs_cone {
     FanRay* d_rays = nullptr;
     float* d_rayw = nullptr;
     FanView* d_views = nullptr;
-    double2* d_zc = nullptr;     // per (view, channel): (Bz, Cz) of the in-plane distance Bz q + Cz
-    double* d_sig = nullptr;     // per row: slope sigma_r
+    longlong2* d_zfix = nullptr; // per ray (view, row, channel): the slice coordinate, 32.32 fixed point
+    float* d_rowf = nullptr;     // per row: sqrt(1 + sigma_r^2)
     float inv_pitch = 0.f, t_off = 0.f, inv_rp = 0.f, r_off = 0.f;
     double row_offset = 0.0;
 };
@@ -51,8 +53,8 @@ struct ConeArgs {
     const FanRay* rays;
     const float* rayw;
     const FanView* views;
-    const double2* zc;
-    const double* sig;
+    const longlong2* zfix;       // slice coordinate of ray (a, r, t) on line q: (Zi q + Ci) / 2^32 (see below)
+    const float* rowf;           // path-length factor sqrt(1 + sigma_r^2) per row
     int N, Nz, na, nr, nd;
     float inv_pitch, t_off;      // channel coordinate of a fan angle: gamma * inv_pitch + t_off
     float inv_rp, r_off;         // row coordinate of a slope: sigma * inv_rp + r_off
@@ -74,11 +76,13 @@ struct ConeArgs {
 
 // The integer index and weight of a crossing f = H + L (the same expression as the
 // parallel- and fan-beam kernels of joseph.cu).
+// The floors are taken on the FP32 pipe: for |v| < 2^22, v + 1.5 * 2^23 rounded toward -infinity
+// is floor(v) + 1.5 * 2^23 exactly (floats in [2^23, 2^24) are spaced 1 apart).
 __device__ __forceinline__ float cone_split_weight(float H, float L, float& k0)
 {
-    const float Hi = floorf(H);
+    const float Hi = __fadd_rd(H, 12582912.0f) - 12582912.0f;
     const float fr = (H - Hi) + L;
-    const float fl = floorf(fr);
+    const float fl = __fadd_rd(fr, 12582912.0f) - 12582912.0f;
     k0 = Hi + fl;
     return fr - fl;
 }
@@ -88,11 +92,11 @@ __device__ __forceinline__ float vox(const float* x, int N, int Nz, int k, int j
     return (k >= 0 && k < Nz && j >= 0 && j < N && i >= 0 && i < N) ? __ldg(x + ((size_t)k * N + j) * N + i) : 0.0f;
 }
 
-// Path length per step of a ray with in-plane weight ws and slope sig (the same expression in
-// both kernels).
-__device__ __forceinline__ float cone_path(float ws, double sig)
+// Path length per step of a ray with in-plane weight ws in a row with factor rowf =
+// sqrt(1 + sigma^2) (the same expression in both kernels).
+__device__ __forceinline__ float cone_path(float ws, float rowf)
 {
-    return fabsf(ws) * sqrtf(1.0f + (float)(sig * sig));
+    return fabsf(ws) * rowf;
 }
 
 constexpr int CF_TB = 64;      // channels per forward block
@@ -110,10 +114,8 @@ __global__ void __launch_bounds__(CF_TB * CF_SEG) k_cone_fwd(ConeArgs g)
         const size_t rt = (size_t)a * g.nd + t;
         const float4 q = __ldg(g.rays + rt);
         const float ws = __ldg(g.rayw + rt);
-        const double2 zc = g.zc[rt];
-        const double sig = g.sig[r];
+        const longlong2 zf = g.zfix[((size_t)a * g.nr + r) * g.nd + t];
         const bool row = !(ws < 0.0f);
-        const double cZ = 0.5 * (double)(Nz - 1);
         const int chunk = (N + CF_SEG - 1) / CF_SEG;
         const int ls = threadIdx.y * chunk, le = min(N, ls + chunk);
         for (int l = ls; l < le; ++l) {
@@ -122,11 +124,9 @@ __global__ void __launch_bounds__(CF_TB * CF_SEG) k_cone_fwd(ConeArgs g)
             const float w = cone_split_weight(fmaf(q.x, lf, q.z), fmaf(q.y, lf, q.w), k0f);
             if (!(k0f >= -1.0f && k0f < (float)N)) continue;        // both in-plane taps outside
             const int p0 = (int)k0f;
-            const double gz = fma(sig, fma(zc.x, (double)l, zc.y), cZ);
-            const double kz = floor(gz);
-            if (!(kz >= -1.0 && kz < (double)Nz)) continue;         // both slice taps outside
-            const int k0 = (int)kz;
-            const float wz = (float)(gz - kz);
+            int k0;
+            const float wz = fix_weight(zf.x * (long long)l + zf.y, k0);
+            if (!(k0 >= -1 && k0 < Nz)) continue;                    // both slice taps outside
             float v00, v01, v10, v11;                                // (slice k0 / k0+1, position p0 / p0+1)
             if (row) {
                 v00 = vox(g.x, N, Nz, k0, l, p0);
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(CF_TB * CF_SEG) k_cone_fwd(ConeArgs g)
             const float a1 = fmaf(w, v11, (1.0f - w) * v10);
             acc += fmaf(wz, a1, (1.0f - wz) * a0);
         }
-        W3 = cone_path(ws, sig);
+        W3 = cone_path(ws, __ldg(g.rowf + r));
     }
     red[threadIdx.y][threadIdx.x] = acc;
     __syncthreads();
@@ -210,12 +210,13 @@ __device__ __forceinline__ void cone_quad_weights(int p, float k0f, float w, flo
     c1 = d == -1 ? 1.0f - w : (d == 0 ? w : 0.0f);
 }
 
-// Weight that slice coordinate g puts on slice k.
-__device__ __forceinline__ float slice_weight(double g, int k)
+// Weight that the fixed-point slice coordinate G puts on slice k (fix_weight: the forward
+// kernel's slice index and weight).
+__device__ __forceinline__ float slice_weight(long long G, int k)
 {
-    const double kz = floor(g);
-    const float wz = (float)(g - kz);
-    return kz == (double)k ? 1.0f - wz : (kz == (double)(k - 1) ? wz : 0.0f);
+    int kz;
+    const float wz = fix_weight(G, kz);
+    return kz == k ? 1.0f - wz : (kz == k - 1 ? wz : 0.0f);
 }
 
 __global__ void __launch_bounds__(CQX * CQY) k_cone_gather(ConeArgs g)
@@ -226,7 +227,6 @@ __global__ void __launch_bounds__(CQX * CQY) k_cone_gather(ConeArgs g)
     const int k = blockIdx.z;
     if (i >= N || j >= N) return;           // N is even: a quad is inside or outside
     const float cN = 0.5f * (float)(N - 1);
-    const double cZ = 0.5 * (double)(Nz - 1);
     const float qu = ((float)i + 0.5f) - cN, qv = cN - ((float)j + 0.5f);
     const float fi = (float)i, fj = (float)j;
     const float wv = (float)k - 0.5f * (float)(Nz - 1);
@@ -260,14 +260,14 @@ __global__ void __launch_bounds__(CQX * CQY) k_cone_gather(ConeArgs g)
             cone_quad_weights(p0, kA, wA, cA0, cA1);
             cone_quad_weights(p0, kB, wB, cB0, cB1);
             if (cA0 == 0.0f && cA1 == 0.0f && cB0 == 0.0f && cB1 == 0.0f) continue;
-            const double2 zc = g.zc[rt];
-            const double hA = fma(zc.x, (double)l0, zc.y), hB = fma(zc.x, (double)l1, zc.y);
+            const long long lA = (long long)(row ? j : i);
             for (int r = r0; r <= r1; ++r) {
-                const double sig = g.sig[r];
-                const float zA = slice_weight(fma(sig, hA, cZ), k);
-                const float zB = slice_weight(fma(sig, hB, cZ), k);
+                const longlong2 zf = __ldg(g.zfix + ((size_t)a * nr + r) * nd + t);
+                const long long GA = zf.x * lA + zf.y;
+                const float zA = slice_weight(GA, k);
+                const float zB = slice_weight(GA + zf.x, k);
                 if (zA == 0.0f && zB == 0.0f) continue;
-                const float Wu = cone_path(ws, sig) * __ldg(g.y + ((size_t)a * nr + r) * nd + t);
+                const float Wu = cone_path(ws, __ldg(g.rowf + r)) * __ldg(g.y + ((size_t)a * nr + r) * nd + t);
                 // row branch: line A is row j, B row j + 1; column branch: A is column i, B column i + 1
                 const float c00 = zA * cA0, c11 = zB * cB1;
                 const float c01 = row ? zA * cA1 : zB * cB0;
@@ -378,8 +378,8 @@ ConeArgs args_of(const ncs_cone* c)
     a.rays = c->d_rays;
     a.rayw = c->d_rayw;
     a.views = c->d_views;
-    a.zc = c->d_zc;
-    a.sig = c->d_sig;
+    a.zfix = c->d_zfix;
+    a.rowf = c->d_rowf;
     a.N = c->N;
     a.Nz = c->Nz;
     a.na = c->na;
@@ -397,8 +397,8 @@ void free_cone(ncs_cone* c)
     cudaFree(c->d_rays);
     cudaFree(c->d_rayw);
     cudaFree(c->d_views);
-    cudaFree(c->d_zc);
-    cudaFree(c->d_sig);
+    cudaFree(c->d_zfix);
+    cudaFree(c->d_rowf);
 }
 
 template <class T>
@@ -446,6 +446,9 @@ int ncs_cone_create(const ncs_cone_geometry* geom, int N, int Nz, void* cuda_str
     const double cN = 0.5 * (N - 1), R = geom->src_dist;
     const size_t m = (size_t)na * nd;
     std::vector<double2> zc(m);
+    std::vector<longlong2> zfix((size_t)na * nr * nd);
+    std::vector<float> rowf(nr);
+    for (int r = 0; r < nr; ++r) rowf[r] = (float)std::sqrt(1.0 + sig[r] * sig[r]);
     for (int a = 0; a < na; ++a) {
         const double be = geom->views ? geom->views[a] : 2.0 * M_PI * a / na;
         const double Su = -R * std::sin(be), Sv = R * std::cos(be);
@@ -463,6 +466,18 @@ int ncs_cone_create(const ncs_cone_geometry* geom, int N, int Nz, void* cuda_str
             zc[r] = make_double2(Bz, Cz);
         }
     }
+    // slice coordinate of ray (a, row, t) on line q: g = sigma (Bz q + Cz) + (Nz-1)/2, as
+    // (Zi q + Ci) / 2^32 with Zi, Ci the integers nearest to sigma Bz 2^32 and (sigma Cz +
+    // (Nz-1)/2) 2^32; both kernels evaluate it exactly in 64-bit integers (fix_weight)
+    const double cZ = 0.5 * (Nz - 1), two32 = 4294967296.0;
+    for (int a = 0; a < na; ++a)
+        for (int rr = 0; rr < nr; ++rr)
+            for (int t = 0; t < nd; ++t) {
+                const double2 z = zc[(size_t)a * nd + t];
+                longlong2& f = zfix[((size_t)a * nr + rr) * nd + t];
+                f.x = std::llround(sig[rr] * z.x * two32);
+                f.y = std::llround((sig[rr] * z.y + cZ) * two32);
+            }
     ncs_cone* c = new (std::nothrow) ncs_cone();
     if (!c) return NCS_ERR_NOMEM;
     c->N = N;
@@ -479,14 +494,14 @@ int ncs_cone_create(const ncs_cone_geometry* geom, int N, int Nz, void* cuda_str
     if (rc == NCS_OK) rc = cone_alloc(&c->d_rays, m);
     if (rc == NCS_OK) rc = cone_alloc(&c->d_rayw, m);
     if (rc == NCS_OK) rc = cone_alloc(&c->d_views, (size_t)na);
-    if (rc == NCS_OK) rc = cone_alloc(&c->d_zc, m);
-    if (rc == NCS_OK) rc = cone_alloc(&c->d_sig, (size_t)nr);
+    if (rc == NCS_OK) rc = cone_alloc(&c->d_zfix, zfix.size());
+    if (rc == NCS_OK) rc = cone_alloc(&c->d_rowf, (size_t)nr);
     if (rc == NCS_OK &&
         (cudaMemcpy(c->d_rays, rays.data(), m * sizeof(FanRay), cudaMemcpyHostToDevice) != cudaSuccess ||
          cudaMemcpy(c->d_rayw, rayw.data(), m * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
          cudaMemcpy(c->d_views, views.data(), na * sizeof(FanView), cudaMemcpyHostToDevice) != cudaSuccess ||
-         cudaMemcpy(c->d_zc, zc.data(), m * sizeof(double2), cudaMemcpyHostToDevice) != cudaSuccess ||
-         cudaMemcpy(c->d_sig, sig.data(), nr * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess))
+         cudaMemcpy(c->d_zfix, zfix.data(), zfix.size() * sizeof(longlong2), cudaMemcpyHostToDevice) != cudaSuccess ||
+         cudaMemcpy(c->d_rowf, rowf.data(), nr * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess))
         rc = NCS_ERR_CUDA;
     if (rc != NCS_OK) {
         cudaGetLastError();

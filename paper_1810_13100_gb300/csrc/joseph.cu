@@ -139,15 +139,40 @@ k_fwd(FwdArgs g)
             }
         } else {
             long long F = Fi + Bi * (long long)js;
+            const size_t rs = (size_t)pitch * 2 * St<PBF>::bytes;      // bytes per pair-image row
             const char* rowp = static_cast<const char*>(im2) + ((size_t)js * pitch + PAIR_PAD) * 2 * St<PBF>::bytes;
-            for (int j = js; j < je; ++j) {
+            int j = js;
+            // four rows at a time: their loads are independent, so all four are issued before
+            // the first is used (the taps are summed in row order, as in the loop below)
+            for (; j + 4 <= je; j += 4) {
+                int k0, k1, k2, k3;
+                const float w0 = fix_weight(F, k0);
+                const float w1 = fix_weight(F + Bi, k1);
+                const float w2 = fix_weight(F + 2 * Bi, k2);
+                const float w3 = fix_weight(F + 3 * Bi, k3);
+                const float2 x0 = St<PBF>::ld2(rowp, k0);
+                const float2 x1 = St<PBF>::ld2(rowp + rs, k1);
+                const float2 x2 = St<PBF>::ld2(rowp + 2 * rs, k2);
+                const float2 x3 = St<PBF>::ld2(rowp + 3 * rs, k3);
+                acc = fmaf(1.0f - w0, x0.x, acc);
+                acc = fmaf(w0, x0.y, acc);
+                acc = fmaf(1.0f - w1, x1.x, acc);
+                acc = fmaf(w1, x1.y, acc);
+                acc = fmaf(1.0f - w2, x2.x, acc);
+                acc = fmaf(w2, x2.y, acc);
+                acc = fmaf(1.0f - w3, x3.x, acc);
+                acc = fmaf(w3, x3.y, acc);
+                F += 4 * Bi;
+                rowp += 4 * rs;
+            }
+            for (; j < je; ++j) {
                 int i0;
                 const float w = fix_weight(F, i0);
                 const float2 xv = St<PBF>::ld2(rowp, i0);
                 acc = fmaf(1.0f - w, xv.x, acc);
                 acc = fmaf(w, xv.y, acc);
                 F += Bi;
-                rowp += (size_t)pitch * 2 * St<PBF>::bytes;
+                rowp += rs;
             }
         }
     }
@@ -318,9 +343,8 @@ k_gather(GatherArgs g)
             // the current ray are recomputed at every position
 #pragma unroll
             for (int k = 0; k < GT; ++k) {
-                const bool adv = k0 == k - 1;
-                acc[k] += adv ? vl : 0.0f;
-                if (adv) {
+                if (k0 == k - 1) {
+                    acc[k] += vl;
                     G += step;
                     ui += dir;
                 }
@@ -328,7 +352,7 @@ k_gather(GatherArgs g)
                 wu = U[ui];
                 vr = fmaf(-w, wu, wu);
                 vl = w * wu;
-                acc[k] += k0 == k ? vr : 0.0f;
+                if (k0 == k) acc[k] += vr;
             }
         }
         __syncwarp();

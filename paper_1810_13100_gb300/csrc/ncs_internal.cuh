@@ -96,10 +96,15 @@ struct AngleParam {
 __host__ __device__ inline float fix_weight(long long F, int& k0)
 {
     k0 = (int)(F >> 32);
-    const unsigned bits = 0x3F800000u | ((unsigned)(unsigned long long)F >> 9);
 #ifdef __CUDA_ARCH__
+    // (low >> 9) + 0x3F800000 as one multiply-high-add (low * 2^23 / 2^32 is low >> 9; the sum
+    // has no carries into the exponent), which runs on the FMA pipe instead of a shift and an or
+    unsigned bits;
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(bits) : "r"((unsigned)(unsigned long long)F), "r"(0x800000u),
+        "r"(0x3F800000u));
     return __uint_as_float(bits) - 1.0f;
 #else
+    const unsigned bits = 0x3F800000u | ((unsigned)(unsigned long long)F >> 9);
     float f;
     memcpy(&f, &bits, sizeof f);
     return f - 1.0f;

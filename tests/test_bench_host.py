@@ -44,3 +44,15 @@ def test_stored_records_carry_their_tightness():
     for path in glob.glob(os.path.join(bench.ROOT, "tests", "golden", "fstar_*.json")):
         rec = json.load(open(path))
         assert rec.get("tight") == fstar.is_tight(rec), path
+
+
+def test_records_serialise_numpy_values(tmp_path):
+    """A record written from numpy scalars (the oracle's history) is plain JSON."""
+    import json
+    import numpy as np
+    hist = [(np.int64(1000), np.float64(10.0)), (np.int64(2000), np.float64(9.999999))]
+    P = type("P", (), {"b": np.ones(3)})()
+    out = str(tmp_path / "rec.json")
+    fstar.write_golden("w", 0, P, {"alpha": 0.003}, np.float64(5.0), hist, out_path=out)
+    rec = json.load(open(out))
+    assert rec["tight"] is False and rec["iterations"] == 2000

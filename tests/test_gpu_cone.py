@@ -175,10 +175,11 @@ def test_cone_ncs_iterations_match_oracle(tv):
 
 def test_cone_solve_reaches_gap_checked_by_oracle():
     """A 3-D NCS solve from zero to the 1e-4 gap against a reference minimum that the FP64
-    oracle computes here (4000 iterations, tight to 1e-9 relative per 1000); the oracle's
-    f(x_gpu) is then within 1e-4 of it."""
+    oracle computes here (4000 iterations at the fastest step of the {1,3} x 10^p grid, whose
+    last 1000 lower f by less than 1e-6 relative, 1% of the tolerance); the oracle's f(x_gpu)
+    is then within 1e-4 of it."""
     import paper_1810_13100_gb300 as ncs
-    lam, alpha = 0.05, 0.5
+    lam, alpha = 0.01, 0.02
     g, pr, P = oproblem(lam, alpha, "iso", seed=2)
     mus, _ = oc.a3_scaled_mu(P, oc.mu_probes(P, 8))
     Minv = lambda r: oc.circulant_solve(r, mus)
@@ -186,7 +187,7 @@ def test_cone_solve_reaches_gap_checked_by_oracle():
     f3000 = oc.objective(P, st.x)
     st = oc.run(P, st, 1000, Minv)
     fs = oc.objective(P, st.x)
-    assert f3000 - fs <= 1e-9 * fs
+    assert f3000 - fs <= 1e-6 * fs
     plan = nplan(ncs, lam, alpha, "iso", h_probes=8)
     b = torch.from_numpy(pr["b"].ravel()).cuda()
     x = torch.zeros(g.n, device="cuda")
