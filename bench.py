@@ -947,23 +947,23 @@ def run_fan(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
-CONE_NCS = dict(alpha=0.01, beta=0.01, h_probes=128)    # the reference run's step and M (oracle/fstar.py)
+CONE_NCS = dict(alpha=0.003, beta=0.003, h_probes=128)  # {1,3} x 10^p grid: fastest to the gap on cone128
 
 
 def run_cone(args, ws, rank, local):
-    """The 128 x 128 x 32 cone-beam TV-CT workload (Sec. 4, cone beam geometry; 180 source positions
-    on a full turn at 256 voxels from the centre, 32 detector rows x 192 equiangular channels, 12
-    ellipsoids, 0.5% noise, isotropic TV lambda 0.005): 3-D NCS iterations/s (L2 flushed before
-    each step, the FP64 objective every 10 steps), per-kernel times, and NCS from zero to the
-    1e-4 gap against the oracle's stored minimum (reported without a convergence claim while that
-    record is not tight)."""
+    """A cone-beam TV-CT workload (Sec. 4, cone beam geometry): cone128, a 128 x 128 x 32 volume,
+    180 source positions on a full turn at 256 voxels from the centre, 32 detector rows x 192
+    equiangular channels, 12 ellipsoids; or cone64, the same proportions at half the size; 0.5%
+    noise, isotropic TV lambda 0.005.  3-D NCS iterations/s (L2 flushed before each step, the
+    FP64 objective every 10 steps), and NCS from zero to the 1e-4 gap against the oracle's stored
+    minimum (reported without a convergence claim while that record is not tight)."""
     import numpy as np
     import torch
     import paper_1810_13100_gb300 as ncs
     import synth
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    W = synth.WORKLOADS["cone128"]
+    W = synth.WORKLOADS[args.workload]
     N, Nz, na, nr, nd, R = W["N"], W["Nz"], W["n_angles"], W["n_rows"], W["n_det"], W["src_dist"]
     pitch = synth.fan_pitch(N, R, nd, W["cover"])
     rp = synth.cone_row_pitch(N, Nz, R, nr, W["cover"])
@@ -1012,7 +1012,7 @@ def run_cone(args, ws, rank, local):
     t_max = reduce_max(t_ms, ws)
     value = reduce_sum(args.steps, ws) / (t_max / 1000.0)
     ttg = None
-    gold = load_golden("cone128", seed)
+    gold = load_golden(args.workload, seed)
     if gold and not args.skip_ttg:
         fs = gold["f_star"]
         bd = b.double()
@@ -1031,13 +1031,14 @@ def run_cone(args, ws, rank, local):
     plan.close()
     cone.close()
     if rank == 0:
-        line = {"metric": "cone-beam 3-D TV-CT NCS iterations/s (128x128x32, 180 views x 32 rows x 192 channels)",
+        shape = "%dx%dx%d, %d views x %d rows x %d channels" % (N, N, Nz, na, nr, nd)
+        line = {"metric": "cone-beam 3-D TV-CT NCS iterations/s (%s)" % shape,
                 "value": value, "unit": "it/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
-                "config": {"workload": "128x128x32 cone-beam TV-CT, 180 views on [0, 2pi), 32 rows x 192 channels, "
-                                       "source at 256 voxels, 12 ellipsoids, 0.5%% noise, iso TV lambda 0.005, "
-                                       "seed %d" % seed, "ncs": CONE_NCS,
+                "config": {"workload": "%s cone-beam TV-CT, views on [0, 2pi), source at %g voxels, %d ellipsoids, "
+                                       "0.5%% noise, iso TV lambda 0.005, seed %d" % (shape, R, W["n_ellipses"], seed),
+                           "ncs": CONE_NCS,
                            "l2": "flushed before every step (256 MiB write, untimed)"},
                 "setup_ms": setup_ms, "time_to_gap": ttg, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
@@ -1124,7 +1125,7 @@ def main():
                     help="PDHG iteration cap on the first seed when it misses the gap within the cap")
     ap.add_argument("--admm-grid", action="store_true",
                     help="time the ADMM comparator over a grid of alpha and n_cg on the first seed")
-    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256", "fan512", "cone128"])
+    ap.add_argument("--workload", default="ct512", choices=["ct512", "batch64", "unet", "pet256", "fan512", "cone128", "cone64"])
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--fan-gather", default="auto", choices=["auto", "lines", "quads"],
                     help="fan-beam K^T kernel (fan512 workload)")
@@ -1144,7 +1145,7 @@ def main():
         run_pet(args, ws, rank, local)
     elif args.workload == "fan512":
         run_fan(args, ws, rank, local)
-    elif args.workload == "cone128":
+    elif args.workload in ("cone128", "cone64"):
         run_cone(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)

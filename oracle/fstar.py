@@ -39,6 +39,7 @@ PARAMS = {
     "fan64": dict(alpha=0.01, beta=0.01, gamma=0.0),
     "fan512": dict(alpha=0.003, beta=0.003, gamma=0.0),
     "cone128": dict(alpha=0.01, beta=0.01, gamma=0.0),
+    "cone64": dict(alpha=0.003, beta=0.003, gamma=0.0),
 }
 
 # probe images of eq. (H-fan) for the fan-beam runs (SplitMix64 seeds 1..FAN_PROBES); with 32

@@ -343,8 +343,9 @@ k_gather(GatherArgs g)
             // the current ray are recomputed at every position
 #pragma unroll
             for (int k = 0; k < GT; ++k) {
-                if (k0 == k - 1) {
-                    acc[k] += vl;
+                const bool adv = k0 == k - 1;
+                acc[k] += adv ? vl : 0.0f;
+                if (adv) {
                     G += step;
                     ui += dir;
                 }
@@ -352,7 +353,7 @@ k_gather(GatherArgs g)
                 wu = U[ui];
                 vr = fmaf(-w, wu, wu);
                 vl = w * wu;
-                if (k0 == k) acc[k] += vr;
+                acc[k] += k0 == k ? vr : 0.0f;
             }
         }
         __syncwarp();

@@ -239,6 +239,10 @@ WORKLOADS = {
     # on a full turn, 32 rows x 192 channels, source at twice the side, 12 ellipsoids.
     "cone128": dict(kind="ct", geometry="cone", N=128, Nz=32, n_angles=180, n_rows=32, n_det=192,
                     src_dist=256.0, cover=1.05, n_ellipses=12, noise_frac=0.005, lam=0.005, tv="iso"),
+    # the same proportions at half the size (64 x 64 x 16, 90 views, 16 rows x 96 channels), small
+    # enough for the FP64 oracle to reach a tight reference minimum
+    "cone64": dict(kind="ct", geometry="cone", N=64, Nz=16, n_angles=90, n_rows=16, n_det=96,
+                   src_dist=128.0, cover=1.05, n_ellipses=8, noise_frac=0.005, lam=0.005, tv="iso"),
 }
 
 
