@@ -49,7 +49,9 @@ TTG_CAP = 2000                      # NCS and ADMM iteration cap of the time-to-
 PDHG_CAP = 20000                    # PDHG needs ~10^4 iterations on this workload
 METRIC = "time to 1e-4 rel. objective gap (512² TV-CT) vs PDHG; NCS iters/s; % HBM roofline"
 # class name of the library's per-kernel timers -> kernel name in ncu's launch list
-NCU_KERNEL = {"joseph_gather": "k_gather", "joseph_fwd": "k_fwd"}
+# ncu kernel names of a kernel class (the strip form of K is two kernels per launch)
+NCU_KERNEL = {"joseph_gather": ["k_gather"], "joseph_fwd": ["k_fwd_strip", "k_fwd_sum"],
+              "joseph_fwd_resid": ["k_fwd_strip", "k_fwd_sum"]}
 
 
 def load_counters(workload, directory=None):
@@ -82,12 +84,19 @@ def load_counters(workload, directory=None):
 
 
 def counters_for(cnt, cls, ncu_name=None):
-    """(dram bytes, warp instructions) per launch of a kernel class, or (None, None) when
-    there is no current capture of it."""
-    c = cnt.get(ncu_name or NCU_KERNEL.get(cls, cls))
-    if not c or not c["current"]:
-        return None, None
-    return c["traffic"], c["warp_instr"]
+    """(dram bytes, warp instructions) per launch of a kernel class (summed over the kernels
+    of one launch), or (None, None) when any of them has no current capture."""
+    names = ncu_name or NCU_KERNEL.get(cls, [cls])
+    if isinstance(names, str):
+        names = [names]
+    traffic = instr = 0.0
+    for nm in names:
+        c = cnt.get(nm)
+        if not c or not c["current"]:
+            return None, None
+        traffic += c["traffic"]
+        instr += c["warp_instr"]
+    return traffic, instr
 
 
 def sm_count(dev):
@@ -529,7 +538,7 @@ def run_ours(args, ws, rank, local):
     N, na, nd = W["N"], W["n_angles"], W["n_det"]
     n, m = N * N, na * nd
     plan = ncs.Plan(N, na, nd, W["lam"], NCS_PARAMS["alpha"], beta=NCS_PARAMS["beta"], gamma=NCS_PARAMS["gamma"],
-                    tv=W["tv"], check_every=CHECK_EVERY, h_probes=NCS_PARAMS["h_probes"])
+                    tv=W["tv"], check_every=CHECK_EVERY, h_probes=NCS_PARAMS["h_probes"], fwd_kernel=args.fwd_kernel)
     W, pr = make_inputs(args.seed + rank, gpu_projector(plan, dev))
     b = torch.from_numpy(pr["b"].ravel()).to(dev)
     x = torch.zeros(n, device=dev)
@@ -587,7 +596,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     kern = plan.profile_read()
     plan.profile(False)
-    launches = sum(c for _, c in kern.values())
+    launches = sum(plan.kernel_launches.values())
 
     # ---- roofline of the dominant kernel (algorithmic work / its duration in the timed region)
     peaks, peak_kind = load_peaks()
@@ -679,7 +688,9 @@ def run_ours(args, ws, rank, local):
                                    "0.5%% noise, seed %d" % args.seed,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": "flushed before every timed step (256 MiB write, untimed)",
-                       "check_every": CHECK_EVERY, "ncs": NCS_PARAMS},
+                       "check_every": CHECK_EVERY, "ncs": NCS_PARAMS,
+                       "fwd_kernel": "strips of %d rows (%d)" % (plan.fwd_strips()[1], plan.fwd_strips()[0])
+                       if plan.fwd_strips()[0] else "row walk"},
             "roofline": roof,
             "iteration_hbm": {"achieved": it_gbs, "peak": hbm, "unit": "GB/s", "frac": it_gbs / hbm,
                               "algorithmic_bytes_per_iter": it_bytes, "peak_kind": peak_kind},
@@ -896,7 +907,7 @@ def run_fan(args, ws, rank, local):
     torch.cuda.synchronize()
     kern = plan.profile_read()
     plan.profile(False)
-    launches = sum(c for _, c in kern.values())
+    launches = sum(plan.kernel_launches.values())
     peaks, peak_kind = load_peaks()
     dom_name = max(kern.items(), key=lambda kv: kv[1][0])[0]
     dom_ms, dom_n = kern_timed[dom_name] if kern_timed.get(dom_name, (0, 0))[1] else kern[dom_name]
@@ -1129,6 +1140,8 @@ def main():
     ap.add_argument("--slices", type=int, default=64)
     ap.add_argument("--fan-gather", default="auto", choices=["auto", "lines", "quads"],
                     help="fan-beam K^T kernel (fan512 workload)")
+    ap.add_argument("--fwd-kernel", default="auto", choices=["auto", "strips", "rows"],
+                    help="parallel-beam K kernel of the ct512 step (the time-to-gap plans take the default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

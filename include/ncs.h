@@ -107,6 +107,12 @@ typedef struct {
                               skipped at creation (PDHG needs only lambda_max(A^T A)); ncs_step, ncs_solve,
                               admm_solve, ncs_apply_Minv, ncs_get_mu and ncs_batch_create then return
                               NCS_ERR_UNSUPPORTED for it, and its report's rho is NaN.  0 (default): full plan */
+    int fwd_kernel;        /* parallel-beam plans, the K kernel (both evaluate the same matrix, summed in a
+                              different order): 0 (default): image strips staged in shared memory where
+                              at most 16 strips cover the image (N up to about 660), else the row walk; 1: the row
+                              walk (each ray reads its rows from L2); 2: strips, NCS_ERR_UNSUPPORTED if the
+                              image is too large for them.  The strip form holds n_strip * n_angles * n_det
+                              floats of scratch (at 512 x 512 with 720 x 730: 10 strips, 21 MB) */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */
@@ -123,7 +129,8 @@ typedef struct ncs_plan ncs_plan;   /* opaque; owns its workspace, tables and so
 
 /* Defaults: beta = NaN (-> alpha), gamma = 0, h_dc = c_r = NaN, kappa = 1, L2 data,
  * anisotropic TV, nonneg 0, FP32, a3_margin 1e-2, power 500 / 1e-6 / seed 0,
- * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0, fan_gather 0, pdhg_only 0. */
+ * check_every 10, NULL stream, autotune 0, warm_dual 0, h_probes 0, fan_gather 0, pdhg_only 0,
+ * fwd_kernel 0. */
 void ncs_options_default(ncs_options* opt);
 
 /* Build a plan for an N x N image (nx == ny == N, N even, N = 2^a 3^b, 8 <= N <= 4096).
@@ -394,6 +401,11 @@ int ncs_get_mu(ncs_plan* plan, double* mu_host);
  * the FFT radix order (fft_radices: host array of at least 12 ints; any pointer may be NULL). */
 int ncs_plan_info(const ncs_plan* plan, int* gather_parts, int* fft_radices, int* n_radices);
 
+/* The plan's K kernel (the fwd_kernel option): *n_strip image strips of *strip_rows rows each
+ * (the last may be shorter) for the strip form, 0 and 0 for the row walk (a fan-beam plan, an
+ * image too large for strips, or fwd_kernel 1).  Either pointer may be NULL. */
+int ncs_plan_fwd_strips(const ncs_plan* plan, int* n_strip, int* strip_rows);
+
 /* Plan sizes: N, n_angles, n_det. */
 int ncs_plan_sizes(const ncs_plan* plan, int* N, int* n_angles, int* n_det);
 
@@ -405,8 +417,8 @@ int ncs_plan_sizes(const ncs_plan* plan, int* N, int* n_angles, int* n_det);
 #define NCS_KERNEL_COLS_SOLVE  2   /* FFT solve: column transforms and 1/mu */
 #define NCS_KERNEL_ROWS_INV    3   /* FFT solve: inverse rows and primal update */
 #define NCS_KERNEL_TD          4   /* D x, TV / nonneg dual prox, transposes, TV sums */
-#define NCS_KERNEL_FWD         5   /* K forward projection with the data prox */
-#define NCS_KERNEL_FWD_RESID   6   /* K forward projection with the FP64 data-term sum */
+#define NCS_KERNEL_FWD         5   /* K forward projection with the data prox (strip pass + strip sum, or row walk) */
+#define NCS_KERNEL_FWD_RESID   6   /* K forward projection with the FP64 data-term sum (the same kernels) */
 #define NCS_KERNEL_REDUCE      7   /* FP64 reductions */
 #define NCS_KERNEL_COUNT       8
 
@@ -421,10 +433,11 @@ int ncs_profile_enable(ncs_plan* plan, int on);
  * Synchronises. */
 int ncs_profile_enable_mask(ncs_plan* plan, unsigned mask);
 
-/* Sum of the recorded kernel durations (ms) and launch counts per class into
- * ms[NCS_KERNEL_COUNT] and launches[NCS_KERNEL_COUNT] (host arrays), then clear
- * the record.  Synchronises. */
-int ncs_profile_read(ncs_plan* plan, double* ms, int* launches);
+/* Sum of the recorded durations (ms) and the number of recorded launches per class into
+ * ms[NCS_KERNEL_COUNT] and launches[NCS_KERNEL_COUNT] (host arrays), and, if kernels is not
+ * NULL, the CUDA kernels those launches enqueued into kernels[NCS_KERNEL_COUNT] (a strip-form
+ * forward projection is one launch of two kernels), then clear the record.  Synchronises. */
+int ncs_profile_read(ncs_plan* plan, double* ms, int* launches, int* kernels);
 
 /* Name of a kernel class (static string). */
 const char* ncs_kernel_name(int kernel_class);

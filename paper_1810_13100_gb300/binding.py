@@ -56,7 +56,7 @@ class Options(ctypes.Structure):
                 ("a3_margin", ctypes.c_double), ("power_max_iter", ctypes.c_int), ("power_tol", ctypes.c_double),
                 ("power_seed", ctypes.c_uint64), ("check_every", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("autotune", ctypes.c_int), ("warm_dual", ctypes.c_int), ("h_probes", ctypes.c_int),
-                ("fan_gather", ctypes.c_int), ("pdhg_only", ctypes.c_int)]
+                ("fan_gather", ctypes.c_int), ("pdhg_only", ctypes.c_int), ("fwd_kernel", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -100,11 +100,12 @@ SIGNATURES = [
     ("ncs_status_string", ctypes.c_char_p, [_I]),
     ("ncs_profile_enable", _I, [_P, _I]),
     ("ncs_profile_enable_mask", _I, [_P, ctypes.c_uint]),
-    ("ncs_profile_read", _I, [_P, _DP, _IP]),
+    ("ncs_profile_read", _I, [_P, _DP, _IP, _IP]),
     ("ncs_kernel_name", ctypes.c_char_p, [_I]),
     ("ncs_plan_nnz", _I, [_P, _DP]),
     ("ncs_apply_KT_static", _I, [ctypes.POINTER(Geometry), _I, _P, _P, _P]),
     ("ncs_plan_info", _I, [_P, _IP, _IP, _IP]),
+    ("ncs_plan_fwd_strips", _I, [_P, _IP, _IP]),
     ("ncs_fbp", _I, [_P, _P, _P]),
     ("ncs_unet_create", _I, [_I, _I, _I, _I, ctypes.c_uint64, ctypes.POINTER(_P)]),
     ("ncs_unet_destroy", None, [_P]),
@@ -205,13 +206,16 @@ class Plan:
     det_offset, angles).  Giving src_dist selects the fan beam (ncs_plan_create_fan):
     n_angles source positions (angles: their beta_a, default 2 pi a / n_angles), n_det
     channels at fan pitch fan_pitch (radians) with centre offset fan_offset; fan_gather picks
-    its K^T kernel ("auto" / "lines": ray-driven tiles, "quads": pixel-driven 2 x 2 quads)."""
+    its K^T kernel ("auto" / "lines": ray-driven tiles, "quads": pixel-driven 2 x 2 quads).
+    fwd_kernel picks the parallel beam's K kernel: "auto" / "strips": image strips staged in
+    shared memory, "rows": the row walk ("auto" takes the row walk where strips do not fit)."""
 
     def __init__(self, N, n_angles, n_det, lam, alpha, *, beta=None, gamma=0.0, h_dc=None, c_r=None,
                  kappa=1.0, data="l2", tv="aniso", nonneg=False, precision="fp32", a3_margin=1e-2,
                  power_max_iter=500, power_tol=1e-6, power_seed=0, check_every=10,
                  det_spacing=1.0, det_offset=0.0, angles=None, stream=None, autotune=False, warm_dual=False,
-                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0, fan_gather="auto", pdhg_only=False):
+                 h_probes=0, src_dist=None, fan_pitch=None, fan_offset=0.0, fan_gather="auto", pdhg_only=False,
+                 fwd_kernel="auto"):
         import torch
         L = load_library()
         self._L = L
@@ -256,6 +260,7 @@ class Plan:
         o.h_probes = int(h_probes)
         o.fan_gather = {"auto": 0, "quads": 1, "lines": 2}[fan_gather]
         o.pdhg_only = 1 if pdhg_only else 0
+        o.fwd_kernel = {"auto": 0, "rows": 1, "strips": 2}[fwd_kernel]
         # With no stream given, the plan runs on a side stream that is ordered
         # after torch's current stream on entry to every call and before it on
         # exit, so results are visible to torch without extra synchronisation.
@@ -428,11 +433,15 @@ class Plan:
         self._call("ncs_profile_enable_mask", self._L.ncs_profile_enable_mask, self._h, mask)
 
     def profile_read(self):
-        """{kernel name: (total ms, launches)} since the last read, then cleared."""
+        """{kernel class: (total ms, launches)} since the last read, then cleared; the CUDA
+        kernels those launches enqueued go to self.kernel_launches ({kernel class: count})."""
         ms = (ctypes.c_double * NCS_KERNEL_COUNT)()
         n = (ctypes.c_int * NCS_KERNEL_COUNT)()
-        self._call("ncs_profile_read", self._L.ncs_profile_read, self._h, ms, n)
-        return {self._L.ncs_kernel_name(k).decode(): (ms[k], n[k]) for k in range(NCS_KERNEL_COUNT)}
+        nk = (ctypes.c_int * NCS_KERNEL_COUNT)()
+        self._call("ncs_profile_read", self._L.ncs_profile_read, self._h, ms, n, nk)
+        names = [self._L.ncs_kernel_name(k).decode() for k in range(NCS_KERNEL_COUNT)]
+        self.kernel_launches = {names[k]: nk[k] for k in range(NCS_KERNEL_COUNT)}
+        return {names[k]: (ms[k], n[k]) for k in range(NCS_KERNEL_COUNT)}
 
     def nnz(self):
         """Nonzero weights of K (2 * nnz flops per application of K or K^T)."""
@@ -446,6 +455,12 @@ class Plan:
         rad = (ctypes.c_int * 12)()
         _check(self._L.ncs_plan_info(self._h, ctypes.byref(gp), rad, ctypes.byref(nr)), "ncs_plan_info")
         return {"gather_parts": gp.value, "fft_radices": [rad[k] for k in range(nr.value)]}
+
+    def fwd_strips(self):
+        """(strips, rows per strip) of the strip form of K, or (0, 0) for the row walk."""
+        ns, nr = ctypes.c_int(), ctypes.c_int()
+        _check(self._L.ncs_plan_fwd_strips(self._h, ctypes.byref(ns), ctypes.byref(nr)), "ncs_plan_fwd_strips")
+        return ns.value, nr.value
 
     def mu(self):
         import numpy as np

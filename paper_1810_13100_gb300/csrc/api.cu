@@ -191,6 +191,9 @@ struct ncs_plan {
     float *d_u = nullptr, *d_v = nullptr, *d_s = nullptr;   // solver state
     int gparts = 1;                  // angle slices of the gather
     float* d_gpart = nullptr;        // gather scratch: gparts * N * N partial sums
+    float* d_spart = nullptr;        // strip form of K: n_strip planes of partial sums (nullptr: row walk)
+    short2* d_wrange = nullptr;      // strip form of K: lines touched per (angle, 32-bin chunk)
+    int n_strip = 0, strip_rows = 0;
     int* d_gcount = nullptr;         // gather scratch: arrival counter per 32 x 32 tile
     double rho = std::numeric_limits<double>::quiet_NaN();
     double lmax = std::numeric_limits<double>::quiet_NaN();
@@ -199,7 +202,7 @@ struct ncs_plan {
     // per-kernel event timing (ncs_profile_enable / ncs_profile_read)
     unsigned prof = 0;            // bit k: kernel class k is timed
     bool capturing = false;
-    struct Rec { int cls; cudaEvent_t a, b; };
+    struct Rec { int cls, n; cudaEvent_t a, b; };   // n: kernels launched between a and b
     std::vector<Rec> recs;
     std::vector<cudaEvent_t> ev_pool;
     double nnz_K = -1.0;
@@ -253,9 +256,9 @@ cudaEvent_t prof_event(ncs_plan* p)
 // profiling is on (never inside graph capture).
 struct ProfScope {
     ncs_plan* p;
-    int cls;
+    int cls, n;
     cudaEvent_t a = nullptr;
-    ProfScope(ncs_plan* p_, int cls_) : p(p_), cls(cls_)
+    ProfScope(ncs_plan* p_, int cls_, int n_ = 1) : p(p_), cls(cls_), n(n_)
     {
         if (((p->prof >> cls) & 1u) && !p->capturing && p->recs.size() < kMaxProfRecords) {
             a = prof_event(p);
@@ -268,7 +271,7 @@ struct ProfScope {
         cudaEvent_t b = prof_event(p);
         if (!b) { p->ev_pool.push_back(a); return; }
         cudaEventRecord(b, p->st);
-        p->recs.push_back({cls, a, b});
+        p->recs.push_back({cls, n, a, b});
     }
 };
 
@@ -276,6 +279,13 @@ struct ProfScope {
     do {                            \
         ProfScope ps_(p, (cls));    \
         CK(expr);                   \
+    } while (0)
+
+// the same for a call that launches n kernels
+#define CKPN(cls, n, expr)             \
+    do {                               \
+        ProfScope ps_(p, (cls), (n));  \
+        CK(expr);                      \
     } while (0)
 
 size_t NN(const ncs_plan* p) { return (size_t)p->N * p->N; }
@@ -328,19 +338,35 @@ int enq_pairs(ncs_plan* p, const float* x, float2* x2, float2* xT2)
     return NCS_OK;
 }
 
-int enq_K(ncs_plan* p, const float2* x2, const float2* xT2, float* y)
+// The projector tables and the strip scratch of a forward launch.
+FwdArgs fwd_args(const ncs_plan* p)
 {
     FwdArgs f{};
-    f.img2 = x2;
-    f.imgT2 = xT2;
     f.ap = p->d_ap;
     f.rays = p->d_rays;
     f.rayw = p->d_rayw;
     f.N = p->N;
     f.n_ang = p->na;
     f.n_det = p->nd;
+    f.order = p->d_order;
+    f.n_row = p->n_row;
+    f.spart = p->d_spart;
+    f.wrange = p->d_wrange;
+    f.n_strip = p->n_strip;
+    f.strip_rows = p->strip_rows;
+    return f;
+}
+
+// kernels one launch_fwd enqueues: the strip pass and the strip sum, or the row walk
+int fwd_kernels(const FwdArgs& f) { return f.spart && !f.rays ? 2 : 1; }
+
+int enq_K(ncs_plan* p, const float2* x2, const float2* xT2, float* y)
+{
+    FwdArgs f = fwd_args(p);
+    f.img2 = x2;
+    f.imgT2 = xT2;
     f.y = y;
-    CKP(NCS_KERNEL_FWD, launch_fwd(FWD_PLAIN, f, p->st));
+    CKPN(NCS_KERNEL_FWD, fwd_kernels(f), launch_fwd(FWD_PLAIN, f, p->st));
     return NCS_OK;
 }
 
@@ -412,15 +438,9 @@ int enq_td_prox(ncs_plan* p, void* v, void* s)
 int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg, float* kx = nullptr,
                  double* partials = nullptr)
 {
-    FwdArgs f{};
+    FwdArgs f = fwd_args(p);
     f.img2 = p->d_xb2;
     f.imgT2 = p->d_xbT2;
-    f.ap = p->d_ap;
-    f.rays = p->d_rays;
-    f.rayw = p->d_rayw;
-    f.N = p->N;
-    f.n_ang = p->na;
-    f.n_det = p->nd;
     f.y = u;
     f.b = b;
     f.bg = bg;
@@ -431,7 +451,7 @@ int enq_fwd_prox(ncs_plan* p, void* u, const float* b, const float* bg, float* k
     f.iter = p->d_iter;
     f.kx = p->kl ? nullptr : kx;
     f.partials = f.kx ? partials : nullptr;
-    CKP(NCS_KERNEL_FWD, launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
+    CKPN(NCS_KERNEL_FWD, fwd_kernels(f), launch_fwd(p->kl ? FWD_PROX_KL : FWD_PROX_L2, f, p->st));
     return NCS_OK;
 }
 
@@ -477,20 +497,14 @@ int enq_objective(ncs_plan* p, const float* x, const float* b, const float* bg, 
     a.iso = p->iso ? 1 : 0;
     a.partials = p->d_part0;
     CKP(NCS_KERNEL_TD, launch_td(TD_OBJ, a, p->st));
-    FwdArgs f{};
+    FwdArgs f = fwd_args(p);
     f.img2 = p->d_tmp2;
     f.imgT2 = p->d_tmpT2;
-    f.ap = p->d_ap;
-    f.rays = p->d_rays;
-    f.rayw = p->d_rayw;
-    f.N = p->N;
-    f.n_ang = p->na;
-    f.n_det = p->nd;
     f.b = b;
     f.bg = bg;
     f.partials = p->d_part1;
-    CKP(NCS_KERNEL_FWD_RESID, launch_fwd(p->kl ? FWD_RESID_KL : FWD_RESID_L2, f, p->st));
-    CKP(NCS_KERNEL_REDUCE, launch_finalize(p->d_part1, fwd_num_blocks(p->nd, p->na), p->kl ? 1.0 : 0.5, p->d_part0,
+    CKPN(NCS_KERNEL_FWD_RESID, fwd_kernels(f), launch_fwd(p->kl ? FWD_RESID_KL : FWD_RESID_L2, f, p->st));
+    CKP(NCS_KERNEL_REDUCE, launch_finalize(p->d_part1, fwd_num_partials(f), p->kl ? 1.0 : 0.5, p->d_part0,
                        td_num_blocks(p->N), p->lam, p->d_scal + slot, p->st));
     return NCS_OK;
 }
@@ -655,7 +669,7 @@ void free_plan(ncs_plan* p)
     cudaFree(p->d_xb2); cudaFree(p->d_xbT2); cudaFree(p->d_tmp2); cudaFree(p->d_tmpT2);
     cudaFree(p->d_spec); cudaFree(p->d_part0); cudaFree(p->d_part1); cudaFree(p->d_scal);
     cudaFree(p->d_u); cudaFree(p->d_v); cudaFree(p->d_s); cudaFree(p->d_kx); cudaFree(p->d_adm); cudaFree(p->d_bfpair);
-    cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter); cudaFree(p->d_q);
+    cudaFree(p->d_gpart); cudaFree(p->d_gcount); cudaFree(p->d_iter); cudaFree(p->d_q); cudaFree(p->d_spart); cudaFree(p->d_wrange);
     if (p->h_pin) cudaFreeHost(p->h_pin);
     if (p->own_stream && p->st) cudaStreamDestroy(p->st);
 }
@@ -801,11 +815,25 @@ int build_common(ncs_plan* p)
     const size_t slices = p->fan ? (size_t)std::max(fan_lines_parts(N, na), fan_gather_parts(N, na)) : p->gparts;
     CKS(dalloc(&p->d_gpart, slices > 1 ? slices * n : 1));
     CKS(dalloc(&p->d_gcount, counters));
+    // K in strips (k_fwd_strip) unless the options ask for the row walk or the image is too large
+    if (!p->fan && p->opt.fwd_kernel != 1) {
+        if (fwd_strip_shape(N, &p->strip_rows, &p->n_strip)) {
+            CK(fwd_prepare());
+            CKS(dalloc(&p->d_spart, (size_t)p->n_strip * fwd_strip_plane(na, nd)));
+            std::vector<short2> wr;
+            fwd_warp_ranges(N, nd, p->h_ap, wr);
+            CKS(dalloc(&p->d_wrange, wr.size()));
+            CK(cudaMemcpyAsync(p->d_wrange, wr.data(), wr.size() * sizeof(short2), cudaMemcpyHostToDevice, p->st));
+            CK(cudaStreamSynchronize(p->st));
+        } else if (p->opt.fwd_kernel == 2) {
+            return NCS_ERR_UNSUPPORTED;
+        }
+    }
     CKS(dalloc(&p->d_iter, 1));
     CK(cudaMemsetAsync(p->d_iter, 0, sizeof(unsigned long long), p->st));
     CK(cudaMemsetAsync(p->d_gcount, 0, counters * sizeof(int), p->st));
     CKS(dalloc(&p->d_part0, kMaxPartials));
-    CKS(dalloc(&p->d_part1, (size_t)fwd_num_blocks(nd, na)));
+    CKS(dalloc(&p->d_part1, (size_t)std::max(fwd_num_blocks(nd, na), (int)((size_t)na * nd / 1024 + 1))));
     CKS(dalloc(&p->d_scal, 16));
     if (cudaMallocHost((void**)&p->h_pin, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
@@ -999,7 +1027,7 @@ int enq_objective_tv(ncs_plan* p, const float* x, int slot)
     a.iso = p->iso ? 1 : 0;
     a.partials = p->d_part0;
     CKP(NCS_KERNEL_TD, launch_td(TD_OBJ, a, p->st));
-    CKP(NCS_KERNEL_REDUCE, launch_finalize(p->d_part1, fwd_num_blocks(p->nd, p->na), 0.5, p->d_part0,
+    CKP(NCS_KERNEL_REDUCE, launch_finalize(p->d_part1, fwd_num_partials(fwd_args(p)), 0.5, p->d_part0,
                        td_num_blocks(p->N), p->lam, p->d_scal + slot, p->st));
     return NCS_OK;
 }
@@ -1318,6 +1346,7 @@ void ncs_options_default(ncs_options* o)
     o->h_probes = 0;
     o->fan_gather = 0;
     o->pdhg_only = 0;
+    o->fwd_kernel = 0;
 }
 
 int ncs_plan_create(const ncs_geometry* geom, int nx, int ny, double lambda, double alpha, const ncs_options* opt,
@@ -1368,6 +1397,7 @@ int ncs_plan_create_fan(const ncs_fan_geometry* geom, int nx, int ny, double lam
     // frequencies far too low (512x512 fan: rho(M^{-1} alpha A^T A) 47 with 32 probes, 8.7 with 128)
     if (o.h_probes == 0) o.h_probes = 128;
     if (o.fan_gather < 0 || o.fan_gather > 2) return NCS_ERR_BADARG;
+    if (o.fwd_kernel < 0 || o.fwd_kernel > 2) return NCS_ERR_BADARG;
     ncs_plan* p = nullptr;
     CKS(new_plan(nx, ny, geom->n_views, geom->n_det, lambda, alpha, &o, &p));
     p->fan_lines = o.fan_gather != 1;
@@ -1487,18 +1517,12 @@ int ncs_apply_K_bf16(ncs_plan* p, const float* x, float* y)
     a.N = p->N;
     a.pair_bf = 1;
     CKP(NCS_KERNEL_TD, launch_td(TD_TRANSPOSE, a, p->st));
-    FwdArgs f{};
+    FwdArgs f = fwd_args(p);
     f.img2 = x2;
     f.imgT2 = xT2;
     f.pair_bf = 1;
-    f.ap = p->d_ap;
-    f.rays = p->d_rays;
-    f.rayw = p->d_rayw;
-    f.N = p->N;
-    f.n_ang = p->na;
-    f.n_det = p->nd;
     f.y = y;
-    CKP(NCS_KERNEL_FWD, launch_fwd(FWD_PLAIN, f, p->st));
+    CKPN(NCS_KERNEL_FWD, fwd_kernels(f), launch_fwd(FWD_PLAIN, f, p->st));
     return NCS_OK;
 }
 
@@ -1590,6 +1614,14 @@ int ncs_plan_info(const ncs_plan* p, int* gather_parts, int* fft_radices, int* n
     if (n_radices) *n_radices = p->rp.n;
     if (fft_radices)
         for (int k = 0; k < p->rp.n; ++k) fft_radices[k] = p->rp.r[k];
+    return NCS_OK;
+}
+
+int ncs_plan_fwd_strips(const ncs_plan* p, int* n_strip, int* strip_rows)
+{
+    CKS(check_plan(p));
+    if (n_strip) *n_strip = p->d_spart ? p->n_strip : 0;
+    if (strip_rows) *strip_rows = p->d_spart ? p->strip_rows : 0;
     return NCS_OK;
 }
 
@@ -1803,19 +1835,24 @@ int ncs_profile_enable(ncs_plan* p, int on)
     return ncs_profile_enable_mask(p, on ? ~0u : 0u);
 }
 
-int ncs_profile_read(ncs_plan* p, double* ms, int* launches)
+int ncs_profile_read(ncs_plan* p, double* ms, int* launches, int* kernels)
 {
     CKS(check_plan(p));
     if (!ms || !launches) return NCS_ERR_BADARG;
     CK(cudaSetDevice(p->dev));
     CK(cudaStreamSynchronize(p->st));
-    for (int k = 0; k < NCS_KERNEL_COUNT; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (int k = 0; k < NCS_KERNEL_COUNT; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+        if (kernels) kernels[k] = 0;
+    }
     int rc = NCS_OK;
     for (auto& r : p->recs) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) { cudaGetLastError(); rc = NCS_ERR_CUDA; }
         ms[r.cls] += t;
         launches[r.cls] += 1;
+        if (kernels) kernels[r.cls] += r.n;
         p->ev_pool.push_back(r.a);
         p->ev_pool.push_back(r.b);
     }

@@ -24,6 +24,9 @@
 // K^T is a pixel-driven gather (k_gather_fan) that evaluates the same weights.
 #include "ncs_internal.cuh"
 
+#include <algorithm>
+#include <climits>
+
 namespace ncs {
 
 namespace {
@@ -68,6 +71,91 @@ __device__ __forceinline__ float kl_conj_prox(float z, float c)
     return d > 0.0f ? 1.0f - 2.0f * c / (d + root) : 1.0f + 0.5f * (d - root);
 }
 
+// Lines [jlo, jhi) of the stepping axis where a ray f = f0 + B q can touch the image:
+// f in [-1, N), found in FP32 with a 2-line margin (|B| <= 1, so f stays in (-4, N + 3) on
+// every line of the range and the pair image's zero border absorbs the steps outside the
+// image).  Every line outside the range has f outside [-1, N), where both taps are zero.
+__device__ __forceinline__ void fwd_lines(float f0, float B, int N, int& jlo, int& jhi)
+{
+    jlo = 0;
+    jhi = N;
+    if (fabsf(B) > 1e-6f) {
+        float j1 = (-1.0f - f0) / B, j2 = ((float)N - f0) / B;
+        float lo = fminf(j1, j2), hi = fmaxf(j1, j2);
+        lo = fmaxf(lo, -4.0f);
+        hi = fminf(hi, (float)N + 4.0f);
+        jlo = max(0, (int)floorf(lo) - 2);
+        jhi = min(N, (int)ceilf(hi) + 2);
+    } else if (!(f0 > -3.0f && f0 < (float)N + 2.0f)) {
+        jhi = 0;
+    }
+}
+
+// The mode's epilogue for sinogram entry idx with y = (K x)[idx]: the prox of the data dual
+// (Sec. 4.1: divide by 1 + alpha; Sec. 4.2: the closed-form S(u; c)), the running K x, or a
+// data-term summand.  Returns the FP64 summand (0 where the mode has none).
+template <int MODE, bool SBF>
+__device__ __forceinline__ double fwd_finish(const FwdArgs& g, size_t idx, float y)
+{
+    double term = 0.0;
+    if (MODE == FWD_PLAIN) {
+        St<false>::put(g.y, idx, y);
+    } else if (MODE == FWD_PROX_L2) {
+        const float bv = St<false>::ld(g.b, idx);
+        const float z = fmaf(g.alpha, y - bv, St<SBF>::get(g.y, idx));
+        St<SBF>::put_sr(g.y, idx, z * g.inv1pa, SBF ? rand16(*g.iter, idx, 1u) : 0u);
+        if (g.kx) {
+            // x+ = (xbar + x) / 2, so K x+ = (K xbar + K x) / 2 without another projection
+            const float kxp = 0.5f * (y + g.kx[idx]);
+            g.kx[idx] = kxp;
+            const double d = (double)kxp - (double)bv;
+            term = d * d;
+        }
+    } else if (MODE == FWD_PROX_KL) {
+        const float bgv = g.bg ? St<false>::ld(g.bg, idx) : 0.0f;
+        const float z = fmaf(g.alpha, y + bgv, St<SBF>::get(g.y, idx));
+        St<SBF>::put_sr(g.y, idx, kl_conj_prox(z, g.alpha * St<false>::ld(g.b, idx)),
+                        SBF ? rand16(*g.iter, idx, 1u) : 0u);
+    } else if (MODE == FWD_RESID_L2) {
+        const double d = (double)y - (double)St<false>::ld(g.b, idx);
+        term = d * d;
+    } else {  // FWD_RESID_KL
+        const double mu = (double)y + (g.bg ? (double)St<false>::ld(g.bg, idx) : 0.0);
+        const double bb = (double)St<false>::ld(g.b, idx);
+        term = mu - bb;
+        if (bb > 0.0) term += bb * log(bb / mu);
+    }
+    return term;
+}
+
+// The end of a forward launch in a (FWD_TB x FWD_SEG) block for ray (a, t): the FWD_SEG
+// partial sums in red are added in a fixed order and scaled by the path length Wr, and the
+// mode's epilogue runs; the RESID modes (and PROX_L2 with a running K x) leave one FP64
+// partial sum per block.  Called by every thread of the block.
+template <int MODE, bool SBF>
+__device__ __forceinline__ void fwd_epilogue(const FwdArgs& g, int a, int t, float Wr, float (*red)[FWD_TB],
+                                             double* dred)
+{
+    __syncthreads();
+    double term = 0.0;
+    if (threadIdx.y == 0 && t < g.n_det) {
+        float tot = red[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < FWD_SEG; ++q) tot += red[q][threadIdx.x];
+        term = fwd_finish<MODE, SBF>(g, (size_t)a * g.n_det + t, Wr * tot);
+    }
+    if (MODE == FWD_RESID_L2 || MODE == FWD_RESID_KL || (MODE == FWD_PROX_L2 && g.partials)) {
+        if (threadIdx.y == 0) dred[threadIdx.x] = term;
+        __syncthreads();
+        if (threadIdx.y == 0 && threadIdx.x < 32) {
+            double s = dred[threadIdx.x] + dred[threadIdx.x + 32];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+            if (threadIdx.x == 0) g.partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+        }
+    }
+}
+
 // FAN: the ray's coefficients come from the per-ray table (fan beam) instead of the
 // block's angle; with no per-bin term the crossing is H = Bhi q + Chi, L = Blo q + Clo.
 template <int MODE, bool PBF, bool SBF, bool FAN>
@@ -109,21 +197,9 @@ k_fwd(FwdArgs g)
     const int N = g.N;
     float acc = 0.0f;
     if (t < g.n_det) {
-        // Rows where the ray can touch the image: f in [-1, N).  Found in FP32
-        // with a 2-row margin (|B| <= 1, so f stays in (-4, N + 3) on every
-        // processed row and the pair image's zero border absorbs the steps
-        // outside the image).
-        int jlo = 0, jhi = N;
-        if (fabsf(B) > 1e-6f) {
-            float j1 = (-1.0f - f0) / B, j2 = ((float)N - f0) / B;
-            float lo = fminf(j1, j2), hi = fmaxf(j1, j2);
-            lo = fmaxf(lo, -4.0f);
-            hi = fminf(hi, (float)N + 4.0f);
-            jlo = max(0, (int)floorf(lo) - 2);
-            jhi = min(N, (int)ceilf(hi) + 2);
-        } else if (!(f0 > -3.0f && f0 < (float)N + 2.0f)) {
-            jhi = 0;
-        }
+        // rows where the ray can touch the image
+        int jlo, jhi;
+        fwd_lines(f0, B, N, jlo, jhi);
         const int len = max(0, jhi - jlo);
         const int chunk = (len + FWD_SEG - 1) / FWD_SEG;
         const int js = jlo + threadIdx.y * chunk;
@@ -177,50 +253,153 @@ k_fwd(FwdArgs g)
         }
     }
     red[threadIdx.y][threadIdx.x] = acc;
+    fwd_epilogue<MODE, SBF>(g, a, t, Wr, red, dred);
+}
+
+// Strip form of the parallel-beam K.  A block holds image rows [r0, r0 + R) of x (row-branch
+// angles) or of x^T (column-branch angles) in shared memory, x[j][i] at column i + PAIR_PAD
+// of a row of SPC floats (N + 2 PAIR_PAD of them used, zeros beyond the image), and runs a
+// slice of that branch's angles through it: one warp per 32 consecutive bins of one angle,
+// lane = ray.  The strip is read from L2 once per block instead of once per angle.  The warp
+// walks the lines of the strip that any of its rays touches (a host table of exact 32.32
+// ranges, wrange), all lanes on the same line, so the two tap loads of a step hit one row of
+// shared memory; a line outside a lane's own range contributes an exact zero (its crossing
+// lies outside [-1, N), and the tap index is clamped to the zero border).  The sum over the
+// strip goes to plane s of spart; k_fwd_sum adds the planes in strip order and runs the
+// epilogue.  Rows are stepped with the same 32.32 crossing and fix_weight as k_fwd and the
+// gather, so all three hold one matrix.  SPC is a compile-time row pitch (fwd_strip_pitch),
+// so the four rows of an unrolled step sit at constant offsets from one another.
+constexpr int FS_WARPS = 16;                 // warps per strip block (two blocks per SM)
+constexpr int FSUM_T = 256;                  // threads per block of the strip sum, 4 rays each
+constexpr int FS_SMEM = 110 * 1024;          // strip bytes per block
+constexpr int FWD_MAX_STRIPS = 16;
+constexpr int FS_PITCHES[] = {72, 136, 264, 392, 520, 656};   // strip row pitches (floats)
+
+template <bool PBF, int SPC>
+__global__ void __launch_bounds__(FS_WARPS * 32, 2)
+k_fwd_strip(FwdArgs g)
+{
+    extern __shared__ float strip[];
+    const int N = g.N, SP = pair_pitch(N);
+    const int r0 = blockIdx.y * g.strip_rows;
+    const int nr = min(g.strip_rows, N - r0);
+    const bool colb = blockIdx.z != 0;
+    const void* im2 = colb ? g.imgT2 : g.img2;
+    // pair entry c of a row holds (x[c - PAIR_PAD], x[c + 1 - PAIR_PAD]): the even entries fill
+    // the strip's row two floats at a time
+    const int half = (SP + 1) >> 1;
+    for (int e = threadIdx.x; e < nr * half; e += FS_WARPS * 32) {
+        const int i = e / half;
+        const int c = 2 * (e - i * half);
+        const float2 v = St<PBF>::ld2(im2, (ptrdiff_t)(r0 + i) * SP + c);
+        strip[i * SPC + c] = v.x;
+        if (c + 1 < SP) strip[i * SPC + c + 1] = v.y;
+    }
     __syncthreads();
-    double term = 0.0;
-    if (threadIdx.y == 0 && t < g.n_det) {
-        float tot = red[0][threadIdx.x];
-#pragma unroll
-        for (int q = 1; q < FWD_SEG; ++q) tot += red[q][threadIdx.x];
-        const float y = Wr * tot;
-        const size_t idx = (size_t)a * g.n_det + t;
-        if (MODE == FWD_PLAIN) {
-            St<false>::put(g.y, idx, y);
-        } else if (MODE == FWD_PROX_L2) {
-            const float bv = St<false>::ld(g.b, idx);
-            const float z = fmaf(g.alpha, y - bv, St<SBF>::get(g.y, idx));
-            St<SBF>::put_sr(g.y, idx, z * g.inv1pa, SBF ? rand16(*g.iter, idx, 1u) : 0u);
-            if (g.kx) {
-                // x+ = (xbar + x) / 2, so K x+ = (K xbar + K x) / 2 without another projection
-                const float kxp = 0.5f * (y + g.kx[idx]);
-                g.kx[idx] = kxp;
-                const double d = (double)kxp - (double)bv;
-                term = d * d;
+    const int nb = colb ? g.n_ang - g.n_row : g.n_row;
+    const int* list = g.order + (colb ? g.n_row : 0);
+    const int per = (nb + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * per;
+    const int cnt = max(0, min(nb, lo + per) - lo);
+    const int chunks = (g.n_det + 31) >> 5;
+    const int lane = threadIdx.x & 31;
+    float* out = g.spart + (size_t)blockIdx.y * fwd_strip_plane(g.n_ang, g.n_det);
+    const unsigned last = (unsigned)(SP - 2);      // the last tap pair inside a strip row
+    for (int it = threadIdx.x >> 5; it < cnt * chunks; it += FS_WARPS) {
+        const int ai = it / chunks;
+        const int c = it - ai * chunks;
+        const int a = __ldg(list + lo + ai);
+        const int t = c * 32 + lane;
+        const short2 wr = __ldg(g.wrange + (size_t)a * chunks + c);
+        const int wa = max((int)wr.x, r0);
+        const int wb = min((int)wr.y, r0 + nr);
+        float acc = 0.0f;
+        if (wa < wb) {
+            const AngleParam& p = g.ap[a];
+            const long long Bi = p.Bi;
+            // crossing of line wa, 32.32, biased by PAIR_PAD so that its integer part is the
+            // strip column of the first tap
+            long long F = p.Ai * (long long)t + p.Ci + Bi * (long long)wa + ((long long)PAIR_PAD << 32);
+            int ro = (wa - r0) * SPC;                       // strip offset of line j
+            int j = wa;
+            for (; j + 4 <= wb; j += 4) {
+                int k0, k1, k2, k3;
+                const float w0 = fix_weight(F, k0);
+                const float w1 = fix_weight(F + Bi, k1);
+                const float w2 = fix_weight(F + 2 * Bi, k2);
+                const float w3 = fix_weight(F + 3 * Bi, k3);
+                const float* q0 = strip + ro + min((unsigned)k0, last);
+                const float* q1 = strip + ro + min((unsigned)k1, last);
+                const float* q2 = strip + ro + min((unsigned)k2, last);
+                const float* q3 = strip + ro + min((unsigned)k3, last);
+                acc = fmaf(1.0f - w0, q0[0], acc);
+                acc = fmaf(w0, q0[1], acc);
+                acc = fmaf(1.0f - w1, q1[SPC], acc);
+                acc = fmaf(w1, q1[SPC + 1], acc);
+                acc = fmaf(1.0f - w2, q2[2 * SPC], acc);
+                acc = fmaf(w2, q2[2 * SPC + 1], acc);
+                acc = fmaf(1.0f - w3, q3[3 * SPC], acc);
+                acc = fmaf(w3, q3[3 * SPC + 1], acc);
+                F += 4 * Bi;
+                ro += 4 * SPC;
             }
-        } else if (MODE == FWD_PROX_KL) {
-            const float bgv = g.bg ? St<false>::ld(g.bg, idx) : 0.0f;
-            const float z = fmaf(g.alpha, y + bgv, St<SBF>::get(g.y, idx));
-            St<SBF>::put_sr(g.y, idx, kl_conj_prox(z, g.alpha * St<false>::ld(g.b, idx)),
-                            SBF ? rand16(*g.iter, idx, 1u) : 0u);
-        } else if (MODE == FWD_RESID_L2) {
-            const double d = (double)y - (double)St<false>::ld(g.b, idx);
-            term = d * d;
-        } else {  // FWD_RESID_KL
-            const double mu = (double)y + (g.bg ? (double)St<false>::ld(g.bg, idx) : 0.0);
-            const double bb = (double)St<false>::ld(g.b, idx);
-            term = mu - bb;
-            if (bb > 0.0) term += bb * log(bb / mu);
+            for (; j < wb; ++j) {
+                int k0;
+                const float w = fix_weight(F, k0);
+                const float* q = strip + ro + min((unsigned)k0, last);
+                acc = fmaf(1.0f - w, q[0], acc);
+                acc = fmaf(w, q[1], acc);
+                F += Bi;
+                ro += SPC;
+            }
+        }
+        if (t < g.n_det) out[(size_t)a * g.n_det + t] = acc;
+    }
+}
+
+// Sum of the strip planes of k_fwd_strip in strip order, then the epilogue of k_fwd: a thread
+// takes four consecutive sinogram entries (one 16-byte load per plane; planes are padded to a
+// multiple of four entries), and a block leaves one FP64 partial sum in the modes that have one.
+template <int MODE, bool SBF>
+__global__ void __launch_bounds__(FSUM_T)
+k_fwd_sum(FwdArgs g)
+{
+    __shared__ double dred[FSUM_T / 32];
+    const unsigned m = (unsigned)g.n_ang * (unsigned)g.n_det;
+    const size_t plane = fwd_strip_plane(g.n_ang, g.n_det);
+    const unsigned i0 = (blockIdx.x * FSUM_T + threadIdx.x) * 4u;
+    double term = 0.0;
+    if (i0 < m) {
+        const float4* src = reinterpret_cast<const float4*>(g.spart + i0);
+        const size_t pl4 = plane / 4;
+        float4 tot = src[0];
+#pragma unroll
+        for (int q = 1; q < FWD_MAX_STRIPS; ++q) {
+            if (q < g.n_strip) {
+                const float4 v = src[q * pl4];
+                tot.x += v.x;
+                tot.y += v.y;
+                tot.z += v.z;
+                tot.w += v.w;
+            }
+        }
+        const float tv[4] = {tot.x, tot.y, tot.z, tot.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const unsigned i = i0 + e;
+            if (i < m) term += fwd_finish<MODE, SBF>(g, i, g.ap[i / (unsigned)g.n_det].W * tv[e]);
         }
     }
     if (MODE == FWD_RESID_L2 || MODE == FWD_RESID_KL || (MODE == FWD_PROX_L2 && g.partials)) {
-        if (threadIdx.y == 0) dred[threadIdx.x] = term;
-        __syncthreads();
-        if (threadIdx.y == 0 && threadIdx.x < 32) {
-            double s = dred[threadIdx.x] + dred[threadIdx.x + 32];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-            if (threadIdx.x == 0) g.partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
+        for (int o = 16; o > 0; o >>= 1) term += __shfl_down_sync(0xffffffffu, term, o);
+        if ((threadIdx.x & 31) == 0) dred[threadIdx.x >> 5] = term;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sum = dred[0];
+#pragma unroll
+            for (int w = 1; w < FSUM_T / 32; ++w) sum += dred[w];
+            g.partials[blockIdx.x] = sum;
         }
     }
 }
@@ -709,12 +888,139 @@ void fwd_dispatch_prec(int mode, const FwdArgs& a, dim3 grid, dim3 block, cudaSt
     else fwd_dispatch<false, false, FAN>(mode, a, grid, block, st);
 }
 
+// Row pitch (floats) of the strip kernel's shared-memory rows for an N x N image: the
+// smallest of FS_PITCHES that holds N + 2 PAIR_PAD floats, or 0 if none does.
+int fwd_strip_pitch(int N)
+{
+    for (int sp : FS_PITCHES)
+        if (sp >= pair_pitch(N)) return sp;
+    return 0;
+}
+
+// Strip shape of the parallel-beam K for an N x N image: the rows per strip that leave room
+// for two blocks per SM (FS_SMEM bytes each) and the number of strips; false when more than
+// FWD_MAX_STRIPS would be needed (the row walk k_fwd serves such images).
+bool fwd_strip_shape(int N, int* rows, int* strips)
+{
+    const int sp = fwd_strip_pitch(N);
+    if (N < 1 || sp == 0) return false;
+    const int rmax = FS_SMEM / (int)(sizeof(float) * sp);
+    const int s = (N + rmax - 1) / rmax;
+    if (s > FWD_MAX_STRIPS) return false;
+    *strips = s;
+    *rows = (N + s - 1) / s;
+    return true;
+}
+
+template <bool PBF, int SPC>
+cudaError_t fwd_strip_attr()
+{
+    return cudaFuncSetAttribute(k_fwd_strip<PBF, SPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, FS_SMEM);
+}
+
+// Opt-in to FS_SMEM bytes of dynamic shared memory for the strip kernels (once, before the
+// first launch and outside any stream capture).
+cudaError_t fwd_prepare()
+{
+    const cudaError_t e[] = {fwd_strip_attr<false, 72>(), fwd_strip_attr<false, 136>(), fwd_strip_attr<false, 264>(),
+                             fwd_strip_attr<false, 392>(), fwd_strip_attr<false, 520>(), fwd_strip_attr<false, 656>(),
+                             fwd_strip_attr<true, 72>(), fwd_strip_attr<true, 136>(), fwd_strip_attr<true, 264>(),
+                             fwd_strip_attr<true, 392>(), fwd_strip_attr<true, 520>(), fwd_strip_attr<true, 656>()};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
+}
+
+template <bool PBF>
+void fwd_strip_dispatch(int sp, const FwdArgs& a, dim3 grid, size_t smem, cudaStream_t st)
+{
+    switch (sp) {
+        case 72: k_fwd_strip<PBF, 72><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        case 136: k_fwd_strip<PBF, 136><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        case 264: k_fwd_strip<PBF, 264><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        case 392: k_fwd_strip<PBF, 392><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        case 520: k_fwd_strip<PBF, 520><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        default: k_fwd_strip<PBF, 656><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+    }
+}
+
+// Per (angle, 32-bin chunk) the lines [lo, hi) of the stepping axis on which some ray of the
+// chunk touches the image (its 32.32 crossing F has F >> 32 in [-1, N - 1]): exact, in 64-bit
+// integers.  F is linear in t and in the line q with the same slope Bi for every ray, so the
+// lines form one interval.  Rays past n_det are left out; an empty chunk gets lo = hi = 0.
+void fwd_warp_ranges(int N, int n_det, const std::vector<AngleParam>& ap, std::vector<short2>& out)
+{
+    const int chunks = (n_det + 31) / 32;
+    out.assign(ap.size() * chunks, short2{0, 0});
+    const long long lo_f = -(1LL << 32), hi_f = (long long)N << 32;
+    for (size_t a = 0; a < ap.size(); ++a) {
+        const AngleParam& p = ap[a];
+        for (int c = 0; c < chunks; ++c) {
+            const int t0 = 32 * c, t1 = std::min(n_det - 1, t0 + 31);
+            const long long f0 = p.Ai * t0 + p.Ci, f1 = p.Ai * t1 + p.Ci;
+            const long long fmin = std::min(f0, f1), fmax = std::max(f0, f1);
+            int lo = -1, hi = -1;
+            for (int q = 0; q < N; ++q) {
+                const long long d = p.Bi * (long long)q;
+                if (fmax + d >= lo_f && fmin + d < hi_f) {
+                    if (lo < 0) lo = q;
+                    hi = q + 1;
+                }
+            }
+            if (lo >= 0) out[a * chunks + c] = short2{(short)lo, (short)hi};
+        }
+    }
+}
+
+// FP64 partial sums one RESID launch (or PROX_L2 launch with a running K x) leaves
+int fwd_num_partials(const FwdArgs& a)
+{
+    if (a.spart && !a.rays) {
+        const long long m = (long long)a.n_ang * a.n_det;
+        return (int)((m + 4LL * FSUM_T - 1) / (4LL * FSUM_T));
+    }
+    return fwd_num_blocks(a.n_det, a.n_ang);
+}
+
+template <bool SBF>
+void fwd_sum_dispatch(int mode, const FwdArgs& a, dim3 grid, dim3 block, cudaStream_t st)
+{
+    switch (mode) {
+        case FWD_PLAIN: k_fwd_sum<FWD_PLAIN, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_PROX_L2: k_fwd_sum<FWD_PROX_L2, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_PROX_KL: k_fwd_sum<FWD_PROX_KL, SBF><<<grid, block, 0, st>>>(a); break;
+        case FWD_RESID_L2: k_fwd_sum<FWD_RESID_L2, SBF><<<grid, block, 0, st>>>(a); break;
+        default: k_fwd_sum<FWD_RESID_KL, SBF><<<grid, block, 0, st>>>(a); break;
+    }
+}
+
 cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st)
 {
     if (mode < FWD_PLAIN || mode > FWD_RESID_KL) return cudaErrorInvalidValue;
     if (mode == FWD_PLAIN && a.sino_bf) return cudaErrorInvalidValue;    // y is float
     if (a.rays && !a.rayw) return cudaErrorInvalidValue;
     dim3 grid((a.n_det + FWD_TB - 1) / FWD_TB, a.n_ang), block(FWD_TB, FWD_SEG);
+    if (a.spart && !a.rays) {
+        const int sp = fwd_strip_pitch(a.N);
+        if (!a.order || !a.ap || !a.wrange || sp == 0 || a.n_row < 0 || a.n_row > a.n_ang || a.n_strip < 1 ||
+            a.strip_rows < 1 || a.n_strip > FWD_MAX_STRIPS || (long long)a.n_strip * a.strip_rows < a.N ||
+            (long long)(a.n_strip - 1) * a.strip_rows >= a.N ||
+            (size_t)a.strip_rows * sp * sizeof(float) > (size_t)FS_SMEM || a.N > 32767)
+            return cudaErrorInvalidValue;
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        // two resident blocks per SM: n_strip x 2 branches x G angle slices fill them once
+        const dim3 sgrid(std::max(1, sms / a.n_strip), a.n_strip, 2);
+        const size_t smem = (size_t)a.strip_rows * sp * sizeof(float);
+        if (a.pair_bf) fwd_strip_dispatch<true>(sp, a, sgrid, smem, st);
+        else fwd_strip_dispatch<false>(sp, a, sgrid, smem, st);
+        const dim3 sum_grid((unsigned)fwd_num_partials(a)), sum_block(FSUM_T);
+        if (a.sino_bf) fwd_sum_dispatch<true>(mode, a, sum_grid, sum_block, st);
+        else fwd_sum_dispatch<false>(mode, a, sum_grid, sum_block, st);
+        return cudaGetLastError();
+    }
     if (a.rays) fwd_dispatch_prec<true>(mode, a, grid, block, st);
     else fwd_dispatch_prec<false>(mode, a, grid, block, st);
     return cudaGetLastError();

@@ -132,6 +132,13 @@ using FanView = float4;
 constexpr int PAIR_PAD = 4;
 inline __host__ __device__ int pair_pitch(int N) { return N + 2 * PAIR_PAD; }
 
+// Entries of one strip plane of the strip-form K's scratch: n_ang * n_det rounded up to a
+// multiple of 4, so that every plane starts on a 16-byte boundary.
+inline __host__ __device__ size_t fwd_strip_plane(int n_ang, int n_det)
+{
+    return ((size_t)n_ang * (size_t)n_det + 3) & ~(size_t)3;
+}
+
 // Forward-projection epilogues.
 enum FwdMode {
     FWD_PLAIN = 0,     // y = K x
@@ -158,6 +165,12 @@ struct FwdArgs {
     float* kx;           // PROX_L2 or nullptr: running K x, updated to (K xbar + K x) / 2 = K x+
     const FanRay* rays;  // fan beam: per-ray table (ap unused), or nullptr for the parallel beam
     const float* rayw;   // fan beam: signed path length per ray
+    // parallel beam, strip form (k_fwd_strip): spart non-null selects it
+    const int* order;    // angle indices, the n_row row-branch ones first (angle_order)
+    int n_row;
+    float* spart;        // scratch: n_strip planes of fwd_strip_plane(n_ang, n_det) partial sums
+    const short2* wrange;  // per (angle, 32-bin chunk): lines touched by the chunk's rays (fwd_warp_ranges)
+    int n_strip, strip_rows;  // strips of strip_rows image rows (fwd_strip_shape)
 };
 
 // Gather epilogues.
@@ -252,6 +265,10 @@ bool fan_ray_tables(int N, int na, int nd, double R, double pitch, double offset
 // ---- launchers (all asynchronous on `st`) ----
 cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st);
 int fwd_num_blocks(int n_det, int n_ang);
+bool fwd_strip_shape(int N, int* rows, int* strips);
+void fwd_warp_ranges(int N, int n_det, const std::vector<AngleParam>& ap, std::vector<short2>& out);
+int fwd_num_partials(const FwdArgs& a);
+cudaError_t fwd_prepare();
 cudaError_t launch_gather(int mode, const GatherArgs& a, cudaStream_t st);
 int gather_parts(int N, int n_ang);          // angle slices the gather uses for this size
 size_t gather_tiles(int N);                  // 32 x 32 tiles of an N x N image
