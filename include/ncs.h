@@ -306,6 +306,12 @@ int ncs_cone_solve(ncs_cone_plan* plan, const float* b, float* x, double tol, in
 /* *f = 1/2 ||K x - b||^2 + lambda TV(x) with FP64 reductions.  Synchronises. */
 int ncs_cone_objective(ncs_cone_plan* plan, const float* x, const float* b, double* f);
 
+/* *n = the CUDA kernels the plan has enqueued on its stream since creation (an iteration of
+ * ncs_cone_step is 8: the gather, five of the 3-D circulant solve, the forward pass with the
+ * data prox, the TV prox; ncs_cone_objective is 3).  A solve's CUDA graph is counted once, when
+ * it is captured, not per replay. */
+int ncs_cone_kernels(const ncs_cone_plan* plan, long long* n);
+
 /* out = M^{-1} r (the plan's 3-D circulant solve; N*N*Nz).  Asynchronous. */
 int ncs_cone_apply_Minv(ncs_cone_plan* plan, const float* r, float* out);
 

@@ -126,6 +126,7 @@ SIGNATURES = [
     ("ncs_cone_step", _I, [_P, _P, _P, _P, _P, _I]),
     ("ncs_cone_solve", _I, [_P, _P, _P, _D, _I, _D, ctypes.POINTER(Report)]),
     ("ncs_cone_objective", _I, [_P, _P, _P, _DP]),
+    ("ncs_cone_kernels", _I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
     ("ncs_cone_apply_Minv", _I, [_P, _P, _P]),
     ("ncs_cone_get_mu", _I, [_P, _DP]),
     ("ncs_cone_power_bound", _I, [_P, _DP]),
@@ -602,6 +603,12 @@ class ConePlan:
         self._call("ncs_cone_objective", self._L.ncs_cone_objective, self._h, _ptr(x, "x", self.n),
                    _ptr(b, "b", self.m), ctypes.byref(f))
         return f.value
+
+    def kernels(self):
+        """CUDA kernels the plan has enqueued since creation (a solve's graph counts once)."""
+        n = ctypes.c_longlong()
+        _check(self._L.ncs_cone_kernels(self._h, ctypes.byref(n)), "ncs_cone_kernels")
+        return n.value
 
     def apply_Minv(self, r, out=None):
         import torch

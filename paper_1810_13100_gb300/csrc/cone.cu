@@ -586,6 +586,7 @@ struct ncs_cone_plan {
     cudaGraphExec_t gexec = nullptr;
     const void* gkey[2] = {nullptr, nullptr};
     int gT = 0;
+    long long n_kern = 0;    // kernels enqueued on the stream (a captured graph counts once, at capture)
 };
 
 namespace {
@@ -630,6 +631,7 @@ int cenq_gather(ncs_cone_plan* p, const float* u, const float* v, float dscale, 
     dim3 grid((p->N + 2 * CQX - 1) / (2 * CQX), (p->N + 2 * CQY - 1) / (2 * CQY), p->Nz), block(CQX * CQY);
     k_cone_gather<<<grid, block, 0, p->st>>>(a);
     CONE_CK(cudaGetLastError());
+    p->n_kern += 1;
     return NCS_OK;
 }
 
@@ -648,6 +650,7 @@ int cenq_fwd(ncs_cone_plan* p, int mode, const float* x, float* out, const float
     else if (mode == FWD_PROX_L2) k_cone_fwd<FWD_PROX_L2><<<grid, block, 0, p->st>>>(a);
     else k_cone_fwd<FWD_RESID_L2><<<grid, block, 0, p->st>>>(a);
     CONE_CK(cudaGetLastError());
+    p->n_kern += 1;
     return NCS_OK;
 }
 
@@ -659,6 +662,7 @@ int cenq_td(ncs_cone_plan* p, int mode, const float* x, float* v, float beta, do
     else if (mode == TD3_APPLY) k_cone_td<TD3_APPLY><<<nb, T3B, 0, p->st>>>(x, v, p->N, p->Nz, beta, rad, p->iso, nullptr);
     else k_cone_td<TD3_OBJ><<<nb, T3B, 0, p->st>>>(x, v, p->N, p->Nz, beta, rad, p->iso, partials);
     CONE_CK(cudaGetLastError());
+    p->n_kern += 1;
     return NCS_OK;
 }
 
@@ -671,6 +675,7 @@ int cenq_solve(ncs_cone_plan* p, const float* r, const float* table, int mode, f
     CONE_CK(launch_z_dft(p->d_spec, table, p->d_twz, p->Nz, p->plane, 1, p->st));
     CONE_CK(launch_cols_fft_stack(p->d_spec, p->d_tw, p->rp, p->N, p->Nz, 1, p->st));
     CONE_CK(launch_rows_inv_stack(p->d_spec, p->d_tw, p->rp, p->N, p->Nz, mode, x, xbar, out, p->st));
+    p->n_kern += 5;
     return NCS_OK;
 }
 
@@ -938,6 +943,7 @@ int cenq_objective(ncs_cone_plan* p, const float* x, const float* b, bool resid,
     CONE_CKS(cenq_td(p, TD3_OBJ, x, nullptr, 0.f, p->d_part0));
     CONE_CK(launch_finalize(p->d_part1, p->n_part1, 0.5, p->d_part0, td_blocks(p->n), p->lam, p->d_scal + slot,
                             p->st));
+    p->n_kern += 1;
     return NCS_OK;
 }
 
@@ -1017,6 +1023,13 @@ int ncs_cone_objective(ncs_cone_plan* p, const float* x, const float* b, double*
     CONE_CK(cudaMemcpyAsync(p->h_pin + 1, p->d_scal + 1, sizeof(double), cudaMemcpyDeviceToHost, p->st));
     CONE_CK(cudaStreamSynchronize(p->st));
     *f = p->h_pin[1];
+    return NCS_OK;
+}
+
+int ncs_cone_kernels(const ncs_cone_plan* p, long long* n)
+{
+    if (!p || !n) return NCS_ERR_BADARG;
+    *n = p->n_kern;
     return NCS_OK;
 }
 
