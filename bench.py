@@ -142,7 +142,7 @@ class ClockSampler:
             fd, self.path = tempfile.mkstemp(prefix="ncs_clocks_", suffix=".csv")
             self.fh = os.fdopen(fd, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -311,8 +311,9 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "it/s", "n_gpus": args.gpus,
         "steps": len(times), "warmup": warm, "ms_per_step": 1000.0 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "512x512 TV-CT, 720 angles x 730 bins, iso TV lambda 0.005, seed %d" % args.seed,
-                   "l2": "n/a (host)"},
+        "config": {"workload": "512x512 TV-CT, 720 angles x 730 bins, iso TV lambda 0.005, 20 ellipses, "
+                               "0.5%% noise, seed %d" % args.seed,
+                   "parallelism": "single", "l2": "n/a (host)", "ncs": NCS_PARAMS},
         "cpu_baseline": {"value": value, "unit": "it/s", "cores": r["cores"], "kind": "oracle",
                          "sample": "%d FP64 oracle NCS iterations of the 512x512 workload from zero" % len(times)},
         "e2e": {"value": value, "unit": "it/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -526,6 +527,25 @@ def oracle_check_stops(ttg, stops):
     ttg["oracle_check"] = ("FP64 oracle objective at every stop on the oracle-made sinogram; a seed counts as "
                            "converged only with a tight f* record (last 1000 oracle iterations lowered f by "
                            "<= 1e-7 relative) and an oracle gap <= tol")
+
+
+def oracle_check_one(ttg, workload, seed, stops):
+    """The CPU leg's check of a single-seed time-to-gap line: the FP64 oracle's objective at
+    each solver's stop on the sinogram the stored f* was computed for (made with the oracle's
+    own K, oracle.fstar.problem); a solver counts as converged only when that gap is <= the
+    tolerance, its GPU solve stopped without error and the stored f* record is tight."""
+    from oracle import fstar, solvers as osv
+    P, _ = fstar.problem(workload, seed)
+    N = P.g.N
+    for solver, x in stops.items():
+        f = osv.objective(P, x.reshape(N, N))
+        tgt = ttg[solver]
+        tgt["oracle_f"] = f
+        tgt["oracle_gap"] = (f - ttg["f_star"]) / abs(ttg["f_star"])
+        ttg[solver + "_converged_oracle"] = int(bool(ttg["f_star_tight"]) and tgt["status"] == 0
+                                                and tgt["oracle_gap"] <= ttg["tol"])
+    ttg["oracle_check"] = ("FP64 oracle objective at every stop on the oracle-made sinogram; converged only "
+                           "with a tight f* record and an oracle gap <= tol")
 
 
 def run_ours(args, ws, rank, local):
@@ -805,24 +825,36 @@ def run_pet(args, ws, rank, local):
     barrier(ws)
     t_max = reduce_max(e0.elapsed_time(e1), ws)
     rate = reduce_sum(args.steps, ws) / (t_max / 1000.0)
+    # the same steps again (untimed), every kernel class bracketed: the kernels they launch
+    plan.profile(True)
+    plan.step(x, u, v, sv, b, bg, n_iter=args.steps)
+    plan.profile_read()
+    plan.profile(False)
+    launches = sum(plan.kernel_launches.values())
     ttg = None
     gold = load_golden("pet256", seed)
     if gold and not args.skip_ttg:
         fs = gold["f_star"]
-        ttg = {"tol": TTG_TOL, "f_star": fs, "oracle_iters": gold.get("iterations")}
+        ttg = {"tol": TTG_TOL, "gpu_stop_tol": TTG_STOP, "f_star": fs, "oracle_iters": gold.get("iterations"),
+               "f_star_tight": bool(gold.get("tight", False))}
+        stops = {}
         if "b_sum" in gold:
             bd = b.double()
             ttg["b_rel_diff"] = {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
                                  "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}
         xs = torch.zeros(n, device=dev)
-        rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=20000, f_star=fs, bg=bg)
+        rep = plan.solve(b, xs, tol=TTG_STOP, max_iter=20000, f_star=fs, bg=bg)
         ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        stops["ncs"] = xs.double().cpu().numpy()
         pplan = ncs.Plan(N, na, nd, W["lam"], PET_PDHG["alpha"], beta=PET_PDHG["beta"], data="kl", tv=W["tv"],
                          nonneg=True, check_every=CHECK_EVERY)
         xs.zero_()
-        rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=60000, f_star=fs, bg=bg)
+        rep = pplan.pdhg_solve(b, xs, tol=TTG_STOP, max_iter=60000, f_star=fs, bg=bg)
         ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        stops["pdhg"] = xs.double().cpu().numpy()
         pplan.close()
+        if rank == 0 and not args.skip_cpu:
+            oracle_check_one(ttg, "pet256", seed, stops)
     plan.close()
     if rank == 0:
         line = {"metric": "TV-PET NCS iterations/s and time to the 1e-4 gap vs PDHG (256x256)", "value": rate,
@@ -832,7 +864,7 @@ def run_pet(args, ws, rank, local):
                 "config": {"workload": "256x256 TV-PET, 180 angles x 257 bins, 15 ellipses, 1e6 counts, 10%% "
                                        "background, KL + aniso TV lambda 0.02 + nonnegativity, seed %d" % seed,
                            "ncs": PET_NCS, "pdhg": PET_PDHG, "l2": "resident (not flushed)"},
-                "time_to_gap": ttg, "clocks": clk.summary()}
+                "gpu_launches": launches, "time_to_gap": ttg, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 
 
@@ -924,24 +956,32 @@ def run_fan(args, ws, rank, local):
     if gold and not args.skip_ttg:
         fs = gold["f_star"]
         bd = b.double()
-        ttg = {"tol": TTG_TOL, "f_star": fs, "oracle_iters": gold.get("iterations"),
+        ttg = {"tol": TTG_TOL, "gpu_stop_tol": TTG_STOP, "f_star": fs, "oracle_iters": gold.get("iterations"),
+               "f_star_tight": bool(gold.get("tight", False)),
+               "f_star_decrease_last_1000_rel": gold["decrease_last_1000"] / abs(fs),
                "b_rel_diff": {"sum": abs(bd.sum().item() - gold["b_sum"]) / abs(gold["b_sum"]),
                               "sumsq": abs((bd * bd).sum().item() - gold["b_sumsq"]) / gold["b_sumsq"]}}
+        stops = {}
         xs = torch.zeros(n, device=dev)
-        rep = plan.solve(b, xs, tol=TTG_TOL, max_iter=4000, f_star=fs)
+        rep = plan.solve(b, xs, tol=TTG_STOP, max_iter=4000, f_star=fs)
         ttg["ncs"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        stops["ncs"] = xs.double().cpu().numpy()
         # PDHG's step comes from lambda_max(A^T A) by the plan's full power iteration
         pplan = fan_plan(ncs, W, FAN_PDHG, h_probes=1, fan_gather=args.fan_gather)
         xs.zero_()
-        rep = pplan.pdhg_solve(b, xs, tol=TTG_TOL, max_iter=args.pdhg_extended, f_star=fs)
+        rep = pplan.pdhg_solve(b, xs, tol=TTG_STOP, max_iter=args.pdhg_extended, f_star=fs)
         ttg["pdhg"] = {k: rep[k] for k in ("iters", "time_ms", "gap", "status")}
+        stops["pdhg"] = xs.double().cpu().numpy()
         pplan.close()
         aplan = fan_plan(ncs, W, FAN_ADMM, h_probes=FAN_NCS["h_probes"], fan_gather=args.fan_gather)
         xs.zero_()
-        rep = aplan.admm_solve(b, xs, tol=TTG_TOL, max_outer=ADMM_CAP, n_cg=FAN_ADMM["n_cg"], f_star=fs)
+        rep = aplan.admm_solve(b, xs, tol=TTG_STOP, max_outer=ADMM_CAP, n_cg=FAN_ADMM["n_cg"], f_star=fs)
         ttg["admm"] = dict(FAN_ADMM, outer=rep["iters"], time_ms=rep["time_ms"], gap=rep["gap"],
                            status=rep["status"])
+        stops["admm"] = xs.double().cpu().numpy()
         aplan.close()
+        if rank == 0 and not args.skip_cpu:
+            oracle_check_one(ttg, "fan512", seed, stops)
     plan.close()
     if rank == 0:
         line = {"metric": "fan-beam TV-CT NCS iterations/s (512x512, 720 views x 768 channels)", "value": value,
@@ -1137,7 +1177,7 @@ def run_unet(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=0)

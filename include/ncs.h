@@ -524,8 +524,9 @@ int ncs_unet_inject_wait_timeout(ncs_unet* net);
  * ncs_plan_create rejects with NCS_ERR_UNSUPPORTED; N < 8, null pointers or an
  * empty geometry return NCS_ERR_BADARG.  All calls share the array: calls whose work overlaps on the
  * GPU (several streams or host threads) race and must be serialised by the
- * caller.  The first call on a device looks up the array's address with that
- * device current; make it before any stream capture. */
+ * caller.  The call cannot be captured into a CUDA graph (it copies the angle
+ * table from host memory it owns): on a capturing stream it returns
+ * NCS_ERR_UNSUPPORTED and enqueues nothing. */
 int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float* y, float* x, void* cuda_stream);
 
 /* Human-readable name of a status code (static string). */

@@ -17,7 +17,9 @@
 // exits.  Every call shares it, so calls whose work overlaps on the GPU (two
 // streams, or two host threads) race; serialise them.  The first call on a
 // device looks up the array's device address (cudaGetSymbolAddress) with that
-// device current; make that first call before any stream capture.
+// device current.  Calls are not capturable into a CUDA graph (the angle table is
+// copied from host memory the call owns); on a capturing stream they return
+// NCS_ERR_UNSUPPORTED before touching the GPU.
 #include "../../include/ncs.h"
 #include "ncs_internal.cuh"
 
@@ -80,10 +82,17 @@ extern "C" int ncs_apply_KT_static(const ncs_geometry* geom, int N, const float*
     const double ds = geom->det_spacing > 0.0 ? geom->det_spacing : 1.0;
     if (!angle_table(N, geom->n_angles, geom->n_det, ds, geom->det_offset, geom->angles, ap))
         return NCS_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the angle table is copied from host memory owned by this call: no graph capture
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return NCS_ERR_UNSUPPORTED;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return NCS_ERR_UNSUPPORTED;
     unsigned char* base = nullptr;
     int rc = scratch_address(&base);
     if (rc != NCS_OK) return rc;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     AngleParam* d_ap = reinterpret_cast<AngleParam*>(base);
     int* d_order = reinterpret_cast<int*>(base + kParamBytes);
     int* d_count = reinterpret_cast<int*>(base + kParamBytes + kOrderBytes);

@@ -25,9 +25,21 @@ def test_counter_file_is_used_only_for_the_recorded_source(tmp_path):
 
 def test_committed_counter_file_parses():
     c = bench.load_counters("ct512")
-    assert set(c) >= {"k_gather", "k_fwd"}
+    assert set(c) >= {"k_gather", "k_fwd_strip", "k_fwd_sum"}
     for v in c.values():
         assert v["traffic"] > 0 and v["warp_instr"] > 0
+
+
+def test_counters_of_a_class_sum_its_kernels():
+    """The strip-form K is two kernels per launch: its class's counters are their sum, and
+    a class with any kernel missing or stale has none."""
+    cnt = {"k_fwd_strip": {"current": True, "traffic": 4.0, "warp_instr": 90.0},
+           "k_fwd_sum": {"current": True, "traffic": 25.0, "warp_instr": 1.0},
+           "k_gather": {"current": False, "traffic": 4.0, "warp_instr": 134.0}}
+    assert bench.counters_for(cnt, "joseph_fwd") == (29.0, 91.0)
+    assert bench.counters_for(cnt, "joseph_gather") == (None, None)
+    assert bench.counters_for(cnt, "joseph_fwd", ["k_fwd"]) == (None, None)
+    assert bench.counters_for(cnt, "joseph_fwd", "k_fwd_strip") == (4.0, 90.0)
 
 
 def test_tightness_of_a_record():

@@ -65,3 +65,27 @@ def test_static_backprojection_rejects_sizes_beyond_its_limit():
     g3.det_spacing = 0.5
     assert L.ncs_apply_KT_static(ctypes.byref(g3), 64, p, p, None) == binding.NCS_ERR_UNSUPPORTED
     assert L.ncs_apply_KT_static(None, 64, p, p, None) == binding.NCS_ERR_BADARG
+
+
+def test_static_backprojection_refuses_graph_capture():
+    """On a stream that is capturing a CUDA graph the call returns NCS_ERR_UNSUPPORTED and
+    enqueues nothing (its angle table is copied from host memory the call owns); the same
+    call outside the capture succeeds."""
+    from paper_1810_13100_gb300 import binding
+    L = binding.load_library()
+    N, na, nd = 64, 90, 92
+    g = _geom(binding, na, nd)
+    y = torch.rand(na * nd, device="cuda")
+    out = torch.zeros(N * N, device="cuda")
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        rc = L.ncs_apply_KT_static(ctypes.byref(g), N, ctypes.c_void_p(y.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+        out.add_(0.0)    # one captured torch op, so the graph is not empty
+    assert rc == binding.NCS_ERR_UNSUPPORTED
+    rc = L.ncs_apply_KT_static(ctypes.byref(g), N, ctypes.c_void_p(y.data_ptr()),
+                               ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(s.cuda_stream))
+    s.synchronize()
+    assert rc == 0 and torch.isfinite(out).all()
