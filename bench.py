@@ -760,6 +760,30 @@ def run_batch(args, ws, rank, local):
         ms = reps[0]["time_ms"]
         t_max = reduce_max(ms, ws)
         total = reduce_sum(args.steps * len(plans), ws)
+        # kernels per iteration of each slice, counted by its plan's profiler on one untimed
+        # step; a solve adds the TV sum and the FP64 finalisation every check_every iterations
+        kpi = []
+        for p_, b_, x_ in zip(plans, bs, xs):
+            m_ = p_.m
+            u_ = torch.zeros(m_, device="cuda", dtype=torch.bfloat16 if prec == "bf16" else torch.float32)
+            v_ = torch.zeros(2 * p_.n, device="cuda", dtype=u_.dtype)
+            xt_ = torch.zeros(p_.n, device="cuda")
+            p_.profile(True)
+            p_.step(xt_, u_, v_, None, b_, n_iter=1)
+            p_.profile_read()
+            p_.profile(False)
+            kpi.append(sum(p_.kernel_launches.values()))
+        launches = sum(args.steps * k + 2 * (args.steps // CHECK_EVERY) for k in kpi)
+        # the same slices one after another, each by its own solve on its plan's stream
+        seq_ms = None
+        if prec == "fp32":
+            for x in xs:
+                x.zero_()
+            torch.cuda.synchronize()
+            seq_ms = 0.0
+            for p_, b_, x_ in zip(plans, bs, xs):
+                rep_ = p_.solve(b_, x_, tol=0.0, max_iter=args.steps, f_star=-1e300)
+                seq_ms += rep_["time_ms"]
         pix = reduce_sum(args.steps * sum(N * N for N in sides), ws)
         # algorithmic HBM bytes of one iteration of every slice (FP32 state read + written
         # once, b read, spectrum round trips: 4 (10 n + 3 m) per slice; BF16 storage halves
@@ -772,7 +796,12 @@ def run_batch(args, ws, rank, local):
                              "peak_gbs": peaks.get("hbm_gbs", 6800.0), "frac": gbs / peaks.get("hbm_gbs", 6800.0),
                              "peak_kind": peak_kind},
                      "ms_per_batch_iteration": t_max / args.steps, "clocks": clk.summary(), "lanes": lanes,
-                     "gather_parts": [p.info()["gather_parts"] for p in plans[:4]]}
+                     "gather_parts": [p.info()["gather_parts"] for p in plans[:4]], "gpu_launches": launches}
+        if seq_ms is not None:
+            out[prec]["sequential"] = {"slice_iters_per_s": args.steps * len(plans) / (seq_ms / 1000.0),
+                                       "ms": seq_ms, "what": "the same slices and iterations, one plan's "
+                                       "ncs_solve after another (CUDA graphs of check_every iterations each)"}
+            out[prec]["speedup_vs_sequential"] = seq_ms / ms
         batch.close()
         for p in plans:
             p.close()
@@ -784,7 +813,7 @@ def run_batch(args, ws, rank, local):
                 "config": {"workload": "%d slices, sides %s, round(1.4 side) angles, side + 2 bins, iso TV "
                                        "lambda 0.005, seed %d" % (len(sides), sorted(set(sides)), args.seed),
                            "sides": sides, "l2": "working set exceeds L2 (not flushed)"},
-                "variants": out}
+                "gpu_launches": out["fp32"]["gpu_launches"], "variants": out}
         print(json.dumps(line), flush=True)
 
 
