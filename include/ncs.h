@@ -108,11 +108,11 @@ typedef struct {
                               admm_solve, ncs_apply_Minv, ncs_get_mu and ncs_batch_create then return
                               NCS_ERR_UNSUPPORTED for it, and its report's rho is NaN.  0 (default): full plan */
     int fwd_kernel;        /* parallel-beam plans, the K kernel (both evaluate the same matrix, summed in a
-                              different order): 0 (default): image strips staged in shared memory where
-                              at most 16 strips cover the image (N up to about 660), else the row walk; 1: the row
-                              walk (each ray reads its rows from L2); 2: strips, NCS_ERR_UNSUPPORTED if the
-                              image is too large for them.  The strip form holds n_strip * n_angles * n_det
-                              floats of scratch (at 512 x 512 with 720 x 730: 10 strips, 21 MB) */
+                              different order): 0 (default): image strips staged in shared memory (N <= 864),
+                              else the row walk; 1: the row walk (each ray reads its rows from L2); 2: strips,
+                              NCS_ERR_UNSUPPORTED if the image is too large for them.  The strip form holds
+                              n_strip * n_angles * n_det floats of scratch (at 512 x 512 with 720 x 730: 5
+                              strips of 103 rows, 10.5 MB) */
 } ncs_options;
 
 /* Result of ncs_solve / pdhg_solve. */

@@ -269,14 +269,14 @@ k_fwd(FwdArgs g)
 // epilogue.  Rows are stepped with the same 32.32 crossing and fix_weight as k_fwd and the
 // gather, so all three hold one matrix.  SPC is a compile-time row pitch (fwd_strip_pitch),
 // so the four rows of an unrolled step sit at constant offsets from one another.
-constexpr int FS_WARPS = 16;                 // warps per strip block (two blocks per SM)
+constexpr int FS_WARPS = 32;                 // warps per strip block (one block per SM)
 constexpr int FSUM_T = 256;                  // threads per block of the strip sum, 4 rays each
-constexpr int FS_SMEM = 110 * 1024;          // strip bytes per block
+constexpr int FS_SMEM = 220 * 1024;          // strip bytes per block
 constexpr int FWD_MAX_STRIPS = 16;
-constexpr int FS_PITCHES[] = {72, 136, 264, 392, 520, 656};   // strip row pitches (floats)
+constexpr int FS_PITCHES[] = {72, 136, 264, 392, 520, 656, 776, 872};   // strip row pitches (floats)
 
 template <bool PBF, int SPC>
-__global__ void __launch_bounds__(FS_WARPS * 32, 2)
+__global__ void __launch_bounds__(FS_WARPS * 32, 1)
 k_fwd_strip(FwdArgs g)
 {
     extern __shared__ float strip[];
@@ -305,9 +305,15 @@ k_fwd_strip(FwdArgs g)
     const int lane = threadIdx.x & 31;
     float* out = g.spart + (size_t)blockIdx.y * fwd_strip_plane(g.n_ang, g.n_det);
     const unsigned last = (unsigned)(SP - 2);      // the last tap pair inside a strip row
-    for (int it = threadIdx.x >> 5; it < cnt * chunks; it += FS_WARPS) {
-        const int ai = it / chunks;
-        const int c = it - ai * chunks;
+    // items (angle ai of the slice, 32-bin chunk c) in order, FS_WARPS apart: (ai, c) advanced
+    // without a division
+    int ai = (threadIdx.x >> 5) / chunks, c = (threadIdx.x >> 5) - ai * chunks;
+    for (; ai < cnt; c += FS_WARPS) {
+        while (c >= chunks) {
+            c -= chunks;
+            ++ai;
+        }
+        if (ai >= cnt) break;
         const int a = __ldg(list + lo + ai);
         const int t = c * 32 + lane;
         const short2 wr = __ldg(g.wrange + (size_t)a * chunks + c);
@@ -898,7 +904,7 @@ int fwd_strip_pitch(int N)
 }
 
 // Strip shape of the parallel-beam K for an N x N image: the rows per strip that leave room
-// for two blocks per SM (FS_SMEM bytes each) and the number of strips; false when more than
+// for one block per SM (FS_SMEM bytes) and the number of strips; false when more than
 // FWD_MAX_STRIPS would be needed (the row walk k_fwd serves such images).
 bool fwd_strip_shape(int N, int* rows, int* strips)
 {
@@ -924,8 +930,10 @@ cudaError_t fwd_prepare()
 {
     const cudaError_t e[] = {fwd_strip_attr<false, 72>(), fwd_strip_attr<false, 136>(), fwd_strip_attr<false, 264>(),
                              fwd_strip_attr<false, 392>(), fwd_strip_attr<false, 520>(), fwd_strip_attr<false, 656>(),
+                             fwd_strip_attr<false, 776>(), fwd_strip_attr<false, 872>(),
                              fwd_strip_attr<true, 72>(), fwd_strip_attr<true, 136>(), fwd_strip_attr<true, 264>(),
-                             fwd_strip_attr<true, 392>(), fwd_strip_attr<true, 520>(), fwd_strip_attr<true, 656>()};
+                             fwd_strip_attr<true, 392>(), fwd_strip_attr<true, 520>(), fwd_strip_attr<true, 656>(),
+                             fwd_strip_attr<true, 776>(), fwd_strip_attr<true, 872>()};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;
@@ -940,7 +948,9 @@ void fwd_strip_dispatch(int sp, const FwdArgs& a, dim3 grid, size_t smem, cudaSt
         case 264: k_fwd_strip<PBF, 264><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
         case 392: k_fwd_strip<PBF, 392><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
         case 520: k_fwd_strip<PBF, 520><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
-        default: k_fwd_strip<PBF, 656><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        case 656: k_fwd_strip<PBF, 656><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        case 776: k_fwd_strip<PBF, 776><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
+        default: k_fwd_strip<PBF, 872><<<grid, FS_WARPS * 32, smem, st>>>(a); break;
     }
 }
 
@@ -1011,8 +1021,8 @@ cudaError_t launch_fwd(int mode, const FwdArgs& a, cudaStream_t st)
         cudaError_t e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        // two resident blocks per SM: n_strip x 2 branches x G angle slices fill them once
-        const dim3 sgrid(std::max(1, sms / a.n_strip), a.n_strip, 2);
+        // one resident block per SM: n_strip x 2 branches x G angle slices fill them once
+        const dim3 sgrid(std::max(1, sms / (2 * a.n_strip)), a.n_strip, 2);
         const size_t smem = (size_t)a.strip_rows * sp * sizeof(float);
         if (a.pair_bf) fwd_strip_dispatch<true>(sp, a, sgrid, smem, st);
         else fwd_strip_dispatch<false>(sp, a, sgrid, smem, st);

@@ -3,8 +3,8 @@ strip and a fixed-order sum of the strips) against the FP64 oracle and against t
 (each ray reads its rows from L2): both evaluate the same 32.32 crossings and weights and
 differ only in the FP32 summation order.
 
-Cases: strip counts 1 to 16 with ragged last strips (N = 256: 86 + 86 + 84 rows; N = 648:
-16 strips of 41 with 33 in the last), bin counts that leave a partial warp, angle sets with
+Cases: strip counts 1 to 14 with ragged last strips (N = 512: 5 strips of 103 rows with 100
+in the last; N = 864: 14 of 62 with 58 in the last), bin counts that leave a partial warp, angle sets with
 an empty branch (every angle within 30 degrees of the x axis, or of the y axis), a single
 ray, and every epilogue of the forward pass inside NCS iterations (L2 data prox with the
 running K x and its FP64 data term, the KL prox, both objective sums), with FP32 and with
@@ -34,8 +34,9 @@ def plan(N, na, nd, kernel, **kw):
     return ncs.Plan(N, na, nd, lam, alpha, fwd_kernel=kernel, **kw)
 
 
-@pytest.mark.parametrize("N,na,nd,strips", [(32, 48, 46, 1), (96, 140, 130, 1), (256, 90, 258, 3),
-                                            (384, 64, 386, 6), (512, 720, 730, 10), (648, 40, 650, 16)])
+@pytest.mark.parametrize("N,na,nd,strips", [(32, 48, 46, 1), (96, 140, 130, 1), (256, 90, 258, 2),
+                                            (384, 64, 386, 3), (512, 720, 730, 5), (648, 40, 650, 8),
+                                            (864, 24, 866, 14)])
 def test_strip_forward_against_oracle_and_row_walk(N, na, nd, strips):
     rng = np.random.default_rng(N + nd)
     x = f32(rng.uniform(-1, 1, (N, N)))
@@ -56,11 +57,11 @@ def test_strip_forward_against_oracle_and_row_walk(N, na, nd, strips):
     [0.0, 1e-4, math.pi / 4, math.pi / 2 - 1e-4, 3 * math.pi / 4],  # ties and near-axis angles
 ])
 def test_strip_forward_with_an_empty_branch(theta):
-    N, nd = 192, 37                                               # 2 strips; 37 bins: one partial warp
+    N, nd = 384, 37                                               # 3 strips; 37 bins: one partial warp
     g = oop.Geometry(N, len(theta), nd, theta=np.array(theta))
     x = f32(np.random.default_rng(5).uniform(0, 1, (N, N)))
     p = plan(N, len(theta), nd, "strips", angles=theta)
-    assert p.fwd_strips()[0] == 2
+    assert p.fwd_strips()[0] == 3
     y = p.apply_K(torch.from_numpy(x.ravel().astype(np.float32)).cuda())
     assert rel_l2(to_np(y), oop.K(x, g)) <= TOL
     p.close()
@@ -118,7 +119,7 @@ def test_strip_forward_inside_iterations(kind):
 def test_strip_option_errors():
     import paper_1810_13100_gb300 as ncs
     from paper_1810_13100_gb300 import binding
-    # 1024 x 1024 needs 38 strips: "strips" is refused, "auto" takes the row walk
+    # 1024 x 1024 has no strip pitch: "strips" is refused, "auto" takes the row walk
     with pytest.raises(binding.NCSError) as e:
         plan(1024, 4, 1026, "strips", pdhg_only=True)
     assert e.value.code == binding.NCS_ERR_UNSUPPORTED
