@@ -197,3 +197,22 @@ def test_cone_solve_reaches_gap_checked_by_oracle():
     f = oc.objective(P, to_np(x).reshape(g.shape))
     print("cone solve: %d iterations, %.1f ms, oracle gap %.3e" % (rep["iters"], rep["time_ms"], (f - fs) / fs))
     assert fs * (1 - 1e-7) <= f <= fs * (1 + 1e-4)
+
+
+def test_cone_plan_counts_its_kernels():
+    """ncs_cone_kernels: an NCS step enqueues 8 kernels (the gather, five of the 3-D circulant
+    solve, the forward pass with the data prox, the TV prox) and an objective 3."""
+    import paper_1810_13100_gb300 as ncs
+    g, pr, _ = oproblem(0.01, 0.02, "iso")
+    plan = nplan(ncs, 0.01, 0.02, "iso", h_probes=4)
+    b = torch.from_numpy(pr["b"].ravel()).cuda()
+    x = torch.zeros(g.n, device="cuda")
+    u = torch.zeros(b.numel(), device="cuda")
+    v = torch.zeros(3 * g.n, device="cuda")
+    k0 = plan.kernels()
+    plan.step(x, u, v, b, n_iter=3)
+    assert plan.kernels() - k0 == 24
+    k1 = plan.kernels()
+    plan.objective(x, b)
+    assert plan.kernels() - k1 == 3
+    plan.close()
