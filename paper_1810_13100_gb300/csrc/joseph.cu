@@ -525,11 +525,14 @@ k_gather(GatherArgs g)
             float wu = U[ui];
             float vr = fmaf(-w, wu, wu), vl = w * wu;
             // branch-free: only the step to the next ray is conditional; the weight and W u of
-            // the current ray are recomputed at every position
+            // the current ray are recomputed at every position.  One compare per position: the
+            // test "the current ray crosses at k" of position k is "at (k + 1) - 1" for position
+            // k + 1, and its 0/1 factor m serves both adds by a multiply-add
+            bool adv = k0 == -1;
+            float m = adv ? 1.0f : 0.0f;
 #pragma unroll
             for (int k = 0; k < GT; ++k) {
-                const bool adv = k0 == k - 1;
-                acc[k] += adv ? vl : 0.0f;
+                acc[k] = fmaf(m, vl, acc[k]);
                 if (adv) {
                     G += step;
                     ui += dir;
@@ -538,7 +541,9 @@ k_gather(GatherArgs g)
                 wu = U[ui];
                 vr = fmaf(-w, wu, wu);
                 vl = w * wu;
-                acc[k] += k0 == k ? vr : 0.0f;
+                adv = k0 == k;
+                m = adv ? 1.0f : 0.0f;
+                acc[k] = fmaf(m, vr, acc[k]);
             }
         }
         __syncwarp();
