@@ -354,8 +354,10 @@ cudaError_t fft_prepare(int N)
 {
     // each FFT block stages two length-N complex sequences: above 48 KB (N > 3072) the
     // kernels must opt in to the larger dynamic shared memory of the current device
-    const int smem = 2 * N * (int)sizeof(float2);
-    if (smem <= 48 * 1024) return cudaSuccess;
+    // (the attribute belongs to the kernel, not to a plan: it is set to what the largest side,
+    // 4096, needs, so that a smaller plan made later does not lower it below an earlier one's)
+    if (2 * N * (int)sizeof(float2) <= 48 * 1024) return cudaSuccess;
+    const int smem = 2 * 4096 * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_rows_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_cols_ratio, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
