@@ -717,7 +717,7 @@ k_gather_fan(GatherArgs g)
 
 constexpr int LT = 32;     // line-walk fan gather: 32 x 32 pixel tile per block
 constexpr int LW = 4;      // warps per block, each with a private shared tile
-constexpr int LCAP = 64;   // rays staged per warp at a time
+constexpr int LCAP = 32;   // rays staged per warp at a time
 
 // K^T for the fan beam, ray-driven (no atomics).  A block owns a 32 x 32 tile and a slice of
 // the views; warps take whole views round robin.  Lane l owns line l of the tile: row j0 + l
@@ -739,16 +739,25 @@ template <int MODE, bool SBF, bool IBF>
 __global__ void __launch_bounds__(LT * LW)
 k_gather_fan_lines(GatherArgs g)
 {
-    __shared__ float acc[LW][LT][LT + 1];
+    // the sums of rays stepped over rows (pitch LT + 2) and over columns (pitch LT) go to separate
+    // tiles: all lanes walk the same staged ray (broadcast reads), and a ray of slope B in
+    // (-1, 1) puts lane l's tap in bank (2 + B) l + c of the row tile and in bank l of the
+    // column tile, so the read-modify-writes conflict at most two ways
+    __shared__ float tr[LW][LT][LT + 2];
+    __shared__ float tc[LW][LT][LT];
     __shared__ float stage[LW][5][LCAP];      // Bhi, Blo, Chi, Clo, |W| u of the staged rays
     __shared__ int s_last;
     const int N = g.N, nd = g.n_det;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int i0 = blockIdx.x * LT, j0 = blockIdx.y * LT;
-    float (*A)[LT + 1] = acc[wid];
+    float (*AR)[LT + 2] = tr[wid];
+    float (*AC)[LT] = tc[wid];
     float (*S)[LCAP] = stage[wid];
     if (g.iter && tid == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) *g.iter += 1ull;
-    for (int rr = 0; rr < LT; ++rr) A[rr][lane] = 0.0f;
+    for (int rr = 0; rr < LT; ++rr) {
+        AR[rr][lane] = 0.0f;
+        AC[rr][lane] = 0.0f;
+    }
     __syncwarp();
     const int P = gridDim.z, part = blockIdx.z;
     const int a_beg = (int)(((long long)g.n_ang * part) / P);
@@ -808,36 +817,37 @@ k_gather_fan_lines(GatherArgs g)
                 const int s0 = rowpass ? 0 : LCAP - nC;
                 const float lf = rowpass ? lrow : lcol;
                 const int o0 = rowpass ? i0 : j0;
-                int sidx = (lane * 11) % n;
                 for (int k = 0; k < n; ++k) {
-                    const int e = s0 + sidx;
+                    const int e = s0 + k;                            // the same ray in every lane
                     int k0;
                     const float w = split_weight(fmaf(S[0][e], lf, S[2][e]), fmaf(S[1][e], lf, S[3][e]), k0);
                     const float Wu = S[4][e];
                     const int kk = k0 - o0;
                     if ((unsigned)kk < (unsigned)LT) {
-                        float& d = rowpass ? A[lane][kk] : A[kk][lane];
+                        float& d = rowpass ? AR[lane][kk] : AC[kk][lane];
                         d = fmaf(1.0f - w, Wu, d);
                     }
                     if ((unsigned)(kk + 1) < (unsigned)LT) {
-                        float& d = rowpass ? A[lane][kk + 1] : A[kk + 1][lane];
+                        float& d = rowpass ? AR[lane][kk + 1] : AC[kk + 1][lane];
                         d = fmaf(w, Wu, d);
                     }
-                    sidx = sidx + 1 == n ? 0 : sidx + 1;
                 }
             }
             __syncwarp();
         }
     }
     __syncthreads();
-    // sum the warp tiles in a fixed order; thread -> pixels (q*LW + wid, lane)
+    // sum the warp tiles in a fixed order (row tiles, then column tiles); thread -> pixels
+    // (q*LW + wid, lane)
     float tot[LT / LW];
 #pragma unroll
     for (int q = 0; q < LT / LW; ++q) {
         const int rr = q * LW + wid;
         float sum = 0.0f;
 #pragma unroll
-        for (int w = 0; w < LW; ++w) sum += acc[w][rr][lane];
+        for (int w = 0; w < LW; ++w) sum += tr[w][rr][lane];
+#pragma unroll
+        for (int w = 0; w < LW; ++w) sum += tc[w][rr][lane];
         tot[q] = sum;
     }
     if (P > 1) {
